@@ -1,0 +1,449 @@
+"""Benchmark: generalized non-exponential Gaussian splatting on GB300, one JSON line on stdout.
+
+Workload (default): one view of a 500k-Gaussian clustered scene (SH degree 3, FP32) at 1920x1080,
+rendered and differentiated under all four transmittance models (exponential; quadratic with
+c = -0.5, 0, +0.5). One step = for each model: render (projection, depth sort, key emission, tile
+sort, tile ranges, compositing) + path-replay backward (compositing replay, projection backward)
+through the library's C ABI, with a fixed upstream gradient (the L1-loss gradient against a target
+rendered from N(0, 0.01)-perturbed parameters). Inputs are resident in HBM before timing; L2 is flushed
+(256 MB write) between steps.
+
+Multi-GPU: one process per GPU (torchrun); rank r renders its own view (a pose rotated about the
+scene) -- independent units, no data-path collective ("weak" scaling). Rank 0 prints the line.
+
+``--impl reference`` times the FP64 CPU oracle on a bounded crop of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MODELS = ("exp", "sub", "lin", "sup")
+METRIC = "Mpix/s fwd & fwd+bwd per transmittance model; overdraw/pixel; p50/p99 latency"
+WORKLOAD = "single view, 500k clustered Gaussians (SH 3, FP32), 1920x1080, 4 transmittance models, fwd+bwd"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--gaussians", type=int, default=500_000)
+    p.add_argument("--width", type=int, default=1920)
+    p.add_argument("--height", type=int, default=1080)
+    p.add_argument("--tile", default="16x16")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-crop", type=int, default=0, help="oracle crop side (0: sized automatically)")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------------
+def workload(args, rank):
+    from paper_2603_02887_gb300 import synth
+
+    scene = synth.clustered_scene(args.gaussians, seed=0, sh_degree=3)
+    cam = synth.outside_camera(args.width, args.height)
+    if rank > 0:  # another view of the same scene: rotate the eye about the vertical axis
+        R = np.asarray(cam["viewmat"], np.float64)[:, :3]
+        t = np.asarray(cam["viewmat"], np.float64)[:, 3]
+        eye = -R.T @ t
+        a = 2 * math.pi * rank / 8
+        rot = np.array([[math.cos(a), 0, math.sin(a)], [0, 1, 0], [-math.sin(a), 0, math.cos(a)]])
+        cam = synth.look_at(rot @ eye, np.zeros(3), args.width, args.height)
+    return scene, cam
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_02887_gb300 import synth
+    from paper_2603_02887_gb300.render import PARAM_KEYS, Renderer
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tw, th = (int(v) for v in args.tile.split("x"))
+    opts = dict(tile_w=tw, tile_h=th)
+
+    scene, cam = workload(args, rank)
+    H, W = cam["height"], cam["width"]
+    params = {k: torch.from_numpy(np.ascontiguousarray(scene[k])).to(dev) for k in PARAM_KEYS}
+    r = Renderer(dev)
+    frames = {m: r.frame() for m in MODELS}
+    images = {m: torch.empty((H, W, 3), device=dev) for m in MODELS}
+    ods = {m: torch.empty((H, W), dtype=torch.int32, device=dev) for m in MODELS}
+    grads = {m: {"d_" + k: torch.empty_like(params[k]) for k in PARAM_KEYS} for m in MODELS}
+    # upstream gradient: L1 loss against a target rendered from perturbed parameters
+    target_params = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+                     for k, v in synth.perturbed(scene, seed=1).items()}
+    dl = {}
+    for m in MODELS:
+        tgt, _, f = r.render(target_params, cam, m, opts)
+        img, _, _ = r.render(params, cam, m, opts, frame=frames[m], image=images[m], overdraw=ods[m])
+        dl[m] = torch.sign(img - tgt).contiguous()
+        r.recycle(f)
+    del target_params
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(per_model_events=None):
+        for m in MODELS:
+            ev = per_model_events[m] if per_model_events is not None else None
+            if ev:
+                ev[0].record()
+            r.render(params, cam, m, opts, frame=frames[m], image=images[m], overdraw=ods[m])
+            if ev:
+                ev[1].record()
+            r.backward(frames[m], params, dl[m], out=grads[m])
+            if ev:
+                ev[2].record()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    # timed region
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    model_ev = [{m: [torch.cuda.Event(enable_timing=True) for _ in range(3)] for m in MODELS} for _ in range(K)]
+    r.set_timing(True)
+    r.reset_stage_times()
+    launches0 = r.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(K):
+        flush.zero_()
+        starts[i].record()
+        step(model_ev[i])
+        ends[i].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = r.launch_count() - launches0
+    stage = r.stage_times()
+    r.set_timing(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / K
+    px = W * H
+    value = world * len(MODELS) * px / (ms_per_step * 1e-3) / 1e6
+
+    per_model = {}
+    for m in MODELS:
+        fwd = statistics.median(model_ev[i][m][0].elapsed_time(model_ev[i][m][1]) for i in range(K))
+        fb = statistics.median(model_ev[i][m][0].elapsed_time(model_ev[i][m][2]) for i in range(K))
+        od = ods[m].double()
+        hist = torch.bincount(ods[m].reshape(-1).clamp(max=255).long(), minlength=256)[:256].cpu().numpy()
+        per_model[m] = dict(fwd_mpix_s=round(px / (fwd * 1e-3) / 1e6, 1), fwd_bwd_mpix_s=round(px / (fb * 1e-3) / 1e6, 1),
+                            fwd_ms=round(fwd, 4), fwd_bwd_ms=round(fb, 4), overdraw_mean=round(float(od.mean()), 3),
+                            overdraw_p50=int(np.searchsorted(np.cumsum(hist), 0.5 * px)),
+                            overdraw_p99=int(np.searchsorted(np.cumsum(hist), 0.99 * px)),
+                            overdraw_hist_16=[int(x) for x in np.add.reduceat(hist, np.arange(0, 256, 16))])
+    for m in MODELS[1:]:
+        per_model[m]["overdraw_reduction_vs_exp"] = round(per_model["exp"]["overdraw_mean"] /
+                                                          max(per_model[m]["overdraw_mean"], 1e-9), 3)
+
+    # roofline of the dominant stage
+    stage_ms = {k: v[0] / K for k, v in stage.items()}
+    dominant = max(stage_ms, key=stage_ms.get)
+    roof = roofline(dominant, stage_ms, frames, ods, args.gaussians, measured_peaks(), clk)
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "gaussians": args.gaussians, "width": W, "height": H, "sh_degree": 3,
+                   "models": {"exp": "exponential", "sub": "quadratic c=-0.5", "lin": "quadratic c=0",
+                              "sup": "quadratic c=+0.5"},
+                   "tile": args.tile, "step": "per model: render + path-replay backward",
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"views x{world}",
+                   "pairs_per_view": int(frames["exp"].view()["n_pairs"])},
+        "per_model": per_model,
+        "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
+        "gpu_launches": int(launches), "gpu_launches_per_step": round(launches / K, 1),
+        "roofline": roof, "clocks": clk,
+    }
+    if not args.no_e2e:
+        line["e2e"] = run_e2e(args, r, scene, cam, opts, dl, dev, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, scene, cam)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    r.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# algorithmic work per unit ("Roofline"): FLOPs count an FMA as 2
+FLOP_TEST = 11                              # per walked list entry: d = p - mu, the quadratic form, the alpha test
+FLOP_FWD = {"quad": 20, "exp": 12}          # per composited splat, forward
+FLOP_BWD = {"quad": 50, "exp": 45}          # per composited splat, replay + chain to the splat record
+BYTES = {  # per Gaussian (projection, depth sort, projection backward) or per (tile, Gaussian) pair
+    "project": 236 + 48 + 12, "depth_sort": 16, "scan_emit": 12, "tile_sort": 24, "tile_ranges": 8,
+    "project_bwd": 236 + 48 + 236,
+}
+
+
+class _DevArray:
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 2, "strides": None}
+
+
+def _walked_and_composited(frame, od):
+    """Sum over pixels of list entries walked (the replay state's n) and of splats composited (overdraw)."""
+    import torch
+
+    v = frame.view()
+    st = torch.as_tensor(_DevArray(v["pixel_state"], (v["height"] * v["width"], 8), "<i4"), device="cuda")
+    walked = float((st[:, 0] & 0x7FFFFFFF).double().sum())
+    return walked, float(od.double().sum())
+
+
+def roofline(dominant, stage_ms, frames, ods, n_gauss, peaks, clk):
+    """Roofline of the dominant stage, per launch (one launch per model per step).
+
+    Compositing stages are bound by FP32 issue: achieved = algorithmic FLOPs / CUDA-event time against
+    152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (maximum SM clock). Streaming stages are HBM bound:
+    algorithmic bytes / time against the measured copy bandwidth."""
+    import torch
+
+    sm_count = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    if dominant in ("composite_fwd", "composite_bwd"):
+        flops = 0.0
+        for m, f in frames.items():
+            walked, comp = _walked_and_composited(f, ods[m])
+            kind = "exp" if m == "exp" else "quad"
+            per = FLOP_FWD[kind] if dominant == "composite_fwd" else FLOP_BWD[kind]
+            flops += FLOP_TEST * walked + per * comp
+        flops /= len(frames)  # per launch
+        t = stage_ms[dominant] / len(frames) * 1e-3
+        achieved = flops / t / 1e12
+        peak = sm_count * 128 * 2 * 2070e6 / 1e12
+        out = {"bound": "alu", "kernel": dominant, "achieved": round(achieved, 3), "peak": round(peak, 2),
+               "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+               "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts and max clock)",
+               "flops_per_launch": flops}
+        if clk.get("sm_mhz"):
+            out["frac_at_observed_clock"] = round(achieved / (peak * clk["sm_mhz"] / 2070.0), 4)
+        return out
+    pairs = float(np.mean([f.view()["n_pairs"] for f in frames.values()]))
+    units = pairs if dominant in ("scan_emit", "tile_sort", "tile_ranges") else n_gauss
+    nbytes = BYTES.get(dominant, 0) * units
+    t = stage_ms[dominant] / len(frames) * 1e-3
+    achieved = nbytes / t / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    return {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+
+def run_e2e(args, r, scene, cam, opts, dl, dev, world):
+    """Same metric through the public API with host buffers: each step copies the parameters and the
+    upstream gradients from pinned host memory, renders + backpropagates every model, and reads the
+    images, overdraw maps and gradients back to pinned host memory."""
+    import torch
+
+    from paper_2603_02887_gb300.render import PARAM_KEYS
+
+    H, W = cam["height"], cam["width"]
+    host = {k: torch.from_numpy(np.ascontiguousarray(scene[k])).pin_memory() for k in PARAM_KEYS}
+    host_dl = {m: dl[m].cpu().pin_memory() for m in MODELS}
+    dev_p = {k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in host.items()}
+    dev_dl = {m: torch.empty_like(dl[m]) for m in MODELS}
+    out_img = {m: torch.empty((H, W, 3)).pin_memory() for m in MODELS}
+    out_od = {m: torch.empty((H, W), dtype=torch.int32).pin_memory() for m in MODELS}
+    out_g = {m: {k: torch.empty(v.shape).pin_memory() for k, v in host.items()} for m in MODELS}
+    frames = {m: r.frame() for m in MODELS}
+    h2d = sum(v.numel() * 4 for v in host.values()) + sum(v.numel() * 4 for v in host_dl.values())
+    d2h = sum(H * W * 16 + sum(v.numel() * 4 for v in host.values()) for _ in MODELS)
+
+    def step():
+        for k in PARAM_KEYS:
+            dev_p[k].copy_(host[k], non_blocking=True)
+        for m in MODELS:
+            dev_dl[m].copy_(host_dl[m], non_blocking=True)
+            img, od, f = r.render(dev_p, cam, m, opts, frame=frames[m])
+            g = r.backward(f, dev_p, dev_dl[m])
+            out_img[m].copy_(img, non_blocking=True)
+            out_od[m].copy_(od, non_blocking=True)
+            for k in PARAM_KEYS:
+                out_g[m][k].copy_(g["d_" + k], non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    K = max(3, args.steps // 2)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(K):
+        step()
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e) / K
+    for f in frames.values():
+        r.recycle(f)
+    return {"value": round(world * len(MODELS) * W * H / (ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
+            "ms_per_step": round(ms, 3), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": K}
+
+
+# ---------------------------------------------------------------------------------------------------
+def oracle_sample(scene, cam, crop, nthreads):
+    """FP64 oracle (as it stands): fwd + bwd of the 4 models on a centred crop x crop window."""
+    import oracle
+    from paper_2603_02887_gb300 import synth
+
+    W, H = cam["width"], cam["height"]
+    win = (W // 2 - crop // 2, H // 2 - crop // 2, crop, crop)
+    g = synth.upstream_gradient(crop, crop, seed=3)
+    t = time.perf_counter()
+    for m in MODELS:
+        oracle.render(scene, cam, m, window=win, nthreads=nthreads, dl_dimage=g)
+    return time.perf_counter() - t, len(MODELS) * crop * crop
+
+
+def cpu_baseline(args, scene, cam, crop=None):
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    crop = crop or args.cpu_crop or 640  # about 10-20 s of oracle work on 16 cores
+    secs, px = oracle_sample(scene, cam, crop, cores)
+    return {"value": round(px / secs / 1e6, 5), "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+            "seconds": round(secs, 2),
+            "sample": f"FP64 oracle, render + backward of the 4 models on the centred {crop}x{crop} crop of the same "
+                      f"view ({len(MODELS)} x {crop * crop} px; every call re-projects all {args.gaussians} Gaussians)"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    scene, cam = workload(args, 0)
+    crop = args.cpu_crop or 96
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_sample(scene, cam, crop, cores)
+    times = []
+    px = 0
+    for _ in range(args.steps):
+        secs, px = oracle_sample(scene, cam, crop, cores)
+        times.append(secs)
+    ms = 1e3 * sum(times) / len(times)
+    value = px / (ms * 1e-3) / 1e6
+    sample = (f"FP64 oracle, render + backward of the 4 models on the centred {crop}x{crop} crop of the view "
+              f"(each step re-projects all {args.gaussians} Gaussians)")
+    line = {"metric": METRIC, "value": round(value, 5), "unit": "Mpix/s", "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "gaussians": args.gaussians, "width": args.width, "height": args.height,
+                       "sh_degree": 3, "crop": crop},
+            "cpu_baseline": {"value": round(value, 5), "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * ngs.h -- C ABI of the GB300 (sm_103a) library for generalized non-exponential Gaussian splatting.
+ *
+ * The library renders a set of 3D Gaussians through a pinhole camera by front-to-back compositing of
+ * depth-sorted splats under a mother transmittance T(tau) (Sec. 4.2, Eq. generalized_gaussian and
+ * Eq. nexp_p; the per-model slope terms of Table 1), stopping each ray once its transmittance
+ * saturates, and differentiates the result by path replay (Sec. 5.1 "Optimization"; App. C).
+ *
+ * Conventions shared by every call:
+ *  - All array arguments are DEVICE pointers owned by the caller (for example PyTorch tensors), FP32
+ *    unless stated, densely packed, row-major. The library never frees them.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default stream. Every kernel of a
+ *    call is launched on that stream; a call returns before its kernels finish, except where a call
+ *    documents one host synchronisation.
+ *  - Return value: NGS_OK (0) or a negative NGS_ERR_* status. On error nothing is launched that would
+ *    write caller memory after the return, and ngs_last_error() holds a one-line message. No C++
+ *    exception crosses this boundary.
+ *  - A context (ngs_ctx) is not thread-safe: use one per host thread / stream. A frame (ngs_frame)
+ *    belongs to the context that created it.
+ */
+#ifndef NGS_H
+#define NGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define NGS_API __attribute__((visibility("default")))
+#else
+#define NGS_API
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------------- */
+#define NGS_OK 0
+#define NGS_ERR_INVALID_ARG (-1)   /* a pointer, size or option is out of its documented range      */
+#define NGS_ERR_OUT_OF_MEMORY (-2) /* device allocation of internal buffers failed                  */
+#define NGS_ERR_CUDA (-3)          /* a CUDA runtime call failed (message in ngs_last_error)       */
+#define NGS_ERR_DEVICE_CHECK (-5)  /* a kernel's own bounds check fired; its output is not valid   */
+
+/* ---- transmittance models (Table 1) ----------------------------------------------------------- */
+#define NGS_MODEL_EXP 0  /* T = exp(-tau): pbar_i = alpha_i prod_{j<i}(1 - alpha_j) (standard 3DGS)      */
+#define NGS_MODEL_QUAD 1 /* T = [1 - tau - c/2 tau^2]_+: pbar_i = alpha_i (1 + c taubar_i); param = c,    */
+                         /* c >= -1/2. c = -1/2 sub-linear, c = 0 linear, c = +1/2 super-linear (Sec. 5)  */
+
+typedef struct ngs_ctx ngs_ctx;
+typedef struct ngs_frame ngs_frame;
+
+/* Gaussian parameters (Sec. 3: centre c_i, covariance Sigma_i, opacity aleph_i, emission E_i(omega)).
+ * Raw parametrisation: Sigma_i = R(q) diag(exp(2 s)) R(q)^T with q = quats[i] normalised inside the
+ * library (w, x, y, z order), aleph_i = sigmoid(opacity_logits[i]),
+ * E_i = max(0, 1/2 + sum_lm Y_lm(d) sh[i][lm]) per colour channel, Y_lm the real spherical harmonics of
+ * degree <= sh_degree in the coefficient order of 3D Gaussian splatting assets, d the unit direction
+ * from the camera centre to the mean. */
+typedef struct {
+  int64_t n;                   /* number of Gaussians, 0 <= n < 2^31                                  */
+  int32_t sh_degree;           /* 0..3                                                              */
+  const float* means;          /* [n][3] world position                                             */
+  const float* log_scales;     /* [n][3] s                                                          */
+  const float* quats;          /* [n][4] (w, x, y, z), nonzero norm                                 */
+  const float* opacity_logits; /* [n]                                                               */
+  const float* sh;             /* [n][(sh_degree + 1)^2][3]                                         */
+} ngs_gaussians;
+
+/* Pinhole camera looking down +z of its view frame. Pixel (x, y) samples the image point
+ * (x + 1/2, y + 1/2); a view-space point (X, Y, Z) maps to (fx X / Z + cx, fy Y / Z + cy). */
+typedef struct {
+  float viewmat[12]; /* world -> view, row-major [R | t] (3 x 4); R must be a rotation                */
+  float fx, fy, cx, cy;
+  int32_t width, height; /* 1 .. 16384                                                              */
+} ngs_camera;
+
+typedef struct {
+  int32_t kind; /* NGS_MODEL_EXP or NGS_MODEL_QUAD                                                    */
+  float param;  /* c for NGS_MODEL_QUAD (>= -0.5); ignored for NGS_MODEL_EXP                          */
+} ngs_model;
+
+/* Rendering options. ngs_default_options() fills the values below, which are the conventions of the
+ * 3D Gaussian splatting baseline the paper builds on (the paper itself states none of them). */
+typedef struct {
+  float alpha_min;     /* 1/255: a splat with alpha_i(p) < alpha_min is skipped at pixel p           */
+  float alpha_max;     /* 0.99: alpha_i(p) = min(alpha_max, aleph_i K_i(p))                          */
+  float t_eps;         /* 1e-4: exponential model only, stop before T would fall below t_eps         */
+  float dilation;      /* 0.3: added to the 2D covariance's diagonal, in pixel^2                     */
+  float near_plane;    /* 0.2: Gaussians with FP32 view depth <= near_plane are culled               */
+  float background[3]; /* L_b of Eq. generalized_gaussian; default black                             */
+  int32_t tile_w, tile_h; /* screen tile: 8x8, 16x16 (default) or 16x32; the image does not depend on it */
+  int32_t max_splats;  /* 0 = unlimited, else at most this many splats composited per pixel (the    */
+                       /* paper's ray tracer caps at 128, Sec. 5.1 "Renderer")                       */
+  int32_t reserved;    /* must be 0                                                                  */
+} ngs_options;
+
+/* Gradient outputs of ngs_render_backward, same shapes as ngs_gaussians' arrays. OVERWRITTEN. */
+typedef struct {
+  float* d_means;
+  float* d_log_scales;
+  float* d_quats;
+  float* d_opacity_logits;
+  float* d_sh;
+} ngs_grads;
+
+/* Read-only view of a frame's device buffers (valid until the frame's next render or destruction). */
+typedef struct {
+  int64_t n_gaussians;
+  int64_t n_pairs;          /* number of (tile, Gaussian) pairs after binning                         */
+  int32_t tiles_x, tiles_y;
+  int32_t width, height;
+  const float* records;     /* [n][12] splat records: u, v, conic*k (3), log2 aleph, E (3), z, r, 0  */
+                            /*   with k = -log2(e)/2 folded into the conic                           */
+  const uint64_t* keys;     /* [n_pairs] sorted keys (tile << 32) | bits(z)                           */
+  const uint32_t* values;   /* [n_pairs] Gaussian index of each key                                   */
+  const uint32_t* ranges;   /* [tiles][2] [start, end) of each tile's pairs                           */
+  const float* pixel_state; /* [height][width][8] replay state written by the forward pass            */
+} ngs_frame_view;
+
+/* Fill `out` with the default options above. */
+NGS_API void ngs_default_options(ngs_options* out);
+
+/* Create a context on the current CUDA device. *out receives the handle. Returns NGS_ERR_CUDA if no
+ * device is usable. */
+NGS_API int ngs_create(ngs_ctx** out);
+
+/* Destroy a context (frees its scratch memory after synchronising the device). NULL is allowed. */
+NGS_API void ngs_destroy(ngs_ctx* ctx);
+
+/* One-line description of the last error on this context ("" if none). Owned by the context. */
+NGS_API const char* ngs_last_error(const ngs_ctx* ctx);
+
+/* A frame holds everything one render leaves for its backward pass: splat records, sorted
+ * (tile, Gaussian) pairs, tile ranges and the per-pixel replay state (the paper's path replay passes
+ * E_k from the forward to the adjoint pass, App. C.1). Its buffers are allocated and grown by the
+ * library on first use and reused by later renders into the same frame. */
+NGS_API int ngs_frame_create(ngs_ctx* ctx, ngs_frame** out);
+NGS_API void ngs_frame_destroy(ngs_frame* frame);
+
+/* Render (Eq. generalized_gaussian with pbar_i from Eq. nexp_p):
+ *   image[y][x][3] = sum_i E_i pbar_i + L_b Tbar_end over the splats i of pixel (x, y), front to back by
+ *   (FP32 view depth, Gaussian index); overdraw[y][x] = number of splats composited at that pixel,
+ *   the saturating one included (Fig. 2 "Overdraws"; Table 3 "Avg. OD").
+ * `image` is [height][width][3] FP32 and `overdraw` [height][width] int32, both caller-owned device
+ * memory; overdraw may be NULL. The frame is overwritten. One host synchronisation happens after
+ * binning, to read the number of (tile, Gaussian) pairs and size the sort buffers.
+ * Errors: NGS_ERR_INVALID_ARG for NULL pointers, n < 0, sh_degree outside 0..3, width/height outside
+ * 1..16384, an unsupported tile shape, kind/param outside the table above, nonzero `reserved`. */
+NGS_API int ngs_render(ngs_ctx* ctx, ngs_frame* frame, const ngs_gaussians* g, const ngs_camera* cam,
+                       const ngs_model* model, const ngs_options* opt, float* image, int32_t* overdraw,
+                       void* stream);
+
+/* Path-replay backward of the frame's last render (App. C: recursive adjoints computed front to back by
+ * replaying each pixel's splat list, recomputing alpha_i and taubar_i instead of storing per-splat state).
+ * dl_dimage: [height][width][3] FP32 device array (dL/dL0 per pixel). `g` must hold the same parameter
+ * values the frame was rendered from. Gradients w.r.t. the raw parameters are written (not accumulated)
+ * into `out`; Gaussians that were culled get zeros. Errors: NGS_ERR_INVALID_ARG if the frame holds no
+ * render or `g` does not match its size. */
+NGS_API int ngs_render_backward(ngs_ctx* ctx, const ngs_frame* frame, const ngs_gaussians* g,
+                                const float* dl_dimage, const ngs_grads* out, void* stream);
+
+/* Fill `out` with device pointers into the frame (for tests and diagnostics). */
+NGS_API int ngs_frame_view_get(const ngs_frame* frame, ngs_frame_view* out);
+
+/* Stage timing. When enabled, every render/backward records CUDA events on its stream around each
+ * stage and ngs_stage_times() adds up the elapsed time per stage (synchronising on the recorded
+ * events). Stages: 0 project, 1 depth sort, 2 scan + key emit, 3 tile sort, 4 tile ranges,
+ * 5 composite forward, 6 composite backward (replay), 7 projection backward. `ms` and `launches` have
+ * room for `n` entries; returns the number of stages. ngs_reset_stage_times() clears the sums. */
+#define NGS_NUM_STAGES 8
+NGS_API int ngs_set_timing(ngs_ctx* ctx, int enable);
+NGS_API int ngs_stage_times(ngs_ctx* ctx, double* ms, int64_t* launches, int32_t n);
+NGS_API void ngs_reset_stage_times(ngs_ctx* ctx);
+
+/* Total number of kernel launches this context has issued (all stages). */
+NGS_API int64_t ngs_launch_count(const ngs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NGS_H */

@@ -81,7 +81,8 @@ class _Fwd(C.Structure):
 class _Bwd(C.Structure):
     _fields_ = [("dl_dimage", C.c_void_p), ("d_means", C.c_void_p), ("d_log_scales", C.c_void_p),
                 ("d_quats", C.c_void_p), ("d_opacity_logits", C.c_void_p), ("d_sh", C.c_void_p),
-                ("fragile_gauss", C.c_void_p)]
+                ("fragile_gauss", C.c_void_p), ("s_means", C.c_void_p), ("s_log_scales", C.c_void_p),
+                ("s_quats", C.c_void_p), ("s_opacity_logits", C.c_void_p), ("s_sh", C.c_void_p)]
 
 
 def _load():
@@ -212,7 +213,8 @@ def render(scene, camera, model, opts=None, window=None, nthreads=1, brute_force
 
     Returns dict(image[h, w, 3], overdraw[h, w], n_listed[h, w], fragile[h, w], signature[h, w]) and, when
     ``dl_dimage`` [h, w, 3] is given, the gradients d_means, d_log_scales, d_quats, d_opacity_logits, d_sh
-    (same shapes as the parameters) and fragile_gauss[n].
+    (same shapes as the parameters), fragile_gauss[n] and, per gradient, its error scale s_* (the sum of
+    the absolute per-pixel terms chained through the absolute Jacobian).
     """
     lib = _load()
     keep = []
@@ -235,8 +237,11 @@ def render(scene, camera, model, opts=None, window=None, nthreads=1, brute_force
         grads = dict(d_means=np.zeros((n, 3)), d_log_scales=np.zeros((n, 3)), d_quats=np.zeros((n, 4)),
                      d_opacity_logits=np.zeros(n), d_sh=np.zeros((n, K, 3)))
         fg = np.zeros(n, dtype=np.uint8)
-        bwd = _Bwd(_ptr(dl), *(_ptr(grads[k]) for k in ("d_means", "d_log_scales", "d_quats", "d_opacity_logits",
-                                                        "d_sh")), _ptr(fg))
+        names = ("means", "log_scales", "quats", "opacity_logits", "sh")
+        scales = {"s_" + k: np.zeros_like(grads["d_" + k]) for k in names}
+        grads.update(scales)
+        bwd = _Bwd(_ptr(dl), *(_ptr(grads["d_" + k]) for k in names), _ptr(fg),
+                   *(_ptr(scales["s_" + k]) for k in names))
         bwd_p = C.byref(bwd)
         keep.append(dl)
     lib.orc_render(C.byref(sc), C.byref(cam), C.byref(m_), C.byref(o), C.byref(win), int(nthreads),

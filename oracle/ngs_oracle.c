@@ -100,6 +100,14 @@ typedef struct {
   double* d_opacity_logits;/* [n] */
   double* d_sh;            /* [n][(d+1)^2][3] */
   uint8_t* fragile_gauss;  /* [n] a colour channel sits within fragile_rel of the max(0,.) clamp (may be NULL) */
+  /* Optional [n]-shaped outputs like the gradients: the sum of the absolute values of every per-pixel term
+   * chained through the absolute Jacobian. It is the scale of the rounding error an FP32 accumulation of
+   * the same terms can make, whatever their cancellation; tests use it to bound that error. */
+  double* s_means;
+  double* s_log_scales;
+  double* s_quats;
+  double* s_opacity_logits;
+  double* s_sh;
 } orc_bwd;
 
 /* ------------------------------------------------------------------------------------------------
@@ -491,7 +499,7 @@ static void* render_rows(void* argp) {
   const orc_window* w = J->win;
   int kind = J->model->kind;
   double par = J->model->param;
-  double* grec = J->grad_rec ? J->grad_rec + (size_t)wa->tid * (size_t)J->nloc * 9 : NULL;
+  double* grec = J->grad_rec ? J->grad_rec + (size_t)wa->tid * (size_t)J->nloc * 18 : NULL;
   int cap = 0;
   double *alpha = NULL, *E = NULL, *pbar = NULL, *dal = NULL, *dE = NULL;
   for (int yy = wa->tid; yy < w->h; yy += J->nthreads) {
@@ -534,8 +542,12 @@ static void* render_rows(void* argp) {
         double px = J->win->x0 + xx + 0.5, py = J->win->y0 + yy + 0.5;
         for (int i = 0; i < r.m; ++i) {
           const splat_d* s = &J->sp[L[i].g];
-          double* gr = grec + (size_t)L[i].g * 9;
-          for (int ch = 0; ch < 3; ++ch) gr[6 + ch] += dE[3 * i + ch];
+          double* gr = grec + (size_t)L[i].g * 18;
+          double* ga = gr + 9; /* absolute values of the same terms */
+          for (int ch = 0; ch < 3; ++ch) {
+            gr[6 + ch] += dE[3 * i + ch];
+            ga[6 + ch] += fabs(dE[3 * i + ch]);
+          }
           if (L[i].clamped == 1) continue; /* alpha = alpha_max does not depend on the splat */
           /* alpha = aleph exp(-q/2), q = A dx^2 + 2 B dx dy + C dy^2, (dx, dy) = p - (u, v) */
           double dx = px - s->rec[0], dy = py - s->rec[1];
@@ -544,12 +556,12 @@ static void* render_rows(void* argp) {
           double G = exp(-0.5 * q);
           double a = L[i].alpha;
           double dq = dal[i] * (-0.5 * a);
-          gr[0] += dq * (-2.0 * (A * dx + B * dy));
-          gr[1] += dq * (-2.0 * (B * dx + C * dy));
-          gr[2] += dq * dx * dx;
-          gr[3] += dq * 2.0 * dx * dy;
-          gr[4] += dq * dy * dy;
-          gr[5] += dal[i] * G;
+          double t[6] = {dq * (-2.0 * (A * dx + B * dy)), dq * (-2.0 * (B * dx + C * dy)), dq * dx * dx,
+                         dq * 2.0 * dx * dy, dq * dy * dy, dal[i] * G};
+          for (int r = 0; r < 6; ++r) {
+            gr[r] += t[r];
+            ga[r] += fabs(t[r]);
+          }
         }
       }
     }
@@ -560,7 +572,7 @@ static void* render_rows(void* argp) {
 
 /* Complex-step chain from record gradients to raw-parameter gradients for one Gaussian. */
 static void chain_to_params(const orc_scene* sc, const orc_camera* cam, const orc_opts* o, int64_t g,
-                            const double* grec, orc_bwd* b) {
+                            const double* grec, const double* gabs, orc_bwd* b) {
   int K = sh_count(sc->sh_degree);
   int np = 3 + 3 + 4 + 1 + 3 * K;
   double h = 1e-30;
@@ -572,15 +584,33 @@ static void chain_to_params(const orc_scene* sc, const orc_camera* cam, const or
     for (int t = 0; t < 3 * K; ++t) sh[t] = sc->sh[(int64_t)3 * K * g + t];
     logit = sc->opacity_logits[g];
     double* dst;
-    if (j < 3) { p[j] += I * h; dst = &b->d_means[3 * g + j]; }
-    else if (j < 6) { s[j - 3] += I * h; dst = &b->d_log_scales[3 * g + j - 3]; }
-    else if (j < 10) { q[j - 6] += I * h; dst = &b->d_quats[4 * g + j - 6]; }
-    else if (j == 10) { logit += I * h; dst = &b->d_opacity_logits[g]; }
-    else { sh[j - 11] += I * h; dst = &b->d_sh[(int64_t)3 * K * g + j - 11]; }
+    double* sdst;
+    if (j < 3) { p[j] += I * h; dst = &b->d_means[3 * g + j]; sdst = b->s_means ? &b->s_means[3 * g + j] : NULL; }
+    else if (j < 6) {
+      s[j - 3] += I * h;
+      dst = &b->d_log_scales[3 * g + j - 3];
+      sdst = b->s_log_scales ? &b->s_log_scales[3 * g + j - 3] : NULL;
+    } else if (j < 10) {
+      q[j - 6] += I * h;
+      dst = &b->d_quats[4 * g + j - 6];
+      sdst = b->s_quats ? &b->s_quats[4 * g + j - 6] : NULL;
+    } else if (j == 10) {
+      logit += I * h;
+      dst = &b->d_opacity_logits[g];
+      sdst = b->s_opacity_logits ? &b->s_opacity_logits[g] : NULL;
+    } else {
+      sh[j - 11] += I * h;
+      dst = &b->d_sh[(int64_t)3 * K * g + j - 11];
+      sdst = b->s_sh ? &b->s_sh[(int64_t)3 * K * g + j - 11] : NULL;
+    }
     if (!project_c(cam, o->dilation, K, p, s, q, logit, sh, rec, &lam, er)) continue;
-    double acc = 0;
-    for (int r = 0; r < 9; ++r) acc += grec[r] * cimag(rec[r]) / h;
+    double acc = 0, sacc = 0;
+    for (int r = 0; r < 9; ++r) {
+      acc += grec[r] * cimag(rec[r]) / h;
+      if (gabs) sacc += gabs[r] * fabs(cimag(rec[r]) / h);
+    }
     *dst = acc;
+    if (sdst) *sdst = sacc;
   }
 }
 
@@ -608,11 +638,12 @@ int orc_project_jacobian(const orc_scene* sc, const orc_camera* cam, const orc_o
   double* dq = (double*)calloc((size_t)sc->n * 4, sizeof(double));
   double* dl = (double*)calloc((size_t)sc->n, sizeof(double));
   double* dh = (double*)calloc((size_t)sc->n * 3 * K, sizeof(double));
+  memset(&b, 0, sizeof(b));
   b.d_means = dm; b.d_log_scales = ds; b.d_quats = dq; b.d_opacity_logits = dl; b.d_sh = dh;
   for (int r = 0; r < 9; ++r) {
     double e[9] = {0};
     e[r] = 1.0;
-    chain_to_params(sc, cam, o, g, e, &b);
+    chain_to_params(sc, cam, o, g, e, NULL, &b);
     double* row = jac + (size_t)r * np;
     for (int t = 0; t < 3; ++t) row[t] = dm[3 * g + t];
     for (int t = 0; t < 3; ++t) row[3 + t] = ds[3 * g + t];
@@ -701,7 +732,7 @@ int orc_render(const orc_scene* sc, const orc_camera* cam, const orc_model* mode
   job.sc = sc; job.cam = cam; job.model = model; job.o = o; job.win = win;
   job.sp = all; job.gid = gid; job.nloc = nloc; job.start = start; job.ent = ent;
   job.px_fragile = pxf; job.fwd = fwd; job.bwd = bwd; job.nthreads = nthreads;
-  if (bwd) job.grad_rec = (double*)calloc((size_t)nthreads * (size_t)nloc * 9 + 1, sizeof(double));
+  if (bwd) job.grad_rec = (double*)calloc((size_t)nthreads * (size_t)nloc * 18 + 1, sizeof(double));
   pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * nthreads);
   worker_arg* wa = (worker_arg*)malloc(sizeof(worker_arg) * nthreads);
   for (int t = 0; t < nthreads; ++t) {
@@ -719,14 +750,18 @@ int orc_render(const orc_scene* sc, const orc_camera* cam, const orc_model* mode
     memset(bwd->d_opacity_logits, 0, sizeof(double) * (size_t)n);
     memset(bwd->d_sh, 0, sizeof(double) * 3 * (size_t)K * (size_t)n);
     if (bwd->fragile_gauss) memset(bwd->fragile_gauss, 0, (size_t)n);
+    double* sarr[5] = {bwd->s_means, bwd->s_log_scales, bwd->s_quats, bwd->s_opacity_logits, bwd->s_sh};
+    size_t swid[5] = {3, 3, 4, 1, 3 * (size_t)K};
+    for (int k = 0; k < 5; ++k)
+      if (sarr[k]) memset(sarr[k], 0, sizeof(double) * swid[k] * (size_t)n);
     for (int64_t l = 0; l < nloc; ++l) {
-      double gr[9] = {0};
+      double gr[18] = {0};
       for (int t = 0; t < nthreads; ++t)
-        for (int r = 0; r < 9; ++r) gr[r] += job.grad_rec[((size_t)t * nloc + l) * 9 + r];
+        for (int r = 0; r < 18; ++r) gr[r] += job.grad_rec[((size_t)t * nloc + l) * 18 + r];
       int nz = 0;
-      for (int r = 0; r < 9; ++r) nz |= gr[r] != 0;
+      for (int r = 0; r < 18; ++r) nz |= gr[r] != 0;
       if (!nz) continue;
-      chain_to_params(sc, cam, o, gid[l], gr, bwd);
+      chain_to_params(sc, cam, o, gid[l], gr, gr + 9, bwd);
       if (bwd->fragile_gauss)
         for (int ch = 0; ch < 3; ++ch)
           if (fabs(all[l].e_real[ch]) < o->fragile_rel) bwd->fragile_gauss[gid[l]] = 1;

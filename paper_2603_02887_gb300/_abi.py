@@ -1,0 +1,104 @@
+"""ctypes mirror of include/ngs.h (argument marshalling only).
+
+Loading fails loudly when the CUDA library has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+NGS_OK = 0
+NGS_ERR_INVALID_ARG = -1
+NGS_ERR_OUT_OF_MEMORY = -2
+NGS_ERR_CUDA = -3
+NGS_ERR_DEVICE_CHECK = -5
+NGS_MODEL_EXP = 0
+NGS_MODEL_QUAD = 1
+NGS_NUM_STAGES = 8
+STAGES = ("project", "depth_sort", "scan_emit", "tile_sort", "tile_ranges", "composite_fwd", "composite_bwd",
+          "project_bwd")
+
+
+class Gaussians(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("means", C.c_void_p), ("log_scales", C.c_void_p),
+                ("quats", C.c_void_p), ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("viewmat", C.c_float * 12), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float),
+                ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class Model(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("param", C.c_float)]
+
+
+class Options(C.Structure):
+    _fields_ = [("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_eps", C.c_float), ("dilation", C.c_float),
+                ("near_plane", C.c_float), ("background", C.c_float * 3), ("tile_w", C.c_int32),
+                ("tile_h", C.c_int32), ("max_splats", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Grads(C.Structure):
+    _fields_ = [("d_means", C.c_void_p), ("d_log_scales", C.c_void_p), ("d_quats", C.c_void_p),
+                ("d_opacity_logits", C.c_void_p), ("d_sh", C.c_void_p)]
+
+
+class FrameView(C.Structure):
+    _fields_ = [("n_gaussians", C.c_int64), ("n_pairs", C.c_int64), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32),
+                ("width", C.c_int32), ("height", C.c_int32), ("records", C.c_void_p), ("keys", C.c_void_p),
+                ("values", C.c_void_p), ("ranges", C.c_void_p), ("pixel_state", C.c_void_p)]
+
+
+#: every function declared in include/ngs.h, with its ctypes signature
+SIGNATURES = {
+    "ngs_default_options": (None, [C.POINTER(Options)]),
+    "ngs_create": (C.c_int, [C.POINTER(C.c_void_p)]),
+    "ngs_destroy": (None, [C.c_void_p]),
+    "ngs_last_error": (C.c_char_p, [C.c_void_p]),
+    "ngs_frame_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "ngs_frame_destroy": (None, [C.c_void_p]),
+    "ngs_render": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.POINTER(Camera), C.POINTER(Model),
+                             C.POINTER(Options), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ngs_render_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.c_void_p, C.POINTER(Grads),
+                                      C.c_void_p]),
+    "ngs_frame_view_get": (C.c_int, [C.c_void_p, C.POINTER(FrameView)]),
+    "ngs_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "ngs_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
+    "ngs_reset_stage_times": (None, [C.c_void_p]),
+    "ngs_launch_count": (C.c_int64, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load the built library (raises if it is missing: call paper_2603_02887_gb300.build.build())."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built ({path} missing); run paper_2603_02887_gb300.build.build()")
+        lib = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class NGSError(RuntimeError):
+    pass
+
+
+def check(rc: int, ctx) -> None:
+    if rc != NGS_OK:
+        msg = load().ngs_last_error(ctx)
+        raise NGSError(f"ngs error {rc}: {msg.decode() if msg else ''}")

@@ -1,0 +1,405 @@
+// C ABI of the ngs library: contexts, frames, argument checks, buffer management and the render /
+// backward pipelines (projection -> depth sort -> scan + key emission -> tile sort -> tile ranges ->
+// composite; composite replay -> projection backward).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "ngs_internal.cuh"
+
+namespace ngs {
+
+int fail(ngs_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int ensure(ngs_ctx* ctx, DevBuf& b, size_t bytes) {
+  if (bytes <= b.cap && b.p) return NGS_OK;
+  size_t nb = std::max(bytes, b.cap + b.cap / 4);
+  nb = (std::max<size_t>(nb, 256) + 255) & ~(size_t)255;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  cudaError_t e = cudaMalloc(&b.p, nb);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    char msg[160];
+    snprintf(msg, sizeof msg, "device allocation of %zu bytes failed: %s", nb, cudaGetErrorString(e));
+    return fail(ctx, NGS_ERR_OUT_OF_MEMORY, msg);
+  }
+  b.cap = nb;
+  return NGS_OK;
+}
+
+static cudaEvent_t take_event(ngs_ctx* ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void stage_begin(ngs_ctx* ctx, cudaStream_t s, int, cudaEvent_t* out) {
+  *out = nullptr;
+  if (!ctx->timing) return;
+  *out = take_event(ctx);
+  cudaEventRecord(*out, s);
+}
+
+void stage_end(ngs_ctx* ctx, cudaStream_t s, int stage, cudaEvent_t start, int launches) {
+  ctx->launches += launches;
+  ctx->stage_launches[stage] += launches;
+  if (!ctx->timing || !start) return;
+  cudaEvent_t b = take_event(ctx);
+  cudaEventRecord(b, s);
+  ctx->pending.push_back({start, b, stage});
+}
+
+static void free_buf(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+static int check_launch(ngs_ctx* ctx, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    char msg[200];
+    snprintf(msg, sizeof msg, "%s: %s", what, cudaGetErrorString(e));
+    return fail(ctx, NGS_ERR_CUDA, msg);
+  }
+  return NGS_OK;
+}
+
+static int tile_bits(uint32_t ntiles) {
+  int b = 0;
+  while (b < 32 && (1ull << b) < ntiles) ++b;
+  return b;
+}
+
+}  // namespace ngs
+
+using namespace ngs;
+
+#define NGS_TRY(x)             \
+  do {                         \
+    int _rc = (x);             \
+    if (_rc != NGS_OK) return _rc; \
+  } while (0)
+
+extern "C" {
+
+NGS_API void ngs_default_options(ngs_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->alpha_min = 1.0f / 255.0f;
+  o->alpha_max = 0.99f;
+  o->t_eps = 1e-4f;
+  o->dilation = 0.3f;
+  o->near_plane = 0.2f;
+  o->tile_w = 16;
+  o->tile_h = 16;
+  o->max_splats = 0;
+}
+
+NGS_API int ngs_create(ngs_ctx** out) {
+  if (!out) return NGS_ERR_INVALID_ARG;
+  *out = nullptr;
+  ngs_ctx* ctx = new (std::nothrow) ngs_ctx();
+  if (!ctx) return NGS_ERR_OUT_OF_MEMORY;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_total, sizeof(uint64_t));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return NGS_ERR_CUDA;
+  }
+  *out = ctx;
+  return NGS_OK;
+}
+
+NGS_API void ngs_destroy(ngs_ctx* ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  free_buf(ctx->hist);
+  free_buf(ctx->scan_tmp);
+  free_buf(ctx->grad2d);
+  free_buf(ctx->total);
+  if (ctx->h_total) cudaFreeHost(ctx->h_total);
+  for (auto& p : ctx->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : ctx->event_pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+NGS_API const char* ngs_last_error(const ngs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+NGS_API int ngs_frame_create(ngs_ctx* ctx, ngs_frame** out) {
+  if (!ctx || !out) return NGS_ERR_INVALID_ARG;
+  ngs_frame* f = new (std::nothrow) ngs_frame();
+  if (!f) return fail(ctx, NGS_ERR_OUT_OF_MEMORY, "host allocation of a frame failed");
+  f->ctx = ctx;
+  *out = f;
+  return NGS_OK;
+}
+
+NGS_API void ngs_frame_destroy(ngs_frame* f) {
+  if (!f) return;
+  cudaDeviceSynchronize();
+  DevBuf* bufs[] = {&f->rec, &f->tile_count, &f->gkeys[0], &f->gkeys[1], &f->gvals[0], &f->gvals[1],
+                    &f->offsets, &f->pkeys[0], &f->pkeys[1], &f->pvals[0], &f->pvals[1], &f->ranges, &f->state};
+  for (DevBuf* b : bufs) free_buf(*b);
+  delete f;
+}
+
+static int check_inputs(ngs_ctx* ctx, const ngs_gaussians* g, const ngs_camera* cam, const ngs_model* model,
+                        const ngs_options* o) {
+  if (!g || !cam || !model || !o) return fail(ctx, NGS_ERR_INVALID_ARG, "null argument");
+  if (g->n < 0 || g->n >= (1ll << 31)) return fail(ctx, NGS_ERR_INVALID_ARG, "n out of range [0, 2^31)");
+  if (g->sh_degree < 0 || g->sh_degree > 3) return fail(ctx, NGS_ERR_INVALID_ARG, "sh_degree must be 0..3");
+  if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+    return fail(ctx, NGS_ERR_INVALID_ARG, "null Gaussian parameter array");
+  if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
+    return fail(ctx, NGS_ERR_INVALID_ARG, "image size out of range 1..16384");
+  if (!(cam->fx > 0) || !(cam->fy > 0) || !isfinite(cam->cx) || !isfinite(cam->cy))
+    return fail(ctx, NGS_ERR_INVALID_ARG, "invalid intrinsics");
+  for (int i = 0; i < 12; ++i)
+    if (!isfinite(cam->viewmat[i])) return fail(ctx, NGS_ERR_INVALID_ARG, "non-finite view matrix");
+  if (model->kind == NGS_MODEL_QUAD) {
+    if (!(model->param >= -0.5f) || !isfinite(model->param))
+      return fail(ctx, NGS_ERR_INVALID_ARG, "quadratic model needs c >= -0.5");
+  } else if (model->kind != NGS_MODEL_EXP) {
+    return fail(ctx, NGS_ERR_INVALID_ARG, "unknown transmittance model");
+  }
+  bool tile_ok = (o->tile_w == 8 && o->tile_h == 8) || (o->tile_w == 16 && o->tile_h == 16) ||
+                 (o->tile_w == 16 && o->tile_h == 32);
+  if (!tile_ok) return fail(ctx, NGS_ERR_INVALID_ARG, "tile shape must be 8x8, 16x16 or 16x32");
+  if (!(o->alpha_min > 0.f && o->alpha_min < 1.f) || !(o->alpha_max > o->alpha_min && o->alpha_max <= 1.f))
+    return fail(ctx, NGS_ERR_INVALID_ARG, "need 0 < alpha_min < alpha_max <= 1");
+  if (!(o->t_eps >= 0.f && o->t_eps < 1.f) || !(o->dilation >= 0.f) || !(o->near_plane > 0.f) ||
+      o->max_splats < 0 || o->reserved != 0)
+    return fail(ctx, NGS_ERR_INVALID_ARG, "invalid option value");
+  for (int i = 0; i < 3; ++i)
+    if (!isfinite(o->background[i])) return fail(ctx, NGS_ERR_INVALID_ARG, "non-finite background");
+  return NGS_OK;
+}
+
+NGS_API int ngs_render(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const ngs_camera* cam,
+                       const ngs_model* model, const ngs_options* o, float* image, int32_t* overdraw, void* stream) {
+  if (!ctx) return NGS_ERR_INVALID_ARG;
+  if (!f || f->ctx != ctx) return fail(ctx, NGS_ERR_INVALID_ARG, "frame missing or from another context");
+  NGS_TRY(check_inputs(ctx, g, cam, model, o));
+  if (!image) return fail(ctx, NGS_ERR_INVALID_ARG, "null image");
+  cudaStream_t s = (cudaStream_t)stream;
+  f->has_render = false;
+
+  CamParams cp;
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) cp.R[3 * r + c] = cam->viewmat[4 * r + c];
+    cp.t[r] = cam->viewmat[4 * r + 3];
+  }
+  for (int c = 0; c < 3; ++c)
+    cp.campos[c] = -(cp.R[c] * cp.t[0] + cp.R[3 + c] * cp.t[1] + cp.R[6 + c] * cp.t[2]);
+  cp.fx = cam->fx;
+  cp.fy = cam->fy;
+  cp.cx = cam->cx;
+  cp.cy = cam->cy;
+  cp.W = cam->width;
+  cp.H = cam->height;
+  RenderParams rp;
+  rp.alpha_min = o->alpha_min;
+  rp.alpha_max = o->alpha_max;
+  rp.t_eps = o->t_eps;
+  rp.dilation = o->dilation;
+  rp.near_plane = o->near_plane;
+  rp.log2_alpha_min = log2f(o->alpha_min);
+  for (int c = 0; c < 3; ++c) rp.bg[c] = o->background[c];
+  rp.c = model->kind == NGS_MODEL_QUAD ? model->param : 0.f;
+  rp.kind = model->kind;
+  rp.tile_w = o->tile_w;
+  rp.tile_h = o->tile_h;
+  rp.tiles_x = (cam->width + o->tile_w - 1) / o->tile_w;
+  rp.tiles_y = (cam->height + o->tile_h - 1) / o->tile_h;
+  rp.max_splats = o->max_splats;
+  rp.sh_degree = g->sh_degree;
+  uint32_t n = (uint32_t)g->n;
+  uint32_t ntiles = (uint32_t)rp.tiles_x * (uint32_t)rp.tiles_y;
+  size_t npix = (size_t)cam->width * cam->height;
+
+  NGS_TRY(ensure(ctx, f->rec, sizeof(float4) * 3 * (size_t)std::max(n, 1u)));
+  NGS_TRY(ensure(ctx, f->tile_count, sizeof(uint32_t) * (size_t)std::max(n, 1u)));
+  for (int k = 0; k < 2; ++k) {
+    NGS_TRY(ensure(ctx, f->gkeys[k], sizeof(uint32_t) * (size_t)std::max(n, 1u)));
+    NGS_TRY(ensure(ctx, f->gvals[k], sizeof(uint32_t) * (size_t)std::max(n, 1u)));
+  }
+  NGS_TRY(ensure(ctx, f->offsets, sizeof(uint32_t) * ((size_t)n + 1)));
+  NGS_TRY(ensure(ctx, f->ranges, sizeof(uint2) * (size_t)ntiles));
+  NGS_TRY(ensure(ctx, f->state, sizeof(float4) * 2 * npix));
+  NGS_TRY(ensure(ctx, ctx->scan_tmp, sizeof(uint64_t) * scan_tmp_words(n)));
+  NGS_TRY(ensure(ctx, ctx->total, sizeof(uint64_t)));
+  NGS_TRY(ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(std::max(n, 1u))));
+
+  cudaEvent_t ev;
+  // 1. projection: splat records, FP32 depth keys (all-ones for splats that take no tile), tile counts
+  stage_begin(ctx, s, 0, &ev);
+  launch_project(*g, cp, rp, f->rec.as<float4>(), f->gkeys[0].as<uint32_t>(), f->tile_count.as<uint32_t>(),
+                 f->gvals[0].as<uint32_t>(), s);
+  stage_end(ctx, s, 0, ev, n ? 1 : 0);
+  NGS_TRY(check_launch(ctx, "project"));
+  // 2. stable sort of the Gaussians by FP32 depth (ties keep index order)
+  stage_begin(ctx, s, 1, &ev);
+  int launches = 0;
+  {
+    uint32_t* k2[2] = {f->gkeys[0].as<uint32_t>(), f->gkeys[1].as<uint32_t>()};
+    uint32_t* v2[2] = {f->gvals[0].as<uint32_t>(), f->gvals[1].as<uint32_t>()};
+    f->g_final = radix_sort_u32(k2, v2, n, 0, 32, ctx->hist.as<uint32_t>(), ctx->hist.cap / 4, s, &launches);
+  }
+  stage_end(ctx, s, 1, ev, launches);
+  NGS_TRY(check_launch(ctx, "depth sort"));
+  // 3. exclusive scan of the tile counts in depth order; the pair count comes back to the host
+  stage_begin(ctx, s, 2, &ev);
+  launches = 0;
+  const uint32_t* order = f->gvals[f->g_final].as<uint32_t>();
+  launch_scan_counts(f->tile_count.as<uint32_t>(), order, n, f->offsets.as<uint32_t>(), ctx->scan_tmp.as<uint64_t>(),
+                     ctx->total.as<uint64_t>(), s, &launches);
+  NGS_TRY(check_launch(ctx, "scan"));
+  cudaError_t e = cudaMemcpyAsync(ctx->h_total, ctx->total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("reading the pair count: ") + cudaGetErrorString(e));
+  uint64_t P = *ctx->h_total;
+  if (P >= (1ull << 31)) return fail(ctx, NGS_ERR_INVALID_ARG, "more than 2^31 (tile, Gaussian) pairs");
+  uint32_t np = (uint32_t)P;
+  for (int k = 0; k < 2; ++k) {
+    NGS_TRY(ensure(ctx, f->pkeys[k], sizeof(uint64_t) * (size_t)std::max(np, 1u)));
+    NGS_TRY(ensure(ctx, f->pvals[k], sizeof(uint32_t) * (size_t)std::max(np, 1u)));
+  }
+  NGS_TRY(ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(std::max(np, 1u))));
+  launch_emit_keys(f->rec.as<float4>(), order, f->offsets.as<uint32_t>(), n, rp, cam->width, cam->height,
+                   f->pkeys[0].as<uint64_t>(), f->pvals[0].as<uint32_t>(), s);
+  stage_end(ctx, s, 2, ev, launches + (n ? 1 : 0));
+  NGS_TRY(check_launch(ctx, "emit keys"));
+  // 4. stable sort of the pairs by tile: the depth order inside each tile is kept, so the result is the
+  //    order of the full 64-bit (tile << 32 | depth) keys
+  stage_begin(ctx, s, 3, &ev);
+  launches = 0;
+  {
+    uint64_t* k2[2] = {f->pkeys[0].as<uint64_t>(), f->pkeys[1].as<uint64_t>()};
+    uint32_t* v2[2] = {f->pvals[0].as<uint32_t>(), f->pvals[1].as<uint32_t>()};
+    int tb = tile_bits(ntiles);
+    f->p_final = radix_sort_u64(k2, v2, np, 32, 32 + tb, ctx->hist.as<uint32_t>(), ctx->hist.cap / 4, s, &launches);
+  }
+  stage_end(ctx, s, 3, ev, launches);
+  NGS_TRY(check_launch(ctx, "tile sort"));
+  // 5. per-tile [start, end)
+  stage_begin(ctx, s, 4, &ev);
+  launch_tile_ranges(f->pkeys[f->p_final].as<uint64_t>(), np, ntiles, f->ranges.as<uint2>(), s);
+  stage_end(ctx, s, 4, ev, np ? 1 : 0);
+  NGS_TRY(check_launch(ctx, "tile ranges"));
+  // 6. composite
+  stage_begin(ctx, s, 5, &ev);
+  launch_composite_forward(f->rec.as<float4>(), f->pvals[f->p_final].as<uint32_t>(), f->ranges.as<uint2>(), rp,
+                           cam->width, cam->height, image, overdraw, f->state.as<float4>(), s);
+  stage_end(ctx, s, 5, ev, 1);
+  NGS_TRY(check_launch(ctx, "composite"));
+
+  f->n = n;
+  f->pairs = np;
+  f->W = cam->width;
+  f->H = cam->height;
+  f->cam = cp;
+  f->rp = rp;
+  f->has_render = true;
+  return NGS_OK;
+}
+
+NGS_API int ngs_render_backward(ngs_ctx* ctx, const ngs_frame* f, const ngs_gaussians* g, const float* dl_dimage,
+                                const ngs_grads* out, void* stream) {
+  if (!ctx) return NGS_ERR_INVALID_ARG;
+  if (!f || f->ctx != ctx || !f->has_render) return fail(ctx, NGS_ERR_INVALID_ARG, "frame holds no render");
+  if (!g || !dl_dimage || !out) return fail(ctx, NGS_ERR_INVALID_ARG, "null argument");
+  if (g->n != f->n || g->sh_degree != f->rp.sh_degree)
+    return fail(ctx, NGS_ERR_INVALID_ARG, "Gaussians do not match the rendered frame");
+  if (g->n > 0 && (!out->d_means || !out->d_log_scales || !out->d_quats || !out->d_opacity_logits || !out->d_sh))
+    return fail(ctx, NGS_ERR_INVALID_ARG, "null gradient array");
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t n = (uint32_t)f->n;
+  NGS_TRY(ensure(ctx, ctx->grad2d, sizeof(float4) * 3 * (size_t)std::max(n, 1u)));
+  cudaMemsetAsync(ctx->grad2d.p, 0, sizeof(float4) * 3 * (size_t)n, s);
+  cudaEvent_t ev;
+  stage_begin(ctx, s, 6, &ev);
+  launch_composite_backward(f->rec.as<float4>(), f->pvals[f->p_final].as<uint32_t>(), f->ranges.as<uint2>(), f->rp,
+                            f->W, f->H, dl_dimage, f->state.as<float4>(), ctx->grad2d.as<float4>(), s);
+  stage_end(ctx, s, 6, ev, 1);
+  NGS_TRY(check_launch(ctx, "composite backward"));
+  stage_begin(ctx, s, 7, &ev);
+  launch_project_backward(*g, f->cam, f->rp, f->rec.as<float4>(), f->tile_count.as<uint32_t>(),
+                          ctx->grad2d.as<float4>(), *out, s);
+  stage_end(ctx, s, 7, ev, n ? 1 : 0);
+  NGS_TRY(check_launch(ctx, "projection backward"));
+  return NGS_OK;
+}
+
+NGS_API int ngs_frame_view_get(const ngs_frame* f, ngs_frame_view* out) {
+  if (!f || !out) return NGS_ERR_INVALID_ARG;
+  memset(out, 0, sizeof(*out));
+  if (!f->has_render) return NGS_ERR_INVALID_ARG;
+  out->n_gaussians = f->n;
+  out->n_pairs = f->pairs;
+  out->tiles_x = f->rp.tiles_x;
+  out->tiles_y = f->rp.tiles_y;
+  out->width = f->W;
+  out->height = f->H;
+  out->records = f->rec.as<float>();
+  out->keys = f->pkeys[f->p_final].as<uint64_t>();
+  out->values = f->pvals[f->p_final].as<uint32_t>();
+  out->ranges = f->ranges.as<uint32_t>();
+  out->pixel_state = f->state.as<float>();
+  return NGS_OK;
+}
+
+NGS_API int ngs_set_timing(ngs_ctx* ctx, int enable) {
+  if (!ctx) return NGS_ERR_INVALID_ARG;
+  ctx->timing = enable != 0;
+  return NGS_OK;
+}
+
+NGS_API int ngs_stage_times(ngs_ctx* ctx, double* ms, int64_t* launches, int32_t n) {
+  if (!ctx) return NGS_ERR_INVALID_ARG;
+  for (auto& p : ctx->pending) {
+    float t = 0.f;
+    cudaEventSynchronize(p.b);
+    if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) ctx->stage_ms[p.stage] += t;
+    ctx->event_pool.push_back(p.a);
+    ctx->event_pool.push_back(p.b);
+  }
+  ctx->pending.clear();
+  for (int i = 0; i < n && i < NGS_NUM_STAGES; ++i) {
+    if (ms) ms[i] = ctx->stage_ms[i];
+    if (launches) launches[i] = ctx->stage_launches[i];
+  }
+  return NGS_NUM_STAGES;
+}
+
+NGS_API void ngs_reset_stage_times(ngs_ctx* ctx) {
+  if (!ctx) return;
+  ngs_stage_times(ctx, nullptr, nullptr, 0);
+  for (int i = 0; i < NGS_NUM_STAGES; ++i) {
+    ctx->stage_ms[i] = 0;
+    ctx->stage_launches[i] = 0;
+  }
+}
+
+NGS_API int64_t ngs_launch_count(const ngs_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

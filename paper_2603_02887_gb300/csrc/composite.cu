@@ -1,0 +1,351 @@
+// Per-tile front-to-back compositing (forward) and its path-replay adjoint (backward).
+//
+// One CTA per screen tile, one thread per pixel; warps cover 8 x 4 pixel blocks so that the pixels of a
+// warp are close and tend to saturate together. The tile's depth-sorted splat list is walked in chunks:
+// each thread stages one splat record (48 B) in shared memory, then every pixel walks the chunk.
+//
+// Forward, per pixel (Eq. generalized_gaussian with pbar_i from Eq. nexp_p and Table 1):
+//   alpha_i = min(alpha_max, aleph_i K_i(p)), skipped when alpha_i < alpha_min;
+//   quadratic:   pt = [alpha_i (1 + c taubar_i)]_+; if S + pt >= 1 the splat is k: pbar_k = 1 - S, the
+//                ray has saturated and stops; else pbar_i = pt, S += pt, taubar += alpha_i;
+//   exponential: stop before the splat that would take T below t_eps; pbar_i = alpha_i T, T *= 1 - alpha_i.
+// A warp whose 32 pixels have all stopped leaves the chunk loop (ballot), and the CTA leaves the tile once
+// every pixel has stopped (__syncthreads_count), which is where the faster-than-exponential models win.
+//
+// Backward (App. C), per pixel, replaying the same list front to back with identical FP32 arithmetic:
+//   quadratic:   dL0/dalpha_i = DeltaE_i (1 + c taubar_i) + c Theta_i for i < k, Theta running down from
+//                Theta_{-1} = A - E_k taubar_k (A = sum_{i<k} E_i alpha_i saved by the forward pass);
+//                dL0/dE_i = pbar_i; dL0/dalpha_k = 0;
+//   exponential: dL0/dalpha_i = T_i E_i - R_i / (1 - alpha_i), R_i = L0 - sum_{j<=i} E_j pbar_j;
+// then the chain through alpha_i = 2^(L + q'(p)) to the splat record, a warp-shuffle reduction over the
+// warp's pixels and one vector atomicAdd per warp and splat into the per-Gaussian gradient buffer.
+#include "ngs_internal.cuh"
+
+namespace ngs {
+namespace {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+template <int TW, int TH>
+struct TileGeom {
+  static constexpr int kThreads = TW * TH;
+  static constexpr int kWarpsX = TW / 8;
+  static_assert(TW % 8 == 0 && TH % 4 == 0, "tile must be a multiple of 8 x 4");
+  __device__ static void pixel(int tid, int tile_x0, int tile_y0, int& x, int& y) {
+    int warp = tid >> 5, lane = tid & 31;
+    x = tile_x0 + (warp % kWarpsX) * 8 + (lane & 7);
+    y = tile_y0 + (warp / kWarpsX) * 4 + (lane >> 3);
+  }
+};
+
+template <int TW, int TH, int KIND>
+__global__ void __launch_bounds__(TW* TH) composite_forward_kernel(const float4* __restrict__ rec,
+                                                                   const uint32_t* __restrict__ ids,
+                                                                   const uint2* __restrict__ ranges, RenderParams rp,
+                                                                   int W, int H, float* __restrict__ image,
+                                                                   int32_t* __restrict__ overdraw,
+                                                                   float4* __restrict__ state) {
+  using G = TileGeom<TW, TH>;
+  constexpr int B = G::kThreads;
+  __shared__ float4 s_r0[B];
+  __shared__ float4 s_r1[B];
+  __shared__ float s_e2[B];
+  int tile = blockIdx.x;
+  int tx = tile % rp.tiles_x, ty = tile / rp.tiles_x;
+  int tid = threadIdx.x;
+  int x, y;
+  G::pixel(tid, tx * TW, ty * TH, x, y);
+  bool inside = x < W && y < H;
+  float px = (float)x + 0.5f, py = (float)y + 0.5f;
+  uint2 range = ranges[tile];
+  bool done = !inside;
+  int od = 0;
+  uint32_t stop = range.y - range.x;  // entries walked (n of the replay state)
+  bool saturated = false;
+  float C0 = 0.f, C1 = 0.f, C2 = 0.f;
+  // quadratic state
+  float S = 0.f, tau = 0.f, A0 = 0.f, A1 = 0.f, A2 = 0.f, Ek0 = rp.bg[0], Ek1 = rp.bg[1], Ek2 = rp.bg[2];
+  // exponential state
+  float T = 1.f;
+  const float amax = rp.alpha_max, l2min = rp.log2_alpha_min, c = rp.c;
+  for (uint32_t base = range.x; base < range.y; base += B) {
+    if (__syncthreads_count(done) == B) break;
+    uint32_t i = base + tid;
+    if (i < range.y) {
+      uint32_t id = ids[i];
+      s_r0[tid] = rec[3 * (size_t)id];
+      s_r1[tid] = rec[3 * (size_t)id + 1];
+      s_e2[tid] = rec[3 * (size_t)id + 2].x;
+    }
+    __syncthreads();
+    int cnt = (int)min((uint32_t)B, range.y - base);
+    if (__any_sync(kFull, !done)) {
+      for (int j = 0; j < cnt && !done; ++j) {
+        float4 r0 = s_r0[j], r1 = s_r1[j];
+        float dx, dy;
+        float e = splat_log2_alpha(px, py, r0, r1, dx, dy);
+        if (e < l2min) continue;
+        float alpha = fminf(amax, fast_exp2(e));
+        float E0 = r1.z, E1 = r1.w, E2 = s_e2[j];
+        if (KIND == NGS_MODEL_QUAD) {
+          float pt = quad_slope(alpha, c, tau);
+          float Sn = __fadd_rn(S, pt);
+          ++od;
+          if (Sn >= 1.0f) {
+            float pk = 1.0f - S;
+            C0 = fmaf(E0, pk, C0);
+            C1 = fmaf(E1, pk, C1);
+            C2 = fmaf(E2, pk, C2);
+            Ek0 = E0;
+            Ek1 = E1;
+            Ek2 = E2;
+            saturated = true;
+            done = true;
+            stop = base + j + 1 - range.x;
+            break;
+          }
+          C0 = fmaf(E0, pt, C0);
+          C1 = fmaf(E1, pt, C1);
+          C2 = fmaf(E2, pt, C2);
+          A0 = fmaf(E0, alpha, A0);
+          A1 = fmaf(E1, alpha, A1);
+          A2 = fmaf(E2, alpha, A2);
+          S = Sn;
+          tau = __fadd_rn(tau, alpha);
+        } else {
+          float testT = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+          if (testT < rp.t_eps) {
+            done = true;
+            stop = base + j - range.x;
+            break;
+          }
+          float w = alpha * T;
+          C0 = fmaf(E0, w, C0);
+          C1 = fmaf(E1, w, C1);
+          C2 = fmaf(E2, w, C2);
+          T = testT;
+          ++od;
+        }
+        if (rp.max_splats > 0 && od == rp.max_splats) {
+          done = true;
+          stop = base + j + 1 - range.x;
+          break;
+        }
+      }
+    }
+  }
+  if (!inside) return;
+  size_t pix = (size_t)y * W + x;
+  float Tend = KIND == NGS_MODEL_QUAD ? (saturated ? 0.f : 1.f - S) : T;
+  float L0 = C0 + rp.bg[0] * Tend, L1 = C1 + rp.bg[1] * Tend, L2 = C2 + rp.bg[2] * Tend;
+  image[3 * pix] = L0;
+  image[3 * pix + 1] = L1;
+  image[3 * pix + 2] = L2;
+  if (overdraw) overdraw[pix] = od;
+  uint32_t nbits = stop | (saturated ? 0x80000000u : 0u);
+  if (KIND == NGS_MODEL_QUAD) {
+    state[2 * pix] = make_float4(__uint_as_float(nbits), Ek0, Ek1, Ek2);
+    state[2 * pix + 1] = make_float4(A0, A1, A2, tau);
+  } else {
+    state[2 * pix] = make_float4(__uint_as_float(nbits), L0, L1, L2);
+    state[2 * pix + 1] = make_float4(Tend, 0.f, 0.f, 0.f);
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+template <int TW, int TH, int KIND>
+__global__ void __launch_bounds__(TW* TH) composite_backward_kernel(const float4* __restrict__ rec,
+                                                                    const uint32_t* __restrict__ ids,
+                                                                    const uint2* __restrict__ ranges, RenderParams rp,
+                                                                    int W, int H, const float* __restrict__ dl_dimage,
+                                                                    const float4* __restrict__ state,
+                                                                    float4* __restrict__ grad2d) {
+  using G = TileGeom<TW, TH>;
+  constexpr int B = G::kThreads;
+  __shared__ float4 s_r0[B];
+  __shared__ float4 s_r1[B];
+  __shared__ float s_e2[B];
+  __shared__ uint32_t s_id[B];
+  int tile = blockIdx.x;
+  int tx = tile % rp.tiles_x, ty = tile / rp.tiles_x;
+  int tid = threadIdx.x, lane = tid & 31;
+  int x, y;
+  G::pixel(tid, tx * TW, ty * TH, x, y);
+  bool inside = x < W && y < H;
+  float px = (float)x + 0.5f, py = (float)y + 0.5f;
+  uint2 range = ranges[tile];
+  uint32_t last = range.x;  // replay entries [range.x, last)
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+  float Ek0 = 0.f, Ek1 = 0.f, Ek2 = 0.f;      // quadratic: E_k; exponential: L0
+  float Th0 = 0.f, Th1 = 0.f, Th2 = 0.f;      // quadratic: Theta
+  bool sat = false;
+  if (inside) {
+    size_t pix = (size_t)y * W + x;
+    float4 s0 = state[2 * pix], s1 = state[2 * pix + 1];
+    uint32_t nbits = __float_as_uint(s0.x);
+    last = range.x + (nbits & 0x7FFFFFFFu);
+    sat = (nbits >> 31) != 0;
+    Ek0 = s0.y;
+    Ek1 = s0.z;
+    Ek2 = s0.w;
+    g0 = dl_dimage[3 * pix];
+    g1 = dl_dimage[3 * pix + 1];
+    g2 = dl_dimage[3 * pix + 2];
+    if (KIND == NGS_MODEL_QUAD) {
+      Th0 = s1.x - Ek0 * s1.w;
+      Th1 = s1.y - Ek1 * s1.w;
+      Th2 = s1.z - Ek2 * s1.w;
+    }
+    if (g0 == 0.f && g1 == 0.f && g2 == 0.f) last = range.x;
+  }
+  (void)sat;
+  float S = 0.f, tau = 0.f, T = 1.f, acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+  const float amax = rp.alpha_max, l2min = rp.log2_alpha_min, c = rp.c;
+  for (uint32_t base = range.x; base < range.y; base += B) {
+    bool done = base >= last;
+    if (__syncthreads_count(done) == B) break;
+    uint32_t i = base + tid;
+    if (i < range.y) {
+      uint32_t id = ids[i];
+      s_id[tid] = id;
+      s_r0[tid] = rec[3 * (size_t)id];
+      s_r1[tid] = rec[3 * (size_t)id + 1];
+      s_e2[tid] = rec[3 * (size_t)id + 2].x;
+    }
+    __syncthreads();
+    int cnt = (int)min((uint32_t)B, range.y - base);
+    if (__any_sync(kFull, !done)) {
+      for (int j = 0; j < cnt; ++j) {
+        uint32_t pos = base + j;
+        if (!__any_sync(kFull, pos < last)) break;
+        float4 r0 = s_r0[j], r1 = s_r1[j];
+        float dx, dy;
+        float e = splat_log2_alpha(px, py, r0, r1, dx, dy);
+        bool on = pos < last && e >= l2min;
+        float gu = 0.f, gv = 0.f, gA = 0.f, gB = 0.f, gC = 0.f, gL = 0.f, gE0 = 0.f, gE1 = 0.f, gE2 = 0.f;
+        if (on) {
+          float raw = fast_exp2(e);
+          float alpha = fminf(amax, raw);
+          float E0 = r1.z, E1 = r1.w, E2 = s_e2[j];
+          float dLda;
+          if (KIND == NGS_MODEL_QUAD) {
+            float pt = quad_slope(alpha, c, tau);
+            float Sn = __fadd_rn(S, pt);
+            if (Sn >= 1.0f) {  // the saturating splat k: pbar_k = 1 - S, no dependence on alpha_k
+              float pk = 1.0f - S;
+              gE0 = g0 * pk;
+              gE1 = g1 * pk;
+              gE2 = g2 * pk;
+              dLda = 0.f;
+            } else {
+              float d0 = E0 - Ek0, d1 = E1 - Ek1, d2 = E2 - Ek2;
+              Th0 = fmaf(-d0, alpha, Th0);
+              Th1 = fmaf(-d1, alpha, Th1);
+              Th2 = fmaf(-d2, alpha, Th2);
+              float f = fmaf(c, tau, 1.0f);
+              dLda = g0 * fmaf(d0, f, c * Th0) + g1 * fmaf(d1, f, c * Th1) + g2 * fmaf(d2, f, c * Th2);
+              gE0 = g0 * pt;
+              gE1 = g1 * pt;
+              gE2 = g2 * pt;
+              S = Sn;
+              tau = __fadd_rn(tau, alpha);
+            }
+          } else {
+            float w = alpha * T;
+            acc0 = fmaf(E0, w, acc0);
+            acc1 = fmaf(E1, w, acc1);
+            acc2 = fmaf(E2, w, acc2);
+            float ia = 1.0f / (1.0f - alpha);
+            float d0 = T * E0 - (Ek0 - acc0) * ia;
+            float d1 = T * E1 - (Ek1 - acc1) * ia;
+            float d2 = T * E2 - (Ek2 - acc2) * ia;
+            dLda = g0 * d0 + g1 * d1 + g2 * d2;
+            gE0 = g0 * w;
+            gE1 = g1 * w;
+            gE2 = g2 * w;
+            T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+          }
+          // alpha = 2^e with e = L + dx (A' dx + B' dy) + C' dy^2, unless clamped at alpha_max
+          float wgt = raw >= amax ? 0.f : dLda * alpha * kLn2;
+          gL = wgt;
+          gA = wgt * dx * dx;
+          gB = wgt * dx * dy;
+          gC = wgt * dy * dy;
+          gu = -wgt * fmaf(2.f * r0.z, dx, r0.w * dy);
+          gv = -wgt * fmaf(r0.w, dx, 2.f * r1.x * dy);
+        }
+        if (__any_sync(kFull, on)) {
+          gu = warp_sum(gu);
+          gv = warp_sum(gv);
+          gA = warp_sum(gA);
+          gB = warp_sum(gB);
+          gC = warp_sum(gC);
+          gL = warp_sum(gL);
+          gE0 = warp_sum(gE0);
+          gE1 = warp_sum(gE1);
+          gE2 = warp_sum(gE2);
+          if (lane == 0) {
+            float4* dst = grad2d + 3 * (size_t)s_id[j];
+            atomicAdd(dst, make_float4(gu, gv, gA, gB));
+            atomicAdd(dst + 1, make_float4(gC, gL, gE0, gE1));
+            atomicAdd(reinterpret_cast<float*>(dst + 2), gE2);
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int TW, int TH>
+void forward_for_tile(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp, int W,
+                      int H, float* image, int32_t* overdraw, float4* state, cudaStream_t s) {
+  int ntiles = rp.tiles_x * rp.tiles_y;
+  if (rp.kind == NGS_MODEL_QUAD)
+    composite_forward_kernel<TW, TH, NGS_MODEL_QUAD><<<ntiles, TW * TH, 0, s>>>(rec, ids, ranges, rp, W, H, image,
+                                                                                  overdraw, state);
+  else
+    composite_forward_kernel<TW, TH, NGS_MODEL_EXP><<<ntiles, TW * TH, 0, s>>>(rec, ids, ranges, rp, W, H, image,
+                                                                                 overdraw, state);
+}
+
+template <int TW, int TH>
+void backward_for_tile(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp, int W,
+                       int H, const float* dl, const float4* state, float4* grad2d, cudaStream_t s) {
+  int ntiles = rp.tiles_x * rp.tiles_y;
+  if (rp.kind == NGS_MODEL_QUAD)
+    composite_backward_kernel<TW, TH, NGS_MODEL_QUAD><<<ntiles, TW * TH, 0, s>>>(rec, ids, ranges, rp, W, H, dl,
+                                                                                   state, grad2d);
+  else
+    composite_backward_kernel<TW, TH, NGS_MODEL_EXP><<<ntiles, TW * TH, 0, s>>>(rec, ids, ranges, rp, W, H, dl,
+                                                                                  state, grad2d);
+}
+
+}  // namespace
+
+void launch_composite_forward(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
+                              int W, int H, float* image, int32_t* overdraw, float4* state, cudaStream_t s) {
+  if (rp.tile_w == 8 && rp.tile_h == 8)
+    forward_for_tile<8, 8>(rec, ids, ranges, rp, W, H, image, overdraw, state, s);
+  else if (rp.tile_w == 16 && rp.tile_h == 16)
+    forward_for_tile<16, 16>(rec, ids, ranges, rp, W, H, image, overdraw, state, s);
+  else
+    forward_for_tile<16, 32>(rec, ids, ranges, rp, W, H, image, overdraw, state, s);
+}
+
+void launch_composite_backward(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
+                               int W, int H, const float* dl_dimage, const float4* state, float4* grad2d,
+                               cudaStream_t s) {
+  if (rp.tile_w == 8 && rp.tile_h == 8)
+    backward_for_tile<8, 8>(rec, ids, ranges, rp, W, H, dl_dimage, state, grad2d, s);
+  else if (rp.tile_w == 16 && rp.tile_h == 16)
+    backward_for_tile<16, 16>(rec, ids, ranges, rp, W, H, dl_dimage, state, grad2d, s);
+  else
+    backward_for_tile<16, 32>(rec, ids, ranges, rp, W, H, dl_dimage, state, grad2d, s);
+}
+
+}  // namespace ngs

@@ -1,0 +1,151 @@
+// Internal declarations shared by the CUDA translation units of the ngs library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ngs.h"
+
+namespace ngs {
+
+// ---- launch-time constants passed by value to kernels ------------------------------------------
+
+struct CamParams {
+  float R[9];       // world -> view rotation, row-major
+  float t[3];
+  float fx, fy, cx, cy;
+  float campos[3];  // camera centre in world space, -R^T t
+  int W, H;
+};
+
+struct RenderParams {
+  float alpha_min, alpha_max, t_eps, dilation, near_plane;
+  float log2_alpha_min;  // the alpha >= alpha_min test is made on log2(alpha)
+  float bg[3];
+  float c;               // quadratic parameter (NGS_MODEL_QUAD)
+  int kind;
+  int tile_w, tile_h, tiles_x, tiles_y;
+  int max_splats;
+  int sh_degree;
+};
+
+// Splat record: 3 float4 per Gaussian.
+//   r0 = (u, v, A', B'), r1 = (C', L, E0, E1), r2 = (E2, z, r, 0)
+// with (u, v) the screen mean, (A, B, C) the conic (inverse 2D covariance), k = -log2(e)/2,
+// A' = k A, B' = 2 k B, C' = k C, L = log2(aleph), so that log2(aleph K(p)) = L + dx (A' dx + B' dy) + C' dy^2.
+// z is the FP32 view depth (the sort key), r the conservative pixel radius (0: the splat takes no tile).
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr float kConicScale = -0.5f * 1.4426950408889634f;
+
+// Per-pixel replay state, 2 float4 per pixel (App. C: E_k is computed in the forward pass and handed
+// to the adjoint pass).
+//   quadratic:   s0 = (n | sat << 31, E_k), s1 = (A = sum_{i<k} E_i alpha_i, taubar_k)
+//   exponential: s0 = (n, C = L0 including background), s1 = (T_end, 0, 0, 0)
+// n = number of list entries of the pixel's tile that the forward pass walked through.
+
+// ---- helpers shared bit-for-bit by the forward and the replay kernels ---------------------------
+
+__device__ __forceinline__ float fast_exp2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// log2 of aleph * K(p) for the splat (r0, r1) at pixel centre (px, py); FP32, fixed operation order.
+__device__ __forceinline__ float splat_log2_alpha(float px, float py, float4 r0, float4 r1, float& dx, float& dy) {
+  dx = __fsub_rn(px, r0.x);
+  dy = __fsub_rn(py, r0.y);
+  float t = __fmaf_rn(r0.w, dy, __fmul_rn(r0.z, dx));
+  float q = __fmaf_rn(dx, t, __fmul_rn(__fmul_rn(r1.x, dy), dy));
+  return __fadd_rn(r1.y, q);
+}
+
+// Quadratic slope term alpha (1 + c taubar), clamped at 0 (Table 1 with the [.]_+ of T).
+__device__ __forceinline__ float quad_slope(float alpha, float c, float tau) {
+  return fmaxf(__fmul_rn(alpha, __fmaf_rn(c, tau, 1.0f)), 0.0f);
+}
+
+// ---- host-side objects ---------------------------------------------------------------------------
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  template <typename T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+}  // namespace ngs
+
+struct ngs_ctx {
+  std::string err;
+  int device = 0;
+  int num_sms = 0;
+  ngs::DevBuf hist;      // radix histograms
+  ngs::DevBuf scan_tmp;  // block sums of scans
+  ngs::DevBuf grad2d;    // per-Gaussian splat-record gradients (backward)
+  ngs::DevBuf total;     // device-side pair count (uint64)
+  uint64_t* h_total = nullptr;  // pinned mirror of `total`
+  bool timing = false;
+  struct Pending { cudaEvent_t a, b; int stage; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  double stage_ms[NGS_NUM_STAGES] = {0};
+  int64_t stage_launches[NGS_NUM_STAGES] = {0};
+  int64_t launches = 0;
+};
+
+struct ngs_frame {
+  ngs_ctx* ctx = nullptr;
+  bool has_render = false;
+  int64_t n = 0;
+  int64_t pairs = 0;
+  int W = 0, H = 0;
+  ngs::CamParams cam;
+  ngs::RenderParams rp;
+  ngs::DevBuf rec, tile_count, gkeys[2], gvals[2], offsets;
+  ngs::DevBuf pkeys[2], pvals[2], ranges, state;
+  int g_final = 0;  // which gvals[] holds the depth-sorted Gaussian order
+  int p_final = 0;  // which pkeys[]/pvals[] hold the sorted pairs
+};
+
+namespace ngs {
+
+// error / allocation helpers (api.cu)
+int fail(ngs_ctx* ctx, int code, const std::string& msg);
+int ensure(ngs_ctx* ctx, DevBuf& b, size_t bytes);
+void stage_begin(ngs_ctx* ctx, cudaStream_t s, int stage, cudaEvent_t* out);
+void stage_end(ngs_ctx* ctx, cudaStream_t s, int stage, cudaEvent_t start, int launches);
+
+// kernels' host launchers
+// writes records, depth keys (0xFFFFFFFF for splats without tiles), tile counts and order[i] = i
+void launch_project(const ngs_gaussians& g, const CamParams& cam, const RenderParams& rp, float4* rec,
+                    uint32_t* depth_key, uint32_t* tile_count, uint32_t* order, cudaStream_t s);
+void launch_project_backward(const ngs_gaussians& g, const CamParams& cam, const RenderParams& rp,
+                             const float4* rec, const uint32_t* tile_count, const float4* grad2d,
+                             const ngs_grads& out, cudaStream_t s);
+// radix sort of (key, value) pairs on bits [begin_bit, end_bit); returns the index (0/1) of the
+// buffer pair holding the result; launches counted into *launches
+int radix_sort_u32(uint32_t* keys[2], uint32_t* vals[2], uint32_t n, int begin_bit, int end_bit, uint32_t* hist,
+                   size_t hist_cap_words, cudaStream_t s, int* launches);
+int radix_sort_u64(uint64_t* keys[2], uint32_t* vals[2], uint32_t n, int begin_bit, int end_bit, uint32_t* hist,
+                   size_t hist_cap_words, cudaStream_t s, int* launches);
+size_t radix_hist_words(uint32_t n);
+// exclusive scan of tile_count[order[i]] into offsets[0..n] (offsets[n] = total) and the total into
+// *total (uint64, device)
+void launch_scan_counts(const uint32_t* tile_count, const uint32_t* order, uint32_t n, uint32_t* offsets,
+                        uint64_t* block_sums, uint64_t* total, cudaStream_t s, int* launches);
+size_t scan_tmp_words(uint32_t n);
+void launch_emit_keys(const float4* rec, const uint32_t* order, const uint32_t* offsets, uint32_t n,
+                      const RenderParams& rp, int W, int H, uint64_t* keys, uint32_t* vals, cudaStream_t s);
+void launch_tile_ranges(const uint64_t* keys, uint32_t npairs, uint32_t ntiles, uint2* ranges, cudaStream_t s);
+void launch_composite_forward(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
+                              int W, int H, float* image, int32_t* overdraw, float4* state, cudaStream_t s);
+void launch_composite_backward(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
+                               int W, int H, const float* dl_dimage, const float4* state, float4* grad2d,
+                               cudaStream_t s);
+
+}  // namespace ngs

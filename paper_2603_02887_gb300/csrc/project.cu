@@ -1,0 +1,387 @@
+// Projection of 3D Gaussians to splat records (forward) and its adjoint (backward).
+//
+// Forward (one thread per Gaussian): view transform, EWA screen covariance
+// Sigma' = J W R(q) S^2 R(q)^T W^T J^T + dilation I (the 3D Gaussian splatting convention the paper
+// builds on, Sec. 3), conic = Sigma'^-1, opacity aleph = sigmoid(logit), emission from real spherical
+// harmonics of degree <= 3, the opacity-aware radius r = sqrt(2 ln(aleph / alpha_min) lambda_max(Sigma'))
+// outside of which alpha < alpha_min, and the covered tile rectangle.
+// Backward: the exact chain rule of the same map, from splat-record gradients to raw parameters.
+#include <math.h>
+
+#include "ngs_internal.cuh"
+
+namespace ngs {
+namespace {
+
+// Real spherical-harmonic normalisations sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (x sqrt(2) for m != 0).
+constexpr float kC0 = 0.28209479177387814f;   // 1 / (2 sqrt(pi))
+constexpr float kC1 = 0.4886025119029199f;    // sqrt(3 / (4 pi))
+constexpr float kC2a = 1.0925484305920792f;   // sqrt(15 / (4 pi))
+constexpr float kC2b = 0.31539156525252005f;  // sqrt(5 / (16 pi))
+constexpr float kC2c = 0.5462742152960396f;   // sqrt(15 / (16 pi))
+constexpr float kC3a = 0.5900435899266435f;   // sqrt(35 / (32 pi))
+constexpr float kC3b = 2.890611442640554f;    // sqrt(105 / (4 pi))
+constexpr float kC3c = 0.4570457994644658f;   // sqrt(21 / (32 pi))
+constexpr float kC3d = 0.3731763325901154f;   // sqrt(7 / (16 pi))
+constexpr float kC3e = 1.445305721320277f;    // sqrt(105 / (16 pi))
+
+// Basis in the coefficient order and sign convention of 3D Gaussian splatting assets.
+__device__ __forceinline__ void sh_basis(int degree, float x, float y, float z, float* Y) {
+  Y[0] = kC0;
+  if (degree < 1) return;
+  Y[1] = -kC1 * y;
+  Y[2] = kC1 * z;
+  Y[3] = -kC1 * x;
+  if (degree < 2) return;
+  float xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = kC2a * x * y;
+  Y[5] = -kC2a * y * z;
+  Y[6] = kC2b * (2.f * zz - xx - yy);
+  Y[7] = -kC2a * x * z;
+  Y[8] = kC2c * (xx - yy);
+  if (degree < 3) return;
+  Y[9] = -kC3a * y * (3.f * xx - yy);
+  Y[10] = kC3b * x * y * z;
+  Y[11] = -kC3c * y * (4.f * zz - xx - yy);
+  Y[12] = kC3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+  Y[13] = -kC3c * x * (4.f * zz - xx - yy);
+  Y[14] = kC3e * z * (xx - yy);
+  Y[15] = -kC3a * x * (xx - 3.f * yy);
+}
+
+// sum_k w_k grad Y_k(x, y, z), treating (x, y, z) as free variables.
+__device__ __forceinline__ void sh_basis_grad(int degree, float x, float y, float z, const float* w, float& gx,
+                                              float& gy, float& gz) {
+  gx = gy = gz = 0.f;
+  if (degree < 1) return;
+  gy += -kC1 * w[1];
+  gz += kC1 * w[2];
+  gx += -kC1 * w[3];
+  if (degree < 2) return;
+  float xx = x * x, yy = y * y, zz = z * z;
+  gx += kC2a * y * w[4];
+  gy += kC2a * x * w[4];
+  gy += -kC2a * z * w[5];
+  gz += -kC2a * y * w[5];
+  gx += -2.f * kC2b * x * w[6];
+  gy += -2.f * kC2b * y * w[6];
+  gz += 4.f * kC2b * z * w[6];
+  gx += -kC2a * z * w[7];
+  gz += -kC2a * x * w[7];
+  gx += 2.f * kC2c * x * w[8];
+  gy += -2.f * kC2c * y * w[8];
+  if (degree < 3) return;
+  gx += -6.f * kC3a * x * y * w[9];
+  gy += -kC3a * (3.f * xx - 3.f * yy) * w[9];
+  gx += kC3b * y * z * w[10];
+  gy += kC3b * x * z * w[10];
+  gz += kC3b * x * y * w[10];
+  gx += 2.f * kC3c * x * y * w[11];
+  gy += -kC3c * (4.f * zz - xx - 3.f * yy) * w[11];
+  gz += -8.f * kC3c * y * z * w[11];
+  gx += -6.f * kC3d * x * z * w[12];
+  gy += -6.f * kC3d * y * z * w[12];
+  gz += kC3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+  gx += -kC3c * (4.f * zz - 3.f * xx - yy) * w[13];
+  gy += 2.f * kC3c * x * y * w[13];
+  gz += -8.f * kC3c * x * z * w[13];
+  gx += 2.f * kC3e * x * z * w[14];
+  gy += -2.f * kC3e * y * z * w[14];
+  gz += kC3e * (xx - yy) * w[14];
+  gx += -kC3a * (3.f * xx - 3.f * yy) * w[15];
+  gy += 6.f * kC3a * x * y * w[15];
+}
+
+// FP32 view depth with a fixed fma order (the sort key; also used for the near-plane test).
+__device__ __forceinline__ float view_depth(const CamParams& c, float px, float py, float pz) {
+  float z = __fmaf_rn(c.R[6], px, c.t[2]);
+  z = __fmaf_rn(c.R[7], py, z);
+  return __fmaf_rn(c.R[8], pz, z);
+}
+
+__device__ __forceinline__ void quat_to_rot(float w, float x, float y, float z, float* R) {
+  R[0] = 1.f - 2.f * (y * y + z * z);
+  R[1] = 2.f * (x * y - w * z);
+  R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z);
+  R[4] = 1.f - 2.f * (x * x + z * z);
+  R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y);
+  R[7] = 2.f * (y * z + w * x);
+  R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Everything the forward map computes that the backward needs again.
+struct ProjState {
+  float x, y, z, iz;       // view-space mean, 1/z
+  float qn[4], qnorm;      // normalised quaternion and the raw norm
+  float Rq[9], S[3];       // rotation and scales
+  float M[9];              // Rq diag(S)
+  float Sig[9];            // world covariance (full symmetric)
+  float T[6];              // J W
+  float s00, s01, s11;     // 2D covariance incl. dilation
+  float A, B, C;           // conic
+  float aleph;
+  float dir[3], dnorm;     // unit direction from the camera centre, |p - campos|
+  float e[3];              // unclamped emission
+  float Y[16];
+};
+
+__device__ __forceinline__ void forward_map(const ngs_gaussians& g, const CamParams& cam, const RenderParams& rp,
+                                            int i, ProjState& st) {
+  const float* m = g.means + 3 * (int64_t)i;
+  float px = m[0], py = m[1], pz = m[2];
+  st.x = cam.R[0] * px + cam.R[1] * py + cam.R[2] * pz + cam.t[0];
+  st.y = cam.R[3] * px + cam.R[4] * py + cam.R[5] * pz + cam.t[1];
+  st.z = view_depth(cam, px, py, pz);
+  st.iz = 1.f / st.z;
+  const float* q = g.quats + 4 * (int64_t)i;
+  st.qnorm = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  float inv = 1.f / st.qnorm;
+  for (int k = 0; k < 4; ++k) st.qn[k] = q[k] * inv;
+  quat_to_rot(st.qn[0], st.qn[1], st.qn[2], st.qn[3], st.Rq);
+  const float* ls = g.log_scales + 3 * (int64_t)i;
+  for (int k = 0; k < 3; ++k) st.S[k] = expf(ls[k]);
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) st.M[3 * r + c] = st.Rq[3 * r + c] * st.S[c];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      st.Sig[3 * r + c] = st.M[3 * r] * st.M[3 * c] + st.M[3 * r + 1] * st.M[3 * c + 1] + st.M[3 * r + 2] * st.M[3 * c + 2];
+  float j00 = cam.fx * st.iz, j02 = -cam.fx * st.x * st.iz * st.iz;
+  float j11 = cam.fy * st.iz, j12 = -cam.fy * st.y * st.iz * st.iz;
+  for (int c = 0; c < 3; ++c) {
+    st.T[c] = j00 * cam.R[c] + j02 * cam.R[6 + c];
+    st.T[3 + c] = j11 * cam.R[3 + c] + j12 * cam.R[6 + c];
+  }
+  float TS0[3], TS1[3];
+  for (int c = 0; c < 3; ++c) {
+    TS0[c] = st.T[0] * st.Sig[c] + st.T[1] * st.Sig[3 + c] + st.T[2] * st.Sig[6 + c];
+    TS1[c] = st.T[3] * st.Sig[c] + st.T[4] * st.Sig[3 + c] + st.T[5] * st.Sig[6 + c];
+  }
+  st.s00 = TS0[0] * st.T[0] + TS0[1] * st.T[1] + TS0[2] * st.T[2] + rp.dilation;
+  st.s01 = TS0[0] * st.T[3] + TS0[1] * st.T[4] + TS0[2] * st.T[5];
+  st.s11 = TS1[0] * st.T[3] + TS1[1] * st.T[4] + TS1[2] * st.T[5] + rp.dilation;
+  float det = st.s00 * st.s11 - st.s01 * st.s01;
+  float idet = 1.f / det;
+  st.A = st.s11 * idet;
+  st.B = -st.s01 * idet;
+  st.C = st.s00 * idet;
+  st.aleph = 1.f / (1.f + expf(-g.opacity_logits[i]));
+  float d0 = px - cam.campos[0], d1 = py - cam.campos[1], d2 = pz - cam.campos[2];
+  st.dnorm = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+  float idn = 1.f / st.dnorm;
+  st.dir[0] = d0 * idn;
+  st.dir[1] = d1 * idn;
+  st.dir[2] = d2 * idn;
+  int K = (rp.sh_degree + 1) * (rp.sh_degree + 1);
+  sh_basis(rp.sh_degree, st.dir[0], st.dir[1], st.dir[2], st.Y);
+  const float* sh = g.sh + (int64_t)i * K * 3;
+  for (int ch = 0; ch < 3; ++ch) {
+    float e = 0.5f;
+    for (int k = 0; k < K; ++k) e += st.Y[k] * sh[3 * k + ch];
+    st.e[ch] = e;
+  }
+}
+
+// Tile rectangle of a splat (u, v, r): identical arithmetic in the projection and the key emission.
+__device__ __forceinline__ bool tile_rect(float u, float v, float r, const RenderParams& rp, int& x0, int& x1,
+                                          int& y0, int& y1) {
+  float itw = 1.0f / (float)rp.tile_w, ith = 1.0f / (float)rp.tile_h;  // powers of two: exact
+  float fx0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(u, r), 0.5f), itw));
+  float fx1 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(u, r), 0.5f), itw));
+  float fy0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(v, r), 0.5f), ith));
+  float fy1 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(v, r), 0.5f), ith));
+  bool ok = r > 0.f && fx1 >= 0.f && fx0 <= (float)(rp.tiles_x - 1) && fy1 >= 0.f &&
+            fy0 <= (float)(rp.tiles_y - 1) && isfinite(fx0) && isfinite(fx1) && isfinite(fy0) && isfinite(fy1);
+  if (!ok) return false;
+  x0 = (int)fmaxf(fx0, 0.f);
+  x1 = (int)fminf(fx1, (float)(rp.tiles_x - 1));
+  y0 = (int)fmaxf(fy0, 0.f);
+  y1 = (int)fminf(fy1, (float)(rp.tiles_y - 1));
+  return true;
+}
+
+__global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, CamParams cam, RenderParams rp, float4* rec,
+                                                      uint32_t* depth_key, uint32_t* tile_count, uint32_t* order) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  const float* m = g.means + 3 * (int64_t)i;
+  float z = view_depth(cam, m[0], m[1], m[2]);
+  float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = make_float4(0.f, z, 0.f, 0.f);
+  uint32_t count = 0;
+  if (z > rp.near_plane) {
+    ProjState st;
+    forward_map(g, cam, rp, i, st);
+    float det = st.s00 * st.s11 - st.s01 * st.s01;
+    if (det > 0.f && st.aleph >= rp.alpha_min && isfinite(st.A) && isfinite(st.C)) {
+      float u = cam.fx * st.x * st.iz + cam.cx;
+      float v = cam.fy * st.y * st.iz + cam.cy;
+      float L = log2f(st.aleph);
+      float ha = 0.5f * (st.s00 + st.s11), hd = 0.5f * (st.s00 - st.s11);
+      float lam = ha + sqrtf(hd * hd + st.s01 * st.s01);
+      // alpha >= alpha_min needs d^T conic d <= 2 ln(aleph/alpha_min), hence |d|^2 <= 2 ln(.) lambda_max;
+      // the radius is widened by a relative 1e-4 and one pixel so that FP32 rounding never cuts a pixel
+      float r = sqrtf(fmaxf(2.f * kLn2 * (L - rp.log2_alpha_min), 0.f) * lam) * 1.0001f + 1.0f;
+      float E[3];
+      for (int ch = 0; ch < 3; ++ch) E[ch] = fmaxf(st.e[ch], 0.f);
+      r0 = make_float4(u, v, kConicScale * st.A, 2.f * kConicScale * st.B);
+      r1 = make_float4(kConicScale * st.C, L, E[0], E[1]);
+      r2 = make_float4(E[2], z, r, 0.f);
+      int x0, x1, y0, y1;
+      if (tile_rect(u, v, r, rp, x0, x1, y0, y1)) count = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+    }
+  }
+  rec[3 * (int64_t)i] = r0;
+  rec[3 * (int64_t)i + 1] = r1;
+  rec[3 * (int64_t)i + 2] = r2;
+  depth_key[i] = count ? __float_as_uint(z) : 0xFFFFFFFFu;
+  tile_count[i] = count;
+  order[i] = (uint32_t)i;
+}
+
+__global__ void __launch_bounds__(256) emit_keys_kernel(const float4* rec, const uint32_t* order,
+                                                        const uint32_t* offsets, uint32_t n, RenderParams rp,
+                                                        uint64_t* keys, uint32_t* vals) {
+  uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  uint32_t off = offsets[s], end = offsets[s + 1];
+  if (off == end) return;
+  uint32_t id = order[s];
+  float4 r0 = rec[3 * (int64_t)id];
+  float4 r2 = rec[3 * (int64_t)id + 2];
+  int x0, x1, y0, y1;
+  if (!tile_rect(r0.x, r0.y, r2.z, rp, x0, x1, y0, y1)) return;
+  uint64_t zb = (uint64_t)__float_as_uint(r2.y);
+  for (int ty = y0; ty <= y1; ++ty)
+    for (int tx = x0; tx <= x1 && off < end; ++tx) {
+      uint64_t tile = (uint64_t)(ty * rp.tiles_x + tx);
+      keys[off] = (tile << 32) | zb;
+      vals[off] = id;
+      ++off;
+    }
+}
+
+__global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, CamParams cam, RenderParams rp,
+                                                               const uint32_t* tile_count, const float4* grad2d,
+                                                               ngs_grads out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  int K = (rp.sh_degree + 1) * (rp.sh_degree + 1);
+  float* dm = out.d_means + 3 * (int64_t)i;
+  float* dls = out.d_log_scales + 3 * (int64_t)i;
+  float* dq = out.d_quats + 4 * (int64_t)i;
+  float* dsh = out.d_sh + (int64_t)i * K * 3;
+  if (tile_count[i] == 0) {
+    for (int k = 0; k < 3; ++k) dm[k] = dls[k] = 0.f;
+    for (int k = 0; k < 4; ++k) dq[k] = 0.f;
+    out.d_opacity_logits[i] = 0.f;
+    for (int k = 0; k < 3 * K; ++k) dsh[k] = 0.f;
+    return;
+  }
+  float4 g0 = grad2d[3 * (int64_t)i], g1 = grad2d[3 * (int64_t)i + 1], g2 = grad2d[3 * (int64_t)i + 2];
+  ProjState st;
+  forward_map(g, cam, rp, i, st);
+  // record -> natural quantities
+  float du = g0.x, dv = g0.y;
+  float dA = g0.z * kConicScale, dB = g0.w * 2.f * kConicScale, dC = g1.x * kConicScale;
+  float dE[3] = {g1.z, g1.w, g2.x};
+  out.d_opacity_logits[i] = g1.y * (1.f - st.aleph) / kLn2;  // L = log2(sigmoid(logit))
+  // conic Q = Sigma2^-1: dLoss/dSigma2 = -Q G Q, G = [[dA, dB/2], [dB/2, dC]]
+  float QG00 = st.A * dA + st.B * 0.5f * dB, QG01 = st.A * 0.5f * dB + st.B * dC;
+  float QG10 = st.B * dA + st.C * 0.5f * dB, QG11 = st.B * 0.5f * dB + st.C * dC;
+  float H00 = -(QG00 * st.A + QG01 * st.B);
+  float H01 = -(QG00 * st.B + QG01 * st.C);
+  float H11 = -(QG10 * st.B + QG11 * st.C);
+  float H[4] = {H00, H01, H01, H11};
+  // Sigma2 = T Sig T^T: dSig = T^T H T, dT = 2 H T Sig
+  float dSig[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      float acc = 0.f;
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) acc += st.T[3 * a + r] * H[2 * a + b] * st.T[3 * b + c];
+      dSig[3 * r + c] = acc;
+    }
+  float HT[6];
+  for (int a = 0; a < 2; ++a)
+    for (int c = 0; c < 3; ++c) HT[3 * a + c] = H[2 * a] * st.T[c] + H[2 * a + 1] * st.T[3 + c];
+  float dT[6];
+  for (int a = 0; a < 2; ++a)
+    for (int c = 0; c < 3; ++c)
+      dT[3 * a + c] = 2.f * (HT[3 * a] * st.Sig[c] + HT[3 * a + 1] * st.Sig[3 + c] + HT[3 * a + 2] * st.Sig[6 + c]);
+  // T = J W: dJ = dT W^T (only the four nonzero entries of J)
+  float dJ00 = dT[0] * cam.R[0] + dT[1] * cam.R[1] + dT[2] * cam.R[2];
+  float dJ02 = dT[0] * cam.R[6] + dT[1] * cam.R[7] + dT[2] * cam.R[8];
+  float dJ11 = dT[3] * cam.R[3] + dT[4] * cam.R[4] + dT[5] * cam.R[5];
+  float dJ12 = dT[3] * cam.R[6] + dT[4] * cam.R[7] + dT[5] * cam.R[8];
+  float iz = st.iz, iz2 = iz * iz, iz3 = iz2 * iz;
+  float dvx = du * cam.fx * iz - dJ02 * cam.fx * iz2;
+  float dvy = dv * cam.fy * iz - dJ12 * cam.fy * iz2;
+  float dvz = -du * cam.fx * st.x * iz2 - dv * cam.fy * st.y * iz2 - dJ00 * cam.fx * iz2 +
+              dJ02 * 2.f * cam.fx * st.x * iz3 - dJ11 * cam.fy * iz2 + dJ12 * 2.f * cam.fy * st.y * iz3;
+  float gm[3];
+  for (int c = 0; c < 3; ++c) gm[c] = cam.R[c] * dvx + cam.R[3 + c] * dvy + cam.R[6 + c] * dvz;
+  // Sig = M M^T: dM = 2 dSig M; M = Rq diag(S)
+  float dRq[9], dS[3] = {0.f, 0.f, 0.f};
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      float dMrc = 2.f * (dSig[3 * r] * st.M[c] + dSig[3 * r + 1] * st.M[3 + c] + dSig[3 * r + 2] * st.M[6 + c]);
+      dRq[3 * r + c] = dMrc * st.S[c];
+      dS[c] += dMrc * st.Rq[3 * r + c];
+    }
+  for (int c = 0; c < 3; ++c) dls[c] = dS[c] * st.S[c];
+  // rotation matrix of the unit quaternion (w, a, b, c)
+  float w = st.qn[0], a = st.qn[1], b = st.qn[2], c = st.qn[3];
+  const float* D = dRq;
+  float dqn[4];
+  dqn[0] = 2.f * (-c * D[1] + b * D[2] + c * D[3] - a * D[5] - b * D[6] + a * D[7]);
+  dqn[1] = 2.f * (b * D[1] + c * D[2] + b * D[3] - 2.f * a * D[4] - w * D[5] + c * D[6] + w * D[7] - 2.f * a * D[8]);
+  dqn[2] = 2.f * (-2.f * b * D[0] + a * D[1] + w * D[2] + a * D[3] + c * D[5] - w * D[6] + c * D[7] - 2.f * b * D[8]);
+  dqn[3] = 2.f * (-2.f * c * D[0] - w * D[1] + a * D[2] + w * D[3] - 2.f * c * D[4] + b * D[5] + a * D[6] + b * D[7]);
+  float dot = st.qn[0] * dqn[0] + st.qn[1] * dqn[1] + st.qn[2] * dqn[2] + st.qn[3] * dqn[3];
+  for (int k = 0; k < 4; ++k) dq[k] = (dqn[k] - st.qn[k] * dot) / st.qnorm;
+  // emission: dE/dsh = Y (unclamped channels); direction term into the mean
+  const float* sh = g.sh + (int64_t)i * K * 3;
+  float wk[16];
+  for (int k = 0; k < K; ++k) wk[k] = 0.f;
+  for (int ch = 0; ch < 3; ++ch) {
+    float d = st.e[ch] < 0.f ? 0.f : dE[ch];
+    for (int k = 0; k < K; ++k) {
+      dsh[3 * k + ch] = d * st.Y[k];
+      wk[k] += d * sh[3 * k + ch];
+    }
+  }
+  float gdx, gdy, gdz;
+  sh_basis_grad(rp.sh_degree, st.dir[0], st.dir[1], st.dir[2], wk, gdx, gdy, gdz);
+  float rad = st.dir[0] * gdx + st.dir[1] * gdy + st.dir[2] * gdz;
+  float idn = 1.f / st.dnorm;
+  gm[0] += (gdx - st.dir[0] * rad) * idn;
+  gm[1] += (gdy - st.dir[1] * rad) * idn;
+  gm[2] += (gdz - st.dir[2] * rad) * idn;
+  for (int k = 0; k < 3; ++k) dm[k] = gm[k];
+}
+
+}  // namespace
+
+void launch_project(const ngs_gaussians& g, const CamParams& cam, const RenderParams& rp, float4* rec,
+                    uint32_t* depth_key, uint32_t* tile_count, uint32_t* order, cudaStream_t s) {
+  if (g.n == 0) return;
+  int blocks = (int)((g.n + 255) / 256);
+  project_kernel<<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order);
+}
+
+void launch_emit_keys(const float4* rec, const uint32_t* order, const uint32_t* offsets, uint32_t n,
+                      const RenderParams& rp, int, int, uint64_t* keys, uint32_t* vals, cudaStream_t s) {
+  if (n == 0) return;
+  emit_keys_kernel<<<(n + 255) / 256, 256, 0, s>>>(rec, order, offsets, n, rp, keys, vals);
+}
+
+void launch_project_backward(const ngs_gaussians& g, const CamParams& cam, const RenderParams& rp,
+                             const float4*, const uint32_t* tile_count, const float4* grad2d, const ngs_grads& out,
+                             cudaStream_t s) {
+  if (g.n == 0) return;
+  int blocks = (int)((g.n + 127) / 128);
+  project_backward_kernel<<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out);
+}
+
+}  // namespace ngs

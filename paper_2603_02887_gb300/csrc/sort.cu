@@ -1,0 +1,305 @@
+// Device radix sort (stable LSD, 8-bit digits), exclusive scan of tile counts, and tile ranges.
+//
+// Each pass over n items runs three kernels:
+//   upsweep   per block of 4096 items: digit histogram -> hist[digit][block]
+//   scan      one block per digit: exclusive scan of hist[digit][*] in place, digit total -> totals[digit]
+//   downsweep per block: stable rank of every item within the block (warp multi-split with
+//             __match_any_sync, warps in order), reorder in shared memory so that items of one digit
+//             are contiguous, then a coalesced scatter to
+//             base(digit) + hist[digit][block] + rank, base = exclusive scan of totals.
+// Stability (equal digits keep their input order) makes the LSD passes a correct sort, and it is what
+// orders equal depths by Gaussian index (the pairs are emitted in index order within one depth).
+#include "ngs_internal.cuh"
+
+namespace ngs {
+namespace {
+
+// Exclusive prefix sum over a block (warp shuffles, then one warp scans the warp totals).
+// `s_warp` needs THREADS/32 entries; all threads must call it. Returns the exclusive prefix of `v`;
+// *total receives the block's sum.
+template <int THREADS, typename T>
+__device__ __forceinline__ T block_exclusive_sum(T v, T* s_warp, T* total) {
+  constexpr int NW = THREADS / 32;
+  static_assert(NW <= 32, "block too large");
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    T w = lane < NW ? s_warp[lane] : (T)0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < NW) s_warp[lane] = w;
+  }
+  __syncthreads();
+  T prefix = warp > 0 ? s_warp[warp - 1] : (T)0;
+  *total = s_warp[NW - 1];
+  __syncthreads();
+  return prefix + x - v;
+}
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;  // items per block
+constexpr int kWarps = kThreads / 32;
+constexpr int kDigits = 256;
+
+template <typename K>
+__device__ __forceinline__ uint32_t digit_of(K key, int shift) {
+  return (uint32_t)(key >> shift) & 0xFFu;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) upsweep_kernel(const K* __restrict__ keys, uint32_t n, int shift,
+                                                           uint32_t* __restrict__ hist, uint32_t nblocks) {
+  __shared__ uint32_t s_hist[kWarps][kDigits];
+  int tid = threadIdx.x, warp = tid >> 5;
+  for (int i = tid; i < kWarps * kDigits; i += kThreads) (&s_hist[0][0])[i] = 0;
+  __syncthreads();
+  uint32_t base = blockIdx.x * (uint32_t)kTile;
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    uint32_t idx = base + j * kThreads + tid;
+    if (idx < n) atomicAdd(&s_hist[warp][digit_of(keys[idx], shift)], 1u);
+  }
+  __syncthreads();
+  for (int d = tid; d < kDigits; d += kThreads) {
+    uint32_t sum = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) sum += s_hist[w][d];
+    hist[(size_t)d * nblocks + blockIdx.x] = sum;
+  }
+}
+
+// One block per digit: exclusive scan of that digit's per-block counts; the digit's total goes to
+// totals[digit] (stored after the histogram).
+__global__ void __launch_bounds__(1024) scan_digit_kernel(uint32_t* hist, uint32_t nblocks, uint32_t* totals) {
+  __shared__ uint32_t s_warp[32];
+  uint32_t* row = hist + (size_t)blockIdx.x * nblocks;
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < nblocks; base += 1024) {
+    uint32_t i = base + threadIdx.x;
+    uint32_t v = i < nblocks ? row[i] : 0u, agg;
+    uint32_t ex = block_exclusive_sum<1024>(v, s_warp, &agg);
+    if (i < nblocks) row[i] = ex + carry;
+    carry += agg;
+  }
+  if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) downsweep_kernel(const K* __restrict__ keys_in,
+                                                             const uint32_t* __restrict__ vals_in,
+                                                             K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                                                             uint32_t n, int shift, const uint32_t* __restrict__ hist,
+                                                             const uint32_t* __restrict__ totals, uint32_t nblocks) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  K* s_keys = reinterpret_cast<K*>(smem);
+  uint32_t* s_vals = reinterpret_cast<uint32_t*>(smem + sizeof(K) * kTile);
+  __shared__ uint32_t s_cnt[kWarps][kDigits];  // per-warp digit counters, then per-warp offsets
+  __shared__ uint32_t s_local[kDigits];         // block-local start of each digit
+  __shared__ uint32_t s_global[kDigits];        // global start of this block's run of each digit
+  __shared__ uint32_t s_warp[kWarps];
+
+  int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < kWarps * kDigits; i += kThreads) (&s_cnt[0][0])[i] = 0;
+  __syncthreads();
+
+  uint32_t base = blockIdx.x * (uint32_t)kTile + warp * (kTile / kWarps);
+  K key[kItems];
+  uint32_t val[kItems], rank[kItems], dig[kItems];
+  uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    uint32_t idx = base + r * 32 + lane;
+    bool valid = idx < n;
+    key[r] = valid ? keys_in[idx] : (K)0;
+    val[r] = valid ? vals_in[idx] : 0u;
+    uint32_t d = valid ? digit_of(key[r], shift) : (uint32_t)kDigits;  // kDigits = "no item"
+    dig[r] = d;
+    uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    uint32_t before = valid ? s_cnt[warp][d] : 0u;
+    rank[r] = before + __popc(peers & lt);
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) s_cnt[warp][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: exclusive offsets over warps, block total, block-local digit start, global start
+  uint32_t total = 0;
+  {
+    int d = tid;  // kThreads == kDigits
+    for (int w = 0; w < kWarps; ++w) {
+      uint32_t c = s_cnt[w][d];
+      s_cnt[w][d] = total;
+      total += c;
+    }
+    uint32_t agg;
+    s_local[d] = block_exclusive_sum<kThreads>(total, s_warp, &agg);
+  }
+  {
+    // global digit base = exclusive scan of the digit totals; this block's run starts hist[d][b] into it
+    uint32_t agg;
+    uint32_t ex = block_exclusive_sum<kThreads>(totals[tid], s_warp, &agg);
+    s_global[tid] = ex + hist[(size_t)tid * nblocks + blockIdx.x];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    if (dig[r] < (uint32_t)kDigits) {
+      uint32_t pos = s_local[dig[r]] + s_cnt[warp][dig[r]] + rank[r];
+      s_keys[pos] = key[r];
+      s_vals[pos] = val[r];
+    }
+  }
+  __syncthreads();
+  uint32_t count = min((uint32_t)kTile, n - blockIdx.x * (uint32_t)kTile);
+  for (uint32_t i = tid; i < count; i += kThreads) {
+    K k = s_keys[i];
+    uint32_t d = digit_of(k, shift);
+    uint32_t g = s_global[d] + (i - s_local[d]);
+    keys_out[g] = k;
+    vals_out[g] = s_vals[i];
+  }
+}
+
+template <typename K>
+int radix_sort(K* keys[2], uint32_t* vals[2], uint32_t n, int begin_bit, int end_bit, uint32_t* hist, size_t cap,
+               cudaStream_t s, int* launches) {
+  int cur = 0;
+  if (n <= 1 || begin_bit >= end_bit) return cur;
+  uint32_t nblocks = (n + kTile - 1) / kTile;
+  uint32_t* totals = hist + (size_t)kDigits * nblocks;
+  (void)cap;
+  size_t smem = (sizeof(K) + sizeof(uint32_t)) * kTile;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(downsweep_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  for (int shift = begin_bit; shift < end_bit; shift += 8) {
+    upsweep_kernel<K><<<nblocks, kThreads, 0, s>>>(keys[cur], n, shift, hist, nblocks);
+    scan_digit_kernel<<<kDigits, 1024, 0, s>>>(hist, nblocks, totals);
+    downsweep_kernel<K><<<nblocks, kThreads, smem, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift,
+                                                        hist, totals, nblocks);
+    cur ^= 1;
+    *launches += 3;
+  }
+  return cur;
+}
+
+// ---- exclusive scan of tile counts taken in depth order ---------------------------------------------
+
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ count,
+                                                                   const uint32_t* __restrict__ order, uint32_t n,
+                                                                   uint64_t* __restrict__ block_sums) {
+  __shared__ uint64_t s_warp[kScanThreads / 32];
+  uint64_t sum = 0;
+  uint32_t base = blockIdx.x * (uint32_t)kScanTile;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    uint32_t i = base + j * kScanThreads + threadIdx.x;
+    if (i < n) sum += count[order[i]];
+  }
+  uint64_t agg;
+  block_exclusive_sum<kScanThreads>(sum, s_warp, &agg);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = agg;
+}
+
+__global__ void __launch_bounds__(1024) scan_block_sums_kernel(uint64_t* block_sums, uint32_t nblocks, uint64_t* total) {
+  __shared__ uint64_t s_warp[32];
+  uint64_t carry = 0;
+  for (uint32_t base = 0; base < nblocks; base += 1024) {
+    uint32_t i = base + threadIdx.x;
+    uint64_t v = i < nblocks ? block_sums[i] : 0, agg;
+    uint64_t ex = block_exclusive_sum<1024>(v, s_warp, &agg);
+    if (i < nblocks) block_sums[i] = ex + carry;
+    carry += agg;
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const uint32_t* __restrict__ count,
+                                                                  const uint32_t* __restrict__ order, uint32_t n,
+                                                                  const uint64_t* __restrict__ block_offsets,
+                                                                  uint32_t* __restrict__ offsets) {
+  __shared__ uint32_t s_warp[kScanThreads / 32];
+  uint32_t base = blockIdx.x * (uint32_t)kScanTile + threadIdx.x * kScanItems;  // blocked arrangement
+  uint32_t v[kScanItems], local = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    uint32_t i = base + j;
+    v[j] = i < n ? count[order[i]] : 0u;
+    local += v[j];
+  }
+  uint32_t agg;
+  uint32_t run = (uint32_t)block_offsets[blockIdx.x] + block_exclusive_sum<kScanThreads>(local, s_warp, &agg);
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    uint32_t i = base + j;
+    if (i < n) offsets[i] = run;
+    run += v[j];
+    if (i == n - 1) offsets[n] = run;
+  }
+}
+
+__global__ void tile_ranges_kernel(const uint64_t* __restrict__ keys, uint32_t npairs, uint2* __restrict__ ranges) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npairs) return;
+  uint32_t t = (uint32_t)(keys[i] >> 32);
+  if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = i;
+  if (i == npairs - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = i + 1;
+}
+
+}  // namespace
+
+size_t radix_hist_words(uint32_t n) {
+  uint32_t nblocks = (n + kTile - 1) / kTile;
+  return (size_t)kDigits * (nblocks + 1);
+}
+
+int radix_sort_u32(uint32_t* keys[2], uint32_t* vals[2], uint32_t n, int begin_bit, int end_bit, uint32_t* hist,
+                   size_t cap, cudaStream_t s, int* launches) {
+  return radix_sort<uint32_t>(keys, vals, n, begin_bit, end_bit, hist, cap, s, launches);
+}
+
+int radix_sort_u64(uint64_t* keys[2], uint32_t* vals[2], uint32_t n, int begin_bit, int end_bit, uint32_t* hist,
+                   size_t cap, cudaStream_t s, int* launches) {
+  return radix_sort<uint64_t>(keys, vals, n, begin_bit, end_bit, hist, cap, s, launches);
+}
+
+size_t scan_tmp_words(uint32_t n) { return (size_t)(n + kScanTile - 1) / kScanTile + 1; }
+
+void launch_scan_counts(const uint32_t* tile_count, const uint32_t* order, uint32_t n, uint32_t* offsets,
+                        uint64_t* block_sums, uint64_t* total, cudaStream_t s, int* launches) {
+  if (n == 0) {
+    cudaMemsetAsync(offsets, 0, sizeof(uint32_t), s);
+    cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
+    return;
+  }
+  uint32_t nblocks = (n + kScanTile - 1) / kScanTile;
+  scan_reduce_kernel<<<nblocks, kScanThreads, 0, s>>>(tile_count, order, n, block_sums);
+  scan_block_sums_kernel<<<1, 1024, 0, s>>>(block_sums, nblocks, total);
+  scan_final_kernel<<<nblocks, kScanThreads, 0, s>>>(tile_count, order, n, block_sums, offsets);
+  *launches += 3;
+}
+
+void launch_tile_ranges(const uint64_t* keys, uint32_t npairs, uint32_t ntiles, uint2* ranges, cudaStream_t s) {
+  cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, s);
+  if (npairs == 0) return;
+  tile_ranges_kernel<<<(npairs + 255) / 256, 256, 0, s>>>(keys, npairs, ranges);
+}
+
+}  // namespace ngs

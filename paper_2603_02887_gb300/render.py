@@ -1,0 +1,245 @@
+"""PyTorch-facing API over the C ABI: ``Renderer`` (contexts and frames), and ``render`` as a
+``torch.autograd.Function`` whose backward is the library's path-replay adjoint.
+
+PyTorch only provides device memory and the current stream; every step of rendering and of its
+gradient runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+
+import numpy as np
+import torch
+
+from . import _abi
+
+#: model name -> (kind, parameter): exponential, and the quadratic mother transmittance with
+#: c = -0.5 (sub-linear), 0 (linear), +0.5 (super-linear) as in the paper's experiments (Sec. 5)
+MODELS = {"exp": (_abi.NGS_MODEL_EXP, 0.0), "sub": (_abi.NGS_MODEL_QUAD, -0.5), "lin": (_abi.NGS_MODEL_QUAD, 0.0),
+          "sup": (_abi.NGS_MODEL_QUAD, 0.5)}
+PARAM_KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+def model_spec(model):
+    if isinstance(model, str):
+        return MODELS[model]
+    kind, param = model
+    if isinstance(kind, str):
+        kind = {"exp": _abi.NGS_MODEL_EXP, "quad": _abi.NGS_MODEL_QUAD}[kind]
+    return int(kind), float(param)
+
+
+def default_options(**overrides) -> dict:
+    o = _abi.Options()
+    _abi.load().ngs_default_options(C.byref(o))
+    d = dict(alpha_min=o.alpha_min, alpha_max=o.alpha_max, t_eps=o.t_eps, dilation=o.dilation,
+             near_plane=o.near_plane, background=tuple(o.background), tile_w=o.tile_w, tile_h=o.tile_h,
+             max_splats=o.max_splats)
+    d.update(overrides)
+    return d
+
+
+def _options(opts) -> _abi.Options:
+    d = default_options(**(opts or {}))
+    o = _abi.Options()
+    for k in ("alpha_min", "alpha_max", "t_eps", "dilation", "near_plane"):
+        setattr(o, k, float(d[k]))
+    for i in range(3):
+        o.background[i] = float(d["background"][i])
+    o.tile_w, o.tile_h, o.max_splats, o.reserved = int(d["tile_w"]), int(d["tile_h"]), int(d["max_splats"]), 0
+    return o
+
+
+def _camera(cam) -> _abi.Camera:
+    c = _abi.Camera()
+    vm = np.asarray(cam["viewmat"], dtype=np.float32).reshape(12)
+    for i in range(12):
+        c.viewmat[i] = float(vm[i])
+    c.fx, c.fy, c.cx, c.cy = (float(cam[k]) for k in ("fx", "fy", "cx", "cy"))
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    return c
+
+
+def _check_param(t: torch.Tensor, name: str, device) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+    return t.contiguous()
+
+
+def _gaussians(params: dict, device=None):
+    ts = {k: _check_param(params[k], k, device) for k in PARAM_KEYS}
+    n = ts["means"].shape[0]
+    if n > 0:
+        K = ts["sh"].numel() // (3 * n)
+    else:
+        K = ts["sh"].shape[1] if ts["sh"].dim() == 3 else 1
+    deg = int(round(K ** 0.5)) - 1
+    if (deg + 1) ** 2 != K or deg > 3:
+        raise ValueError("sh must have (d+1)^2 coefficients per Gaussian, d <= 3")
+    expect = {"means": n * 3, "log_scales": n * 3, "quats": n * 4, "opacity_logits": n, "sh": n * K * 3}
+    for k, m in expect.items():
+        if ts[k].numel() != m:
+            raise ValueError(f"{k} has {ts[k].numel()} elements, expected {m}")
+    g = _abi.Gaussians(n, deg, *(ts[k].data_ptr() for k in PARAM_KEYS))
+    return g, ts
+
+
+class Frame:
+    """Replay state of one render (owned by the library, reused across renders)."""
+
+    def __init__(self, renderer: "Renderer"):
+        self.renderer = renderer
+        self.handle = C.c_void_p()
+        _abi.check(_abi.load().ngs_frame_create(renderer.ctx, C.byref(self.handle)), renderer.ctx)
+        self.width = self.height = 0
+
+    def view(self) -> dict:
+        v = _abi.FrameView()
+        _abi.check(_abi.load().ngs_frame_view_get(self.handle, C.byref(v)), self.renderer.ctx)
+        return {f: getattr(v, f) for f, _ in _abi.FrameView._fields_}
+
+    def release(self):
+        if self.handle:
+            _abi.load().ngs_frame_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class Renderer:
+    """One library context on one CUDA device. Not thread-safe; use one per thread."""
+
+    def __init__(self, device=None):
+        self.lib = _abi.load()
+        device = torch.device("cuda") if device is None else torch.device(device)
+        if device.index is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        self.device = device
+        with torch.cuda.device(self.device):
+            self.ctx = C.c_void_p()
+            _abi.check(self.lib.ngs_create(C.byref(self.ctx)), None)
+        self._pool = []
+
+    def close(self):
+        for f in self._pool:
+            f.release()
+        self._pool = []
+        if self.ctx:
+            self.lib.ngs_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # frames -------------------------------------------------------------------------------------
+    def frame(self) -> Frame:
+        return self._pool.pop() if self._pool else Frame(self)
+
+    def recycle(self, frame: Frame):
+        self._pool.append(frame)
+
+    # calls --------------------------------------------------------------------------------------
+    def render(self, params: dict, camera: dict, model="sup", options=None, frame: Frame | None = None,
+               image: torch.Tensor | None = None, overdraw: torch.Tensor | None = None):
+        """Render ``params`` through ``camera``. Returns (image [H,W,3] f32, overdraw [H,W] i32, frame)."""
+        g, keep = _gaussians(params, self.device)
+        cam = _camera(camera)
+        kind, param = model_spec(model)
+        m = _abi.Model(kind, param)
+        o = _options(options)
+        H, W = cam.height, cam.width
+        if image is None:
+            image = torch.empty((H, W, 3), dtype=torch.float32, device=self.device)
+        if overdraw is None:
+            overdraw = torch.empty((H, W), dtype=torch.int32, device=self.device)
+        frame = frame or self.frame()
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        rc = self.lib.ngs_render(self.ctx, frame.handle, C.byref(g), C.byref(cam), C.byref(m), C.byref(o),
+                                 image.data_ptr(), overdraw.data_ptr(), stream)
+        _abi.check(rc, self.ctx)
+        frame.width, frame.height = W, H
+        del keep
+        return image, overdraw, frame
+
+    def backward(self, frame: Frame, params: dict, dl_dimage: torch.Tensor, out: dict | None = None) -> dict:
+        """Path-replay gradients of the frame's render w.r.t. the raw parameters (overwritten into ``out``)."""
+        g, keep = _gaussians(params, self.device)
+        dl = _check_param(dl_dimage, "dl_dimage", self.device)
+        if dl.numel() != frame.height * frame.width * 3:
+            raise ValueError("dl_dimage must be [H, W, 3] of the rendered frame")
+        if out is None:
+            out = {"d_" + k: torch.empty_like(keep[k]) for k in PARAM_KEYS}
+        gr = _abi.Grads(*(out["d_" + k].data_ptr() for k in PARAM_KEYS))
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        rc = self.lib.ngs_render_backward(self.ctx, frame.handle, C.byref(g), dl.data_ptr(), C.byref(gr), stream)
+        _abi.check(rc, self.ctx)
+        return out
+
+    def set_timing(self, enable: bool):
+        _abi.check(self.lib.ngs_set_timing(self.ctx, int(bool(enable))), self.ctx)
+
+    def stage_times(self) -> dict:
+        ms = (C.c_double * _abi.NGS_NUM_STAGES)()
+        cnt = (C.c_int64 * _abi.NGS_NUM_STAGES)()
+        self.lib.ngs_stage_times(self.ctx, ms, cnt, _abi.NGS_NUM_STAGES)
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(_abi.STAGES)}
+
+    def reset_stage_times(self):
+        self.lib.ngs_reset_stage_times(self.ctx)
+
+    def launch_count(self) -> int:
+        return int(self.lib.ngs_launch_count(self.ctx))
+
+
+_renderers = threading.local()
+
+
+def default_renderer(device=None) -> Renderer:
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    if dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+    cache = getattr(_renderers, "by_device", None)
+    if cache is None:
+        cache = _renderers.by_device = {}
+    if dev not in cache:
+        cache[dev] = Renderer(dev)
+    return cache[dev]
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, camera, model, options, renderer, means, log_scales, quats, opacity_logits, sh):
+        params = dict(means=means, log_scales=log_scales, quats=quats, opacity_logits=opacity_logits, sh=sh)
+        image, overdraw, frame = renderer.render(params, camera, model, options)
+        ctx.frame, ctx.renderer = frame, renderer
+        ctx.save_for_backward(means, log_scales, quats, opacity_logits, sh)
+        ctx.mark_non_differentiable(overdraw)
+        return image, overdraw
+
+    @staticmethod
+    def backward(ctx, dl_dimage, _dl_overdraw):
+        means, log_scales, quats, opacity_logits, sh = ctx.saved_tensors
+        params = dict(means=means, log_scales=log_scales, quats=quats, opacity_logits=opacity_logits, sh=sh)
+        grads = ctx.renderer.backward(ctx.frame, params, dl_dimage.contiguous())
+        ctx.renderer.recycle(ctx.frame)
+        ctx.frame = None
+        return (None, None, None, None, *(grads["d_" + k] for k in PARAM_KEYS))
+
+
+def render(params: dict, camera: dict, model="sup", options=None, renderer: Renderer | None = None):
+    """Differentiable render: returns (image [H,W,3], overdraw [H,W]); gradients reach the five parameter
+    tensors of ``params`` through the library's path-replay backward."""
+    renderer = renderer or default_renderer(params["means"].device)
+    return _RenderFn.apply(camera, model, options, renderer, *(params[k] for k in PARAM_KEYS))

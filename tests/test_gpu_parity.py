@@ -1,0 +1,212 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: keys, sort order, tile ranges and overdraw are bit-exact; pixels agree to max-abs 1e-4 and
+gradients to relative 1e-3 (with a floor of 1e-3 x the tensor's largest gradient), FP32 against FP64.
+Pixels the oracle flags as fragile (a threshold decision within 1e-4 relative of its threshold, where
+FP32 and FP64 may legitimately decide differently) are excluded from pixel parity and get a zero
+upstream gradient in gradient parity; their share is bounded.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+from oracle import binning  # noqa: E402
+from paper_2603_02887_gb300 import synth  # noqa: E402
+from paper_2603_02887_gb300.render import Renderer, render  # noqa: E402
+from tests.gpu_util import describe_mismatch, frame_arrays, grad_mismatch, upload  # noqa: E402
+
+MODELS = ["exp", "sub", "lin", "sup"]
+NT = os.cpu_count() or 4
+KC = -0.5 * 1.4426950408889634  # conic scale folded into the records
+
+
+@pytest.fixture(scope="module")
+def rnd():
+    r = Renderer("cuda:0")
+    yield r
+    r.close()
+
+
+def _records_to_oracle_layout(rec):
+    return dict(u=rec[:, 0], v=rec[:, 1], A=rec[:, 2] / KC, B=rec[:, 3] / (2 * KC), C=rec[:, 4] / KC,
+                aleph=np.exp2(rec[:, 5].astype(np.float64)), E=rec[:, [6, 7, 8]], z=rec[:, 9], r=rec[:, 10])
+
+
+@pytest.mark.parametrize("which", ["tiny", "clustered"])
+def test_projection_matches_oracle(rnd, which):
+    if which == "tiny":
+        scene, cam = synth.tiny_scene(0), synth.tiny_camera()
+    else:
+        scene, cam = synth.clustered_scene(4000, seed=1, sh_degree=3), synth.outside_camera(640, 360)
+    params = upload(scene)
+    _, _, frame = rnd.render(params, cam, "sup")
+    fa = frame_arrays(frame)
+    g = _records_to_oracle_layout(fa["records"])
+    ref = oracle.project(scene, cam)
+    live = fa["records"][:, 10] > 0
+    assert np.array_equal(live, ref["valid"]), "valid set differs"
+    rr = ref["rec"][live]
+    np.testing.assert_allclose(g["u"][live], rr[:, 0], rtol=2e-6, atol=2e-4)
+    np.testing.assert_allclose(g["v"][live], rr[:, 1], rtol=2e-6, atol=2e-4)
+    scale = np.maximum(np.abs(rr[:, 2]), np.abs(rr[:, 4]))
+    for j, key in ((2, "A"), (3, "B"), (4, "C")):
+        assert np.all(np.abs(g[key][live] - rr[:, j]) <= 2e-4 * scale), key
+    np.testing.assert_allclose(g["aleph"][live], rr[:, 5], rtol=2e-6)
+    np.testing.assert_allclose(g["E"][live], rr[:, 6:9], atol=2e-5)
+    assert np.array_equal(g["z"], ref["z32"]), "FP32 sort depth must be bit-identical"
+    assert np.all(g["r"][live] >= rr[:, 9]), "the pixel radius must be conservative"
+
+
+@pytest.mark.parametrize("tile", [(8, 8), (16, 16), (16, 32)])
+def test_binning_keys_bit_exact(rnd, tile):
+    scene, cam = synth.clustered_scene(3000, seed=2, sh_degree=1), synth.outside_camera(333, 211)
+    params = upload(scene)
+    _, _, frame = rnd.render(params, cam, "exp", options=dict(tile_w=tile[0], tile_h=tile[1]))
+    fa = frame_arrays(frame)
+    rec = fa["records"]
+    keys, vals, ranges = binning.sorted_pairs(rec[:, 0], rec[:, 1], rec[:, 10], rec[:, 9], tile[0], tile[1],
+                                              cam["width"], cam["height"])
+    assert fa["view"]["n_pairs"] == len(keys)
+    assert np.array_equal(fa["keys"], keys)
+    assert np.array_equal(fa["values"], vals)
+    assert np.array_equal(fa["ranges"].astype(np.int64), ranges)
+
+
+def _forward_check(rnd, scene, cam, model, options=None, max_fragile=0.01):
+    params = upload(scene)
+    image, overdraw, frame = rnd.render(params, cam, model, options)
+    ref = oracle.render(scene, cam, model, opts=options and {k: v for k, v in options.items()
+                                                                 if k not in ("tile_w", "tile_h")}, nthreads=NT)
+    ok = ~ref["fragile"]
+    img = image.cpu().numpy()
+    od = overdraw.cpu().numpy()
+    assert ref["fragile"].sum() <= max(2, max_fragile * ref["fragile"].size), f"fragile share {ref['fragile'].mean()}"
+    err = np.abs(img - ref["image"])[ok]
+    assert err.size == 0 or err.max() <= 1e-4, f"max abs error {err.max()}"
+    assert np.array_equal(od[ok], ref["overdraw"][ok])
+    return image, overdraw, frame, ref
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_forward_matches_oracle_tiny(rnd, model):
+    _forward_check(rnd, synth.tiny_scene(0), synth.tiny_camera(), model)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_forward_matches_oracle_clustered_ragged(rnd, model):
+    """Several tiles and a ragged tail in both directions, SH degree 3, an oblique camera."""
+    _forward_check(rnd, synth.clustered_scene(20000, seed=4, sh_degree=3), synth.outside_camera(203, 141, 12.0),
+                   model)
+
+
+def test_tile_shapes_bit_identical(rnd):
+    scene, cam = synth.clustered_scene(20000, seed=5, sh_degree=2), synth.outside_camera(250, 170, 13.0)
+    params = upload(scene)
+    for model in MODELS:
+        outs = []
+        for tile in ((8, 8), (16, 16), (16, 32)):
+            img, od, _ = rnd.render(params, cam, model, dict(tile_w=tile[0], tile_h=tile[1]))
+            outs.append((img.cpu().numpy(), od.cpu().numpy()))
+        for img, od in outs[1:]:
+            assert np.array_equal(img, outs[0][0]) and np.array_equal(od, outs[0][1]), model
+
+
+def _backward_check(rnd, scene, cam, model, seed=3):
+    params = upload(scene)
+    image, overdraw, frame = rnd.render(params, cam, model)
+    ref0 = oracle.render(scene, cam, model, nthreads=NT)
+    g = synth.upstream_gradient(cam["height"], cam["width"], seed=seed).astype(np.float64)
+    g *= ~ref0["fragile"][..., None]
+    ref = oracle.render(scene, cam, model, nthreads=NT, dl_dimage=g)
+    grads = rnd.backward(frame, params, torch.from_numpy(g.astype(np.float32)).cuda())
+    torch.cuda.synchronize()
+    report = {}
+    for k in ("d_means", "d_log_scales", "d_quats", "d_opacity_logits", "d_sh"):
+        a = grads[k].cpu().numpy()
+        sc = ref["s_" + k[2:]]
+        bad = grad_mismatch(a, ref[k], exclude=ref["fragile_gauss"], scale=sc)
+        if bad.any():
+            report[k] = f"{int(bad.sum())} of {bad.size}: " + describe_mismatch(a, ref[k], bad, sc)
+    assert not report, report
+    return grads, ref
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_backward_matches_oracle_tiny(rnd, model):
+    _backward_check(rnd, synth.tiny_scene(0), synth.tiny_camera(), model)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_backward_matches_oracle_clustered(rnd, model):
+    _backward_check(rnd, synth.clustered_scene(6000, seed=6, sh_degree=3), synth.outside_camera(160, 120, 12.0),
+                    model)
+
+
+def test_forward_is_deterministic(rnd):
+    scene, cam = synth.clustered_scene(20000, seed=7, sh_degree=3), synth.outside_camera(300, 200)
+    params = upload(scene)
+    a = rnd.render(params, cam, "exp")[0].cpu().numpy()
+    b = rnd.render(params, cam, "exp")[0].cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_edge_cases(rnd):
+    cam = synth.tiny_camera()
+    # no Gaussians: background everywhere, no overdraw
+    empty = {k: v[:0] for k, v in synth.tiny_scene(0).items()}
+    img, od, _ = rnd.render(upload(empty), cam, "sup", dict(background=(0.25, 0.5, 0.75)))
+    assert np.allclose(img.cpu().numpy(), [0.25, 0.5, 0.75]) and not od.cpu().numpy().any()
+    # every Gaussian behind the camera
+    behind = synth.tiny_scene(0)
+    behind["means"] = behind["means"] * np.float32([1, 1, -1])
+    img, od, _ = rnd.render(upload(behind), cam, "exp")
+    assert not img.cpu().numpy().any() and not od.cpu().numpy().any()
+    # one Gaussian covering the whole image, with a background
+    one = synth.tiny_scene(0, n=1)
+    one["means"][:] = [0.0, 0.0, 3.0]
+    one["log_scales"][:] = 0.0
+    for model in MODELS:  # one large splat: the alpha_min / alpha_max contours make a few % of pixels fragile
+        _forward_check(rnd, one, cam, model, dict(background=(0.2, 0.5, 0.9)), max_fragile=0.05)
+    # ragged image smaller than one tile
+    small = synth.pinhole(np.concatenate([np.eye(3), np.zeros((3, 1))], 1), 13, 7, 20.0, 20.0)
+    for model in MODELS:
+        _forward_check(rnd, synth.tiny_scene(1, n=200), small, model)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_max_splats_cap(rnd, model):
+    _forward_check(rnd, synth.tiny_scene(2), synth.tiny_camera(), model, dict(max_splats=3))
+
+
+def test_invalid_arguments_are_rejected(rnd):
+    from paper_2603_02887_gb300._abi import NGSError
+
+    params = upload(synth.tiny_scene(0, n=10))
+    cam = synth.tiny_camera()
+    with pytest.raises(NGSError):
+        rnd.render(params, cam, ("quad", -0.75))
+    with pytest.raises(NGSError):
+        rnd.render(params, cam, "sup", dict(tile_w=12, tile_h=12))
+    with pytest.raises(NGSError):
+        rnd.render(params, dict(cam, width=0), "sup")
+
+
+def test_autograd_function_matches_direct_backward(rnd):
+    scene, cam = synth.tiny_scene(3, n=500), synth.tiny_camera()
+    params = upload(scene)
+    leaf = {k: v.clone().requires_grad_(True) for k, v in params.items()}
+    image, _ = render(leaf, cam, "lin", renderer=rnd)
+    g = torch.from_numpy(synth.upstream_gradient(128, 128, seed=9)).cuda()
+    (image * g).sum().backward()
+    _, _, frame = rnd.render(params, cam, "lin")
+    direct = rnd.backward(frame, params, g)
+    for k in params:  # the same kernels; only the order of the float atomics may differ
+        a, b = leaf[k].grad, direct["d_" + k]
+        assert torch.all((a - b).abs() <= 1e-4 * b.abs() + 1e-5 * b.abs().max()), k
