@@ -133,6 +133,7 @@ def run_ours(args):
     import torch.distributed as dist
 
     from paper_2603_02887_gb300 import synth
+    from paper_2603_02887_gb300.distributed import max_over_ranks
     from paper_2603_02887_gb300.render import PARAM_KEYS, Renderer
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -208,11 +209,7 @@ def run_ours(args):
     stage = r.stage_times()
     r.set_timing(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), device=dev)
     ms_per_step = total_ms / K
     px = W * H
     value = world * len(MODELS) * px / (ms_per_step * 1e-3) / 1e6
