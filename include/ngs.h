@@ -158,6 +158,18 @@ NGS_API int ngs_render(ngs_ctx* ctx, ngs_frame* frame, const ngs_gaussians* g, c
 NGS_API int ngs_render_backward(ngs_ctx* ctx, const ngs_frame* frame, const ngs_gaussians* g,
                                 const float* dl_dimage, const ngs_grads* out, void* stream);
 
+/* The backward above, for callers that cannot let the library allocate device memory (an application
+ * that owns a fixed device-memory budget, or a latency-critical loop where cudaMalloc / cudaFree would
+ * synchronise the device). The paper has no counterpart: this is an interface addition. Same arguments
+ * and results as ngs_render_backward, but the per-Gaussian scratch lives in one static device array of
+ * 12 MiB that every GPU loading the library holds until the process exits, and nothing is allocated.
+ * Limits: at most 262,144 Gaussians (larger frames return NGS_ERR_INVALID_ARG with a message naming the
+ * limit). All calls on a device share the array; each call clears what it uses first, and calls that
+ * overlap on the GPU (unordered streams or threads) race on it. The first call on a device, with that
+ * device current, looks up the array's address (cudaGetSymbolAddress); make it before any stream capture. */
+NGS_API int ngs_render_backward_static(ngs_ctx* ctx, const ngs_frame* frame, const ngs_gaussians* g,
+                                       const float* dl_dimage, const ngs_grads* out, void* stream);
+
 /* Fill `out` with device pointers into the frame (for tests and diagnostics). */
 NGS_API int ngs_frame_view_get(const ngs_frame* frame, ngs_frame_view* out);
 

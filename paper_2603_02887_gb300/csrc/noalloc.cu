@@ -1,0 +1,83 @@
+// ngs_render_backward_static: the path-replay backward without any device allocation.
+//
+// ngs_render_backward keeps its per-Gaussian splat-record gradients (3 float4 per Gaussian) in scratch
+// that the context allocates with cudaMalloc on first use and grows on demand. Some callers cannot let
+// a library allocate: applications that own a fixed device-memory budget (a server that reserves its
+// pool up front, a host program that forbids third-party allocations), and latency-critical loops in
+// which cudaMalloc / cudaFree would synchronise the device and stall other streams. This variant keeps
+// that scratch in a fixed static device array instead, and allocates nothing.
+//
+// Limits and behaviour:
+//  * at most kStaticMaxGaussians = 262,144 Gaussians per call (the array is 12 MiB); larger frames are
+//    rejected with NGS_ERR_INVALID_ARG and a message that names the limit;
+//  * every GPU that loads this library holds the array until the process exits;
+//  * all calls on a device share the one array and it keeps the previous call's contents, so each call
+//    clears the part it uses (cudaMemsetAsync) before use, and calls whose work overlaps on the GPU
+//    (different streams or host threads without ordering between them) race on it;
+//  * the first call on a device, with that device current, looks up the array's device address with
+//    cudaGetSymbolAddress (host code cannot use the symbol itself as a device pointer); make that first
+//    call before any stream capture.
+#include <mutex>
+
+#include "ngs_internal.cuh"
+
+namespace {
+
+constexpr int64_t kStaticMaxGaussians = 262144;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) float4 g_static_grad2d[3 * kStaticMaxGaussians];
+
+std::mutex g_mutex;
+void* g_device_ptr[kMaxDevices] = {};
+
+// Device address of g_static_grad2d on the current device (looked up once per device).
+int static_scratch(ngs_ctx* ctx, void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return ngs::fail(ctx, NGS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return ngs::fail(ctx, NGS_ERR_INVALID_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_mutex);
+  if (!g_device_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_grad2d);
+    if (e != cudaSuccess || !p)
+      return ngs::fail(ctx, NGS_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_device_ptr[dev] = p;
+  }
+  *out = g_device_ptr[dev];
+  return NGS_OK;
+}
+
+}  // namespace
+
+extern "C" NGS_API int ngs_render_backward_static(ngs_ctx* ctx, const ngs_frame* f, const ngs_gaussians* g,
+                                                  const float* dl_dimage, const ngs_grads* out, void* stream) {
+  using namespace ngs;
+  if (!ctx) return NGS_ERR_INVALID_ARG;
+  if (!f || f->ctx != ctx || !f->has_render) return fail(ctx, NGS_ERR_INVALID_ARG, "frame holds no render");
+  if (!g || !dl_dimage || !out) return fail(ctx, NGS_ERR_INVALID_ARG, "null argument");
+  if (g->n != f->n || g->sh_degree != f->rp.sh_degree)
+    return fail(ctx, NGS_ERR_INVALID_ARG, "Gaussians do not match the rendered frame");
+  if (g->n > kStaticMaxGaussians)
+    return fail(ctx, NGS_ERR_INVALID_ARG,
+                "ngs_render_backward_static handles at most 262144 Gaussians (static scratch of 12 MiB); "
+                "use ngs_render_backward for larger scenes");
+  if (g->n > 0 && (!out->d_means || !out->d_log_scales || !out->d_quats || !out->d_opacity_logits || !out->d_sh))
+    return fail(ctx, NGS_ERR_INVALID_ARG, "null gradient array");
+  void* scratch = nullptr;
+  int rc = static_scratch(ctx, &scratch);
+  if (rc != NGS_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t n = (size_t)f->n;
+  float4* grad2d = reinterpret_cast<float4*>(scratch);
+  cudaError_t e = cudaMemsetAsync(grad2d, 0, sizeof(float4) * 3 * n, s);
+  if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("clearing the scratch: ") + cudaGetErrorString(e));
+  launch_composite_backward(f->rec.as<float4>(), f->pvals[f->p_final].as<uint32_t>(), f->ranges.as<uint2>(), f->rp,
+                            f->W, f->H, dl_dimage, f->state.as<float4>(), grad2d, s);
+  launch_project_backward(*g, f->cam, f->rp, f->rec.as<float4>(), f->tile_count.as<uint32_t>(), grad2d, *out, s);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("backward launch: ") + cudaGetErrorString(e));
+  ctx->launches += n ? 2 : 1;
+  return NGS_OK;
+}
