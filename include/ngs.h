@@ -108,8 +108,12 @@ typedef struct {
   int64_t n_pairs;          /* number of (tile, Gaussian) pairs after binning                         */
   int32_t tiles_x, tiles_y;
   int32_t width, height;
-  const float* records;     /* [n][12] splat records: u, v, conic*k (3), log2 aleph, E (3), z, r, 0  */
-                            /*   with k = -log2(e)/2 folded into the conic                           */
+  float log2_alpha_min;     /* FP32 threshold of the alpha test on the exponent                       */
+  int32_t reserved;
+  const float* records;     /* [n][12] splat records: u, v, A', B', C', L, E0, E1, E2, z, rx, ry with  */
+                            /*   (A', B', C') = -log2(e)/2 (A, 2B, C) of the conic, L = log2 aleph, z  */
+                            /*   the FP32 view depth, (rx, ry) the half extents of the alpha >= alpha_min */
+                            /*   ellipse's bounding box (0: no tile)                                  */
   const uint64_t* keys;     /* [n_pairs] sorted keys (tile << 32) | bits(z)                           */
   const uint32_t* values;   /* [n_pairs] Gaussian index of each key                                   */
   const uint32_t* ranges;   /* [tiles][2] [start, end) of each tile's pairs                           */

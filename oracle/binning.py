@@ -2,71 +2,114 @@
 
 TEST INFRASTRUCTURE, like the rest of ``oracle/``.
 
-Input: FP32 splat records as the GPU wrote them (screen mean u, v, the conservative pixel radius r,
-and the FP32 view depth z; r <= 0 marks a splat that takes no tiles). The definition written out here:
+Input: FP32 splat records as the GPU wrote them: screen mean (u, v), the concave exponent
+q'(d) = A' dx^2 + B' dx dy + C' dy^2 (conic pre-scaled by -log2(e)/2), L = log2(aleph), the FP32 view
+depth z, and the half extents (rx, ry) of the bounding box of the ellipse where alpha >= alpha_min
+(rx <= 0 marks a splat that takes no tile). The definition written out here:
 
-* pixel (x, y) samples the image point (x + 1/2, y + 1/2); a splat can only reach pixels with
-  |p - (u, v)| <= r, so it covers tile column tx iff tx is in
-  [floor(((u - r) - 1/2) / tile_w), floor(((u + r) - 1/2) / tile_w)] (and likewise for rows), clipped to
-  the image's tile grid; every operation is one FP32 rounding, in this order (tile sizes are powers of
-  two, so the division is an exact multiply);
-* each covered tile t = ty * tiles_x + tx gives one pair (key, value) = ((t << 32) | bits(z), g);
-* pairs are emitted in Gaussian order (row-major over the rectangle), then sorted stably by key, so
-  equal keys keep Gaussian order. This is the front-to-back order of Sec. 3 within each tile.
+* pixel (x, y) samples the image point (x + 1/2, y + 1/2); the splat's bounding box covers tile column tx
+  iff tx is in [floor(((u - rx) - 1/2) / tile_w), floor(((u + rx) - 1/2) / tile_w)] (likewise for rows
+  with ry), clipped to the tile grid;
+* a tile of that box is covered iff the maximum of q' over the box of its pixel centres reaches
+  Tm = T' - (0.01 + 0.001 |T'|), T' = log2(alpha_min) - L. The maximum of a concave quadratic on a box is
+  0 if the box contains the mean, else it is the largest of the four edge maxima, each at the vertex of
+  the quadratic along that edge clamped to the edge. Boxes of more than 256 tiles are taken whole;
+* every operation is one FP32 rounding in a fixed order (tile sizes are powers of two, so the division by
+  the tile size is an exact multiply);
+* each covered tile t = ty * tiles_x + tx gives one pair (key, value) = ((t << 32) | bits(z), g), emitted
+  in Gaussian order and row-major over the box, then sorted stably by key, so equal keys keep Gaussian
+  order: the front-to-back order of Sec. 3 within each tile.
 """
 from __future__ import annotations
 
 import numpy as np
 
+F = np.float32
+MAX_TESTED = 256
 
-def tile_rects(u, v, r, tile_w, tile_h, width, height):
-    """Per splat: (x0, x1, y0, y1) inclusive tile bounds and the covered tile count (0 when empty)."""
-    u = np.asarray(u, np.float32)
-    v = np.asarray(v, np.float32)
-    r = np.asarray(r, np.float32)
+
+def tile_box(u, v, rx, ry, tile_w, tile_h, width, height):
+    """Per splat: (x0, x1, y0, y1) inclusive tile bounds of the bounding box and whether it is non-empty."""
+    u, v, rx, ry = (np.asarray(a, F) for a in (u, v, rx, ry))
     tiles_x = (width + tile_w - 1) // tile_w
     tiles_y = (height + tile_h - 1) // tile_h
-    half = np.float32(0.5)
-    itw = np.float32(1.0 / tile_w)
-    ith = np.float32(1.0 / tile_h)
+    half, itw, ith = F(0.5), F(1.0 / tile_w), F(1.0 / tile_h)
     with np.errstate(over="ignore", invalid="ignore"):
-        fx0 = np.floor(((u - r) - half) * itw)
-        fx1 = np.floor(((u + r) - half) * itw)
-        fy0 = np.floor(((v - r) - half) * ith)
-        fy1 = np.floor(((v + r) - half) * ith)
-    ok = (r > 0) & (fx1 >= 0) & (fx0 <= tiles_x - 1) & (fy1 >= 0) & (fy0 <= tiles_y - 1)
+        fx0 = np.floor(((u - rx) - half) * itw)
+        fx1 = np.floor(((u + rx) - half) * itw)
+        fy0 = np.floor(((v - ry) - half) * ith)
+        fy1 = np.floor(((v + ry) - half) * ith)
+    ok = (rx > 0) & (ry > 0) & (fx1 >= 0) & (fx0 <= tiles_x - 1) & (fy1 >= 0) & (fy0 <= tiles_y - 1)
     ok &= np.isfinite(fx0) & np.isfinite(fx1) & np.isfinite(fy0) & np.isfinite(fy1)
     x0 = np.where(ok, np.clip(fx0, 0, tiles_x - 1), 0).astype(np.int64)
     x1 = np.where(ok, np.clip(fx1, 0, tiles_x - 1), -1).astype(np.int64)
     y0 = np.where(ok, np.clip(fy0, 0, tiles_y - 1), 0).astype(np.int64)
     y1 = np.where(ok, np.clip(fy1, 0, tiles_y - 1), -1).astype(np.int64)
-    count = np.where(ok, (x1 - x0 + 1) * (y1 - y0 + 1), 0)
-    return x0, x1, y0, y1, count, tiles_x, tiles_y
+    return x0, x1, y0, y1, ok, tiles_x, tiles_y
 
 
-def sorted_pairs(u, v, r, z, tile_w, tile_h, width, height):
+def _edge_max(A, B, C, d, lo, hi):
+    """max over t in [lo, hi] of A d^2 + B d t + C t^2 (C < 0), FP32 operation by operation."""
+    Bd = F(B * d)
+    t = -F(Bd / F(F(2.0) * C))
+    t = min(max(t, lo), hi)
+    return F(F(F(F(A * d) * d) + F(Bd * t)) + F(F(C * t) * t))
+
+
+def tile_hit(rec_row, log2_amin, tx, ty, tile_w, tile_h):
+    u, v, A, B = (F(x) for x in rec_row[0:4])
+    C, L = F(rec_row[4]), F(rec_row[5])
+    Tp = F(F(log2_amin) - L)
+    Tm = F(Tp - F(F(0.01) + F(F(0.001) * abs(Tp))))
+    x0 = F(F(F(tx * tile_w) + F(0.5)) - u)
+    x1 = F(F(F(tx * tile_w + tile_w) - F(0.5)) - u)
+    y0 = F(F(F(ty * tile_h) + F(0.5)) - v)
+    y1 = F(F(F(ty * tile_h + tile_h) - F(0.5)) - v)
+    if x0 <= 0 and x1 >= 0 and y0 <= 0 and y1 >= 0:
+        return True
+    m = _edge_max(A, B, C, x0, y0, y1)
+    m = max(m, _edge_max(A, B, C, x1, y0, y1))
+    m = max(m, _edge_max(C, B, A, y0, x0, x1))
+    m = max(m, _edge_max(C, B, A, y1, x0, x1))
+    return bool(m >= Tm)
+
+
+def covered_tiles(rec, log2_amin, tile_w, tile_h, width, height):
+    """For each splat record [n, 12], the list of covered tile ids in emission order."""
+    rec = np.asarray(rec, F)
+    x0, x1, y0, y1, ok, tiles_x, tiles_y = tile_box(rec[:, 0], rec[:, 1], rec[:, 10], rec[:, 11], tile_w, tile_h,
+                                                     width, height)
+    out = []
+    with np.errstate(over="ignore", invalid="ignore"):
+        for g in range(rec.shape[0]):
+            tiles = []
+            if ok[g]:
+                box = (x1[g] - x0[g] + 1) * (y1[g] - y0[g] + 1)
+                for ty in range(y0[g], y1[g] + 1):
+                    for tx in range(x0[g], x1[g] + 1):
+                        if box > MAX_TESTED or tile_hit(rec[g], log2_amin, tx, ty, tile_w, tile_h):
+                            tiles.append(ty * tiles_x + tx)
+            out.append(tiles)
+    return out, tiles_x, tiles_y
+
+
+def sorted_pairs(rec, log2_amin, tile_w, tile_h, width, height):
     """Expected (keys uint64, values uint32, tile ranges [tiles, 2]) after binning and the stable sort."""
-    x0, x1, y0, y1, count, tiles_x, tiles_y = tile_rects(u, v, r, tile_w, tile_h, width, height)
-    zbits = np.asarray(z, np.float32).view(np.uint32).astype(np.uint64)
-    total = int(count.sum())
-    keys = np.empty(total, np.uint64)
-    vals = np.empty(total, np.uint32)
-    pos = 0
-    for g in np.nonzero(count)[0]:
-        ty, tx = np.meshgrid(np.arange(y0[g], y1[g] + 1), np.arange(x0[g], x1[g] + 1), indexing="ij")
-        t = (ty * tiles_x + tx).reshape(-1).astype(np.uint64)
-        c = t.shape[0]
-        keys[pos:pos + c] = (t << np.uint64(32)) | zbits[g]
-        vals[pos:pos + c] = g
-        pos += c
+    rec = np.asarray(rec, F)
+    tiles, tiles_x, tiles_y = covered_tiles(rec, log2_amin, tile_w, tile_h, width, height)
+    zbits = rec[:, 9].view(np.uint32).astype(np.uint64)
+    keys = [((np.uint64(t) << np.uint64(32)) | zbits[g]) for g, ts in enumerate(tiles) for t in ts]
+    vals = [g for g, ts in enumerate(tiles) for _ in ts]
+    keys = np.array(keys, np.uint64)
+    vals = np.array(vals, np.uint32)
     order = np.argsort(keys, kind="stable")
     keys, vals = keys[order], vals[order]
     ntiles = tiles_x * tiles_y
-    tiles = (keys >> np.uint64(32)).astype(np.int64)
+    tile_of = (keys >> np.uint64(32)).astype(np.int64)
     ranges = np.zeros((ntiles, 2), np.int64)
-    if total:
-        starts = np.searchsorted(tiles, np.arange(ntiles), side="left")
-        ends = np.searchsorted(tiles, np.arange(ntiles), side="right")
+    if len(keys):
+        starts = np.searchsorted(tile_of, np.arange(ntiles), side="left")
+        ends = np.searchsorted(tile_of, np.arange(ntiles), side="right")
         ranges[:, 0] = np.where(ends > starts, starts, 0)
         ranges[:, 1] = np.where(ends > starts, ends, 0)
     return keys, vals, ranges

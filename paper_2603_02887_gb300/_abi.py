@@ -48,7 +48,8 @@ class Grads(C.Structure):
 
 class FrameView(C.Structure):
     _fields_ = [("n_gaussians", C.c_int64), ("n_pairs", C.c_int64), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32),
-                ("width", C.c_int32), ("height", C.c_int32), ("records", C.c_void_p), ("keys", C.c_void_p),
+                ("width", C.c_int32), ("height", C.c_int32), ("log2_alpha_min", C.c_float), ("reserved", C.c_int32),
+                ("records", C.c_void_p), ("keys", C.c_void_p),
                 ("values", C.c_void_p), ("ranges", C.c_void_p), ("pixel_state", C.c_void_p)]
 
 

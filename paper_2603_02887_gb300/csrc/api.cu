@@ -360,6 +360,7 @@ NGS_API int ngs_frame_view_get(const ngs_frame* f, ngs_frame_view* out) {
   out->tiles_y = f->rp.tiles_y;
   out->width = f->W;
   out->height = f->H;
+  out->log2_alpha_min = f->rp.log2_alpha_min;
   out->records = f->rec.as<float>();
   out->keys = f->pkeys[f->p_final].as<uint64_t>();
   out->values = f->pvals[f->p_final].as<uint32_t>();

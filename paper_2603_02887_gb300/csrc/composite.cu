@@ -18,7 +18,7 @@
 //                dL0/dE_i = pbar_i; dL0/dalpha_k = 0;
 //   exponential: dL0/dalpha_i = T_i E_i - R_i / (1 - alpha_i), R_i = L0 - sum_{j<=i} E_j pbar_j;
 // then the chain through alpha_i = 2^(L + q'(p)) to the splat record, a warp-shuffle reduction over the
-// warp's pixels and one vector atomicAdd per warp and splat into the per-Gaussian gradient buffer.
+// warp's pixels and one atomic-add instruction per warp and splat into the per-Gaussian gradient buffer.
 #include "ngs_internal.cuh"
 
 namespace ngs {
@@ -152,10 +152,38 @@ __global__ void __launch_bounds__(TW* TH) composite_forward_kernel(const float4*
   }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Sum nine per-lane values over the warp and add the totals to dst[0..8] with one atomic instruction.
+// Values 0..7 go through a transposing butterfly: at each of three steps a lane keeps half of the values
+// it carries and sends the other half to its partner, so after xor 16, 8, 4 (and two plain xor 2, 1
+// steps) lane l holds the warp total of value ((l >> 2) & 7). Value 8 uses an ordinary tree.
+// 21 shuffles + 21 adds instead of 45 + 45.
+__device__ __forceinline__ void warp_reduce9_add(const float (&v)[9], float* dst, int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  float w[4];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
+  for (int p = 0; p < 4; ++p) {
+    float send = b4 ? v[p] : v[p + 4];
+    float keep = b4 ? v[p + 4] : v[p];
+    w[p] = keep + __shfl_xor_sync(kFull, send, 16);
+  }
+  float x[2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    float send = b3 ? w[p] : w[p + 2];
+    float keep = b3 ? w[p + 2] : w[p];
+    x[p] = keep + __shfl_xor_sync(kFull, send, 8);
+  }
+  float send = b2 ? x[0] : x[1];
+  float y = (b2 ? x[1] : x[0]) + __shfl_xor_sync(kFull, send, 4);
+  y += __shfl_xor_sync(kFull, y, 2);
+  y += __shfl_xor_sync(kFull, y, 1);
+  float e = v[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(kFull, e, o);
+  if ((lane & 3) == 0)
+    atomicAdd(dst + ((lane >> 2) & 7), y);
+  else if (lane == 1)
+    atomicAdd(dst + 8, e);
 }
 
 template <int TW, int TH, int KIND>
@@ -206,6 +234,8 @@ __global__ void __launch_bounds__(TW* TH) composite_backward_kernel(const float4
   (void)sat;
   float S = 0.f, tau = 0.f, T = 1.f, acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
   const float amax = rp.alpha_max, l2min = rp.log2_alpha_min, c = rp.c;
+  // the warp walks entries up to the largest stop of its lanes
+  const uint32_t warp_last = __reduce_max_sync(kFull, last);
   for (uint32_t base = range.x; base < range.y; base += B) {
     bool done = base >= last;
     if (__syncthreads_count(done) == B) break;
@@ -218,11 +248,10 @@ __global__ void __launch_bounds__(TW* TH) composite_backward_kernel(const float4
       s_e2[tid] = rec[3 * (size_t)id + 2].x;
     }
     __syncthreads();
-    int cnt = (int)min((uint32_t)B, range.y - base);
-    if (__any_sync(kFull, !done)) {
+    if (base < warp_last) {
+      int cnt = (int)(min(warp_last, min(base + (uint32_t)B, range.y)) - base);
       for (int j = 0; j < cnt; ++j) {
         uint32_t pos = base + j;
-        if (!__any_sync(kFull, pos < last)) break;
         float4 r0 = s_r0[j], r1 = s_r1[j];
         float dx, dy;
         float e = splat_log2_alpha(px, py, r0, r1, dx, dy);
@@ -280,21 +309,8 @@ __global__ void __launch_bounds__(TW* TH) composite_backward_kernel(const float4
           gv = -wgt * fmaf(r0.w, dx, 2.f * r1.x * dy);
         }
         if (__any_sync(kFull, on)) {
-          gu = warp_sum(gu);
-          gv = warp_sum(gv);
-          gA = warp_sum(gA);
-          gB = warp_sum(gB);
-          gC = warp_sum(gC);
-          gL = warp_sum(gL);
-          gE0 = warp_sum(gE0);
-          gE1 = warp_sum(gE1);
-          gE2 = warp_sum(gE2);
-          if (lane == 0) {
-            float4* dst = grad2d + 3 * (size_t)s_id[j];
-            atomicAdd(dst, make_float4(gu, gv, gA, gB));
-            atomicAdd(dst + 1, make_float4(gC, gL, gE0, gE1));
-            atomicAdd(reinterpret_cast<float*>(dst + 2), gE2);
-          }
+          const float v[9] = {gu, gv, gA, gB, gC, gL, gE0, gE1, gE2};
+          warp_reduce9_add(v, reinterpret_cast<float*>(grad2d + 3 * (size_t)s_id[j]), lane);
         }
       }
     }

@@ -33,10 +33,11 @@ struct RenderParams {
 };
 
 // Splat record: 3 float4 per Gaussian.
-//   r0 = (u, v, A', B'), r1 = (C', L, E0, E1), r2 = (E2, z, r, 0)
+//   r0 = (u, v, A', B'), r1 = (C', L, E0, E1), r2 = (E2, z, rx, ry)
 // with (u, v) the screen mean, (A, B, C) the conic (inverse 2D covariance), k = -log2(e)/2,
 // A' = k A, B' = 2 k B, C' = k C, L = log2(aleph), so that log2(aleph K(p)) = L + dx (A' dx + B' dy) + C' dy^2.
-// z is the FP32 view depth (the sort key), r the conservative pixel radius (0: the splat takes no tile).
+// z is the FP32 view depth (the sort key); (rx, ry) are conservative half extents of the bounding box of the
+// ellipse where alpha >= alpha_min (0: the splat takes no tile).
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kConicScale = -0.5f * 1.4426950408889634f;

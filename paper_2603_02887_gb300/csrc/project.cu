@@ -112,7 +112,9 @@ __device__ __forceinline__ void quat_to_rot(float w, float x, float y, float z, 
 }
 
 // Everything the forward map computes that the backward needs again.
+template <int DEG>
 struct ProjState {
+  static constexpr int K = (DEG + 1) * (DEG + 1);
   float x, y, z, iz;       // view-space mean, 1/z
   float qn[4], qnorm;      // normalised quaternion and the raw norm
   float Rq[9], S[3];       // rotation and scales
@@ -124,11 +126,13 @@ struct ProjState {
   float aleph;
   float dir[3], dnorm;     // unit direction from the camera centre, |p - campos|
   float e[3];              // unclamped emission
-  float Y[16];
+  float Y[K];
 };
 
+template <int DEG>
 __device__ __forceinline__ void forward_map(const ngs_gaussians& g, const CamParams& cam, const RenderParams& rp,
-                                            int i, ProjState& st) {
+                                            int i, ProjState<DEG>& st) {
+  constexpr int K = ProjState<DEG>::K;
   const float* m = g.means + 3 * (int64_t)i;
   float px = m[0], py = m[1], pz = m[2];
   st.x = cam.R[0] * px + cam.R[1] * py + cam.R[2] * pz + cam.t[0];
@@ -138,22 +142,30 @@ __device__ __forceinline__ void forward_map(const ngs_gaussians& g, const CamPar
   const float* q = g.quats + 4 * (int64_t)i;
   st.qnorm = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
   float inv = 1.f / st.qnorm;
+#pragma unroll
   for (int k = 0; k < 4; ++k) st.qn[k] = q[k] * inv;
   quat_to_rot(st.qn[0], st.qn[1], st.qn[2], st.qn[3], st.Rq);
   const float* ls = g.log_scales + 3 * (int64_t)i;
+#pragma unroll
   for (int k = 0; k < 3; ++k) st.S[k] = expf(ls[k]);
+#pragma unroll
   for (int r = 0; r < 3; ++r)
+#pragma unroll
     for (int c = 0; c < 3; ++c) st.M[3 * r + c] = st.Rq[3 * r + c] * st.S[c];
+#pragma unroll
   for (int r = 0; r < 3; ++r)
+#pragma unroll
     for (int c = 0; c < 3; ++c)
       st.Sig[3 * r + c] = st.M[3 * r] * st.M[3 * c] + st.M[3 * r + 1] * st.M[3 * c + 1] + st.M[3 * r + 2] * st.M[3 * c + 2];
   float j00 = cam.fx * st.iz, j02 = -cam.fx * st.x * st.iz * st.iz;
   float j11 = cam.fy * st.iz, j12 = -cam.fy * st.y * st.iz * st.iz;
+#pragma unroll
   for (int c = 0; c < 3; ++c) {
     st.T[c] = j00 * cam.R[c] + j02 * cam.R[6 + c];
     st.T[3 + c] = j11 * cam.R[3 + c] + j12 * cam.R[6 + c];
   }
   float TS0[3], TS1[3];
+#pragma unroll
   for (int c = 0; c < 3; ++c) {
     TS0[c] = st.T[0] * st.Sig[c] + st.T[1] * st.Sig[3 + c] + st.T[2] * st.Sig[6 + c];
     TS1[c] = st.T[3] * st.Sig[c] + st.T[4] * st.Sig[3 + c] + st.T[5] * st.Sig[6 + c];
@@ -173,25 +185,79 @@ __device__ __forceinline__ void forward_map(const ngs_gaussians& g, const CamPar
   st.dir[0] = d0 * idn;
   st.dir[1] = d1 * idn;
   st.dir[2] = d2 * idn;
-  int K = (rp.sh_degree + 1) * (rp.sh_degree + 1);
-  sh_basis(rp.sh_degree, st.dir[0], st.dir[1], st.dir[2], st.Y);
+  sh_basis(DEG, st.dir[0], st.dir[1], st.dir[2], st.Y);
   const float* sh = g.sh + (int64_t)i * K * 3;
-  for (int ch = 0; ch < 3; ++ch) {
-    float e = 0.5f;
-    for (int k = 0; k < K; ++k) e += st.Y[k] * sh[3 * k + ch];
-    st.e[ch] = e;
+  float e0 = 0.5f, e1 = 0.5f, e2 = 0.5f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    e0 += st.Y[k] * sh[3 * k];
+    e1 += st.Y[k] * sh[3 * k + 1];
+    e2 += st.Y[k] * sh[3 * k + 2];
   }
+  st.e[0] = e0;
+  st.e[1] = e1;
+  st.e[2] = e2;
 }
 
-// Tile rectangle of a splat (u, v, r): identical arithmetic in the projection and the key emission.
-__device__ __forceinline__ bool tile_rect(float u, float v, float r, const RenderParams& rp, int& x0, int& x1,
-                                          int& y0, int& y1) {
+// ---- tile binning --------------------------------------------------------------------------------
+// A splat reaches pixel p iff L + q'(p - mu) >= log2(alpha_min) with the concave q' of the record
+// (the compositing kernels' test). Its tiles are those of the bounding box of that ellipse (half
+// extents rx, ry from the record) for which the maximum of q' over the tile's box of pixel centres
+// reaches T' - margin, T' = log2(alpha_min) - L. The maximum of a concave quadratic over a box is 0
+// at the mean if the box contains it, else it lies on an edge, at the clamped vertex of the quadratic
+// along that edge. Every operation is one FP32 rounding in a fixed order, so the count (projection)
+// and the emission agree, and so does the tile-binning oracle. Boxes of more than kMaxTested tiles
+// are taken whole.
+constexpr int kMaxTested = 256;
+
+struct SplatBin {
+  float u, v, A, B, C, Tm, rx, ry;
+};
+
+__device__ __forceinline__ SplatBin splat_bin(float4 r0, float4 r1, float4 r2, float log2_amin) {
+  SplatBin b;
+  b.u = r0.x;
+  b.v = r0.y;
+  b.A = r0.z;
+  b.B = r0.w;
+  b.C = r1.x;
+  float Tp = __fsub_rn(log2_amin, r1.y);
+  b.Tm = __fsub_rn(Tp, __fadd_rn(0.01f, __fmul_rn(0.001f, fabsf(Tp))));
+  b.rx = r2.z;
+  b.ry = r2.w;
+  return b;
+}
+
+// max over t in [lo, hi] of q'(d, t) = A d^2 + B d t + C t^2 (d fixed; C < 0)
+__device__ __forceinline__ float edge_max(float A, float B, float C, float d, float lo, float hi) {
+  float Bd = __fmul_rn(B, d);
+  float t = -__fdiv_rn(Bd, __fmul_rn(2.0f, C));
+  t = fminf(fmaxf(t, lo), hi);
+  return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, d), d), __fmul_rn(Bd, t)), __fmul_rn(__fmul_rn(C, t), t));
+}
+
+__device__ __forceinline__ bool tile_hit(const SplatBin& b, const RenderParams& rp, int tx, int ty) {
+  float x0 = __fsub_rn((float)(tx * rp.tile_w) + 0.5f, b.u);
+  float x1 = __fsub_rn((float)(tx * rp.tile_w + rp.tile_w) - 0.5f, b.u);
+  float y0 = __fsub_rn((float)(ty * rp.tile_h) + 0.5f, b.v);
+  float y1 = __fsub_rn((float)(ty * rp.tile_h + rp.tile_h) - 0.5f, b.v);
+  if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return true;
+  float m = edge_max(b.A, b.B, b.C, x0, y0, y1);               // left edge: dx fixed, maximise over dy
+  m = fmaxf(m, edge_max(b.A, b.B, b.C, x1, y0, y1));           // right edge
+  m = fmaxf(m, edge_max(b.C, b.B, b.A, y0, x0, x1));           // top edge: dy fixed, maximise over dx
+  m = fmaxf(m, edge_max(b.C, b.B, b.A, y1, x0, x1));           // bottom edge
+  return m >= b.Tm;
+}
+
+// Tile bounding box of the splat (u, v) with half extents (rx, ry): identical arithmetic everywhere.
+__device__ __forceinline__ bool tile_rect(float u, float v, float rx, float ry, const RenderParams& rp, int& x0,
+                                          int& x1, int& y0, int& y1) {
   float itw = 1.0f / (float)rp.tile_w, ith = 1.0f / (float)rp.tile_h;  // powers of two: exact
-  float fx0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(u, r), 0.5f), itw));
-  float fx1 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(u, r), 0.5f), itw));
-  float fy0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(v, r), 0.5f), ith));
-  float fy1 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(v, r), 0.5f), ith));
-  bool ok = r > 0.f && fx1 >= 0.f && fx0 <= (float)(rp.tiles_x - 1) && fy1 >= 0.f &&
+  float fx0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(u, rx), 0.5f), itw));
+  float fx1 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(u, rx), 0.5f), itw));
+  float fy0 = floorf(__fmul_rn(__fsub_rn(__fsub_rn(v, ry), 0.5f), ith));
+  float fy1 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(v, ry), 0.5f), ith));
+  bool ok = rx > 0.f && ry > 0.f && fx1 >= 0.f && fx0 <= (float)(rp.tiles_x - 1) && fy1 >= 0.f &&
             fy0 <= (float)(rp.tiles_y - 1) && isfinite(fx0) && isfinite(fx1) && isfinite(fy0) && isfinite(fy1);
   if (!ok) return false;
   x0 = (int)fmaxf(fx0, 0.f);
@@ -201,6 +267,18 @@ __device__ __forceinline__ bool tile_rect(float u, float v, float r, const Rende
   return true;
 }
 
+__device__ __forceinline__ uint32_t count_tiles(const SplatBin& b, const RenderParams& rp) {
+  int x0, x1, y0, y1;
+  if (!tile_rect(b.u, b.v, b.rx, b.ry, rp, x0, x1, y0, y1)) return 0;
+  uint32_t box = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+  if (box > (uint32_t)kMaxTested) return box;
+  uint32_t c = 0;
+  for (int ty = y0; ty <= y1; ++ty)
+    for (int tx = x0; tx <= x1; ++tx) c += tile_hit(b, rp, tx, ty) ? 1u : 0u;
+  return c;
+}
+
+template <int DEG>
 __global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, CamParams cam, RenderParams rp, float4* rec,
                                                       uint32_t* depth_key, uint32_t* tile_count, uint32_t* order) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -210,25 +288,24 @@ __global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, CamParams
   float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = make_float4(0.f, z, 0.f, 0.f);
   uint32_t count = 0;
   if (z > rp.near_plane) {
-    ProjState st;
-    forward_map(g, cam, rp, i, st);
+    ProjState<DEG> st;
+    forward_map<DEG>(g, cam, rp, i, st);
     float det = st.s00 * st.s11 - st.s01 * st.s01;
     if (det > 0.f && st.aleph >= rp.alpha_min && isfinite(st.A) && isfinite(st.C)) {
       float u = cam.fx * st.x * st.iz + cam.cx;
       float v = cam.fy * st.y * st.iz + cam.cy;
       float L = log2f(st.aleph);
-      float ha = 0.5f * (st.s00 + st.s11), hd = 0.5f * (st.s00 - st.s11);
-      float lam = ha + sqrtf(hd * hd + st.s01 * st.s01);
-      // alpha >= alpha_min needs d^T conic d <= 2 ln(aleph/alpha_min), hence |d|^2 <= 2 ln(.) lambda_max;
-      // the radius is widened by a relative 1e-4 and one pixel so that FP32 rounding never cuts a pixel
-      float r = sqrtf(fmaxf(2.f * kLn2 * (L - rp.log2_alpha_min), 0.f) * lam) * 1.0001f + 1.0f;
-      float E[3];
-      for (int ch = 0; ch < 3; ++ch) E[ch] = fmaxf(st.e[ch], 0.f);
+      // alpha >= alpha_min needs d^T conic d <= tau = 2 ln(aleph/alpha_min): an ellipse whose bounding box
+      // has half extents sqrt(tau s00), sqrt(tau s11); widened by 1e-4 relative and one pixel so that FP32
+      // rounding never cuts a pixel
+      float tau = fmaxf(2.f * kLn2 * (L - rp.log2_alpha_min), 0.f);
+      float rx = sqrtf(tau * st.s00) * 1.0001f + 1.0f;
+      float ry = sqrtf(tau * st.s11) * 1.0001f + 1.0f;
+      float E0 = fmaxf(st.e[0], 0.f), E1 = fmaxf(st.e[1], 0.f), E2 = fmaxf(st.e[2], 0.f);
       r0 = make_float4(u, v, kConicScale * st.A, 2.f * kConicScale * st.B);
-      r1 = make_float4(kConicScale * st.C, L, E[0], E[1]);
-      r2 = make_float4(E[2], z, r, 0.f);
-      int x0, x1, y0, y1;
-      if (tile_rect(u, v, r, rp, x0, x1, y0, y1)) count = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+      r1 = make_float4(kConicScale * st.C, L, E0, E1);
+      r2 = make_float4(E2, z, rx, ry);
+      count = count_tiles(splat_bin(r0, r1, r2, rp.log2_alpha_min), rp);
     }
   }
   rec[3 * (int64_t)i] = r0;
@@ -247,13 +324,15 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const float4* rec, const
   uint32_t off = offsets[s], end = offsets[s + 1];
   if (off == end) return;
   uint32_t id = order[s];
-  float4 r0 = rec[3 * (int64_t)id];
-  float4 r2 = rec[3 * (int64_t)id + 2];
+  float4 r0 = rec[3 * (int64_t)id], r1 = rec[3 * (int64_t)id + 1], r2 = rec[3 * (int64_t)id + 2];
+  SplatBin b = splat_bin(r0, r1, r2, rp.log2_alpha_min);
   int x0, x1, y0, y1;
-  if (!tile_rect(r0.x, r0.y, r2.z, rp, x0, x1, y0, y1)) return;
+  if (!tile_rect(b.u, b.v, b.rx, b.ry, rp, x0, x1, y0, y1)) return;
+  bool test = (x1 - x0 + 1) * (y1 - y0 + 1) <= kMaxTested;
   uint64_t zb = (uint64_t)__float_as_uint(r2.y);
-  for (int ty = y0; ty <= y1; ++ty)
+  for (int ty = y0; ty <= y1 && off < end; ++ty)
     for (int tx = x0; tx <= x1 && off < end; ++tx) {
+      if (test && !tile_hit(b, rp, tx, ty)) continue;
       uint64_t tile = (uint64_t)(ty * rp.tiles_x + tx);
       keys[off] = (tile << 32) | zb;
       vals[off] = id;
@@ -261,26 +340,30 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const float4* rec, const
     }
 }
 
+template <int DEG>
 __global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, CamParams cam, RenderParams rp,
                                                                const uint32_t* tile_count, const float4* grad2d,
                                                                ngs_grads out) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
-  int K = (rp.sh_degree + 1) * (rp.sh_degree + 1);
   float* dm = out.d_means + 3 * (int64_t)i;
   float* dls = out.d_log_scales + 3 * (int64_t)i;
   float* dq = out.d_quats + 4 * (int64_t)i;
   float* dsh = out.d_sh + (int64_t)i * K * 3;
   if (tile_count[i] == 0) {
+#pragma unroll
     for (int k = 0; k < 3; ++k) dm[k] = dls[k] = 0.f;
+#pragma unroll
     for (int k = 0; k < 4; ++k) dq[k] = 0.f;
     out.d_opacity_logits[i] = 0.f;
+#pragma unroll
     for (int k = 0; k < 3 * K; ++k) dsh[k] = 0.f;
     return;
   }
   float4 g0 = grad2d[3 * (int64_t)i], g1 = grad2d[3 * (int64_t)i + 1], g2 = grad2d[3 * (int64_t)i + 2];
-  ProjState st;
-  forward_map(g, cam, rp, i, st);
+  ProjState<DEG> st;
+  forward_map<DEG>(g, cam, rp, i, st);
   // record -> natural quantities
   float du = g0.x, dv = g0.y;
   float dA = g0.z * kConicScale, dB = g0.w * 2.f * kConicScale, dC = g1.x * kConicScale;
@@ -295,18 +378,26 @@ __global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, 
   float H[4] = {H00, H01, H01, H11};
   // Sigma2 = T Sig T^T: dSig = T^T H T, dT = 2 H T Sig
   float dSig[9];
+#pragma unroll
   for (int r = 0; r < 3; ++r)
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
       float acc = 0.f;
+#pragma unroll
       for (int a = 0; a < 2; ++a)
+#pragma unroll
         for (int b = 0; b < 2; ++b) acc += st.T[3 * a + r] * H[2 * a + b] * st.T[3 * b + c];
       dSig[3 * r + c] = acc;
     }
   float HT[6];
+#pragma unroll
   for (int a = 0; a < 2; ++a)
+#pragma unroll
     for (int c = 0; c < 3; ++c) HT[3 * a + c] = H[2 * a] * st.T[c] + H[2 * a + 1] * st.T[3 + c];
   float dT[6];
+#pragma unroll
   for (int a = 0; a < 2; ++a)
+#pragma unroll
     for (int c = 0; c < 3; ++c)
       dT[3 * a + c] = 2.f * (HT[3 * a] * st.Sig[c] + HT[3 * a + 1] * st.Sig[3 + c] + HT[3 * a + 2] * st.Sig[6 + c]);
   // T = J W: dJ = dT W^T (only the four nonzero entries of J)
@@ -320,15 +411,19 @@ __global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, 
   float dvz = -du * cam.fx * st.x * iz2 - dv * cam.fy * st.y * iz2 - dJ00 * cam.fx * iz2 +
               dJ02 * 2.f * cam.fx * st.x * iz3 - dJ11 * cam.fy * iz2 + dJ12 * 2.f * cam.fy * st.y * iz3;
   float gm[3];
+#pragma unroll
   for (int c = 0; c < 3; ++c) gm[c] = cam.R[c] * dvx + cam.R[3 + c] * dvy + cam.R[6 + c] * dvz;
   // Sig = M M^T: dM = 2 dSig M; M = Rq diag(S)
   float dRq[9], dS[3] = {0.f, 0.f, 0.f};
+#pragma unroll
   for (int r = 0; r < 3; ++r)
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
       float dMrc = 2.f * (dSig[3 * r] * st.M[c] + dSig[3 * r + 1] * st.M[3 + c] + dSig[3 * r + 2] * st.M[6 + c]);
       dRq[3 * r + c] = dMrc * st.S[c];
       dS[c] += dMrc * st.Rq[3 * r + c];
     }
+#pragma unroll
   for (int c = 0; c < 3; ++c) dls[c] = dS[c] * st.S[c];
   // rotation matrix of the unit quaternion (w, a, b, c)
   float w = st.qn[0], a = st.qn[1], b = st.qn[2], c = st.qn[3];
@@ -339,25 +434,30 @@ __global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, 
   dqn[2] = 2.f * (-2.f * b * D[0] + a * D[1] + w * D[2] + a * D[3] + c * D[5] - w * D[6] + c * D[7] - 2.f * b * D[8]);
   dqn[3] = 2.f * (-2.f * c * D[0] - w * D[1] + a * D[2] + w * D[3] - 2.f * c * D[4] + b * D[5] + a * D[6] + b * D[7]);
   float dot = st.qn[0] * dqn[0] + st.qn[1] * dqn[1] + st.qn[2] * dqn[2] + st.qn[3] * dqn[3];
-  for (int k = 0; k < 4; ++k) dq[k] = (dqn[k] - st.qn[k] * dot) / st.qnorm;
+  float iq = 1.f / st.qnorm;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) dq[k] = (dqn[k] - st.qn[k] * dot) * iq;
   // emission: dE/dsh = Y (unclamped channels); direction term into the mean
   const float* sh = g.sh + (int64_t)i * K * 3;
-  float wk[16];
-  for (int k = 0; k < K; ++k) wk[k] = 0.f;
-  for (int ch = 0; ch < 3; ++ch) {
-    float d = st.e[ch] < 0.f ? 0.f : dE[ch];
-    for (int k = 0; k < K; ++k) {
-      dsh[3 * k + ch] = d * st.Y[k];
-      wk[k] += d * sh[3 * k + ch];
-    }
+  float d0 = st.e[0] < 0.f ? 0.f : dE[0];
+  float d1 = st.e[1] < 0.f ? 0.f : dE[1];
+  float d2 = st.e[2] < 0.f ? 0.f : dE[2];
+  float wk[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    dsh[3 * k] = d0 * st.Y[k];
+    dsh[3 * k + 1] = d1 * st.Y[k];
+    dsh[3 * k + 2] = d2 * st.Y[k];
+    wk[k] = d0 * sh[3 * k] + d1 * sh[3 * k + 1] + d2 * sh[3 * k + 2];
   }
   float gdx, gdy, gdz;
-  sh_basis_grad(rp.sh_degree, st.dir[0], st.dir[1], st.dir[2], wk, gdx, gdy, gdz);
+  sh_basis_grad(DEG, st.dir[0], st.dir[1], st.dir[2], wk, gdx, gdy, gdz);
   float rad = st.dir[0] * gdx + st.dir[1] * gdy + st.dir[2] * gdz;
   float idn = 1.f / st.dnorm;
   gm[0] += (gdx - st.dir[0] * rad) * idn;
   gm[1] += (gdy - st.dir[1] * rad) * idn;
   gm[2] += (gdz - st.dir[2] * rad) * idn;
+#pragma unroll
   for (int k = 0; k < 3; ++k) dm[k] = gm[k];
 }
 
@@ -367,7 +467,12 @@ void launch_project(const ngs_gaussians& g, const CamParams& cam, const RenderPa
                     uint32_t* depth_key, uint32_t* tile_count, uint32_t* order, cudaStream_t s) {
   if (g.n == 0) return;
   int blocks = (int)((g.n + 255) / 256);
-  project_kernel<<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order);
+  switch (rp.sh_degree) {
+    case 0: project_kernel<0><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order); break;
+    case 1: project_kernel<1><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order); break;
+    case 2: project_kernel<2><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order); break;
+    default: project_kernel<3><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order); break;
+  }
 }
 
 void launch_emit_keys(const float4* rec, const uint32_t* order, const uint32_t* offsets, uint32_t n,
@@ -381,7 +486,12 @@ void launch_project_backward(const ngs_gaussians& g, const CamParams& cam, const
                              cudaStream_t s) {
   if (g.n == 0) return;
   int blocks = (int)((g.n + 127) / 128);
-  project_backward_kernel<<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out);
+  switch (rp.sh_degree) {
+    case 0: project_backward_kernel<0><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out); break;
+    case 1: project_backward_kernel<1><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out); break;
+    case 2: project_backward_kernel<2><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out); break;
+    default: project_backward_kernel<3><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out); break;
+  }
 }
 
 }  // namespace ngs

@@ -36,7 +36,8 @@ def rnd():
 
 def _records_to_oracle_layout(rec):
     return dict(u=rec[:, 0], v=rec[:, 1], A=rec[:, 2] / KC, B=rec[:, 3] / (2 * KC), C=rec[:, 4] / KC,
-                aleph=np.exp2(rec[:, 5].astype(np.float64)), E=rec[:, [6, 7, 8]], z=rec[:, 9], r=rec[:, 10])
+                aleph=np.exp2(rec[:, 5].astype(np.float64)), E=rec[:, [6, 7, 8]], z=rec[:, 9], rx=rec[:, 10],
+                ry=rec[:, 11])
 
 
 @pytest.mark.parametrize("which", ["tiny", "clustered"])
@@ -61,7 +62,11 @@ def test_projection_matches_oracle(rnd, which):
     np.testing.assert_allclose(g["aleph"][live], rr[:, 5], rtol=2e-6)
     np.testing.assert_allclose(g["E"][live], rr[:, 6:9], atol=2e-5)
     assert np.array_equal(g["z"], ref["z32"]), "FP32 sort depth must be bit-identical"
-    assert np.all(g["r"][live] >= rr[:, 9]), "the pixel radius must be conservative"
+    # the bounding box of the alpha >= alpha_min ellipse: half extents sqrt(tau Sigma'_xx), sqrt(tau Sigma'_yy)
+    det = rr[:, 2] * rr[:, 4] - rr[:, 3] ** 2
+    tau = 2 * np.log(rr[:, 5] / np.float32(1 / 255.0))
+    assert np.all(g["rx"][live] >= np.sqrt(tau * rr[:, 4] / det)), "bounding box must be conservative"
+    assert np.all(g["ry"][live] >= np.sqrt(tau * rr[:, 2] / det)), "bounding box must be conservative"
 
 
 @pytest.mark.parametrize("tile", [(8, 8), (16, 16), (16, 32)])
@@ -70,8 +75,7 @@ def test_binning_keys_bit_exact(rnd, tile):
     params = upload(scene)
     _, _, frame = rnd.render(params, cam, "exp", options=dict(tile_w=tile[0], tile_h=tile[1]))
     fa = frame_arrays(frame)
-    rec = fa["records"]
-    keys, vals, ranges = binning.sorted_pairs(rec[:, 0], rec[:, 1], rec[:, 10], rec[:, 9], tile[0], tile[1],
+    keys, vals, ranges = binning.sorted_pairs(fa["records"], fa["view"]["log2_alpha_min"], tile[0], tile[1],
                                               cam["width"], cam["height"])
     assert fa["view"]["n_pairs"] == len(keys)
     assert np.array_equal(fa["keys"], keys)
