@@ -10,22 +10,23 @@ depth z, and the half extents (rx, ry) of the bounding box of the ellipse where 
 * pixel (x, y) samples the image point (x + 1/2, y + 1/2); the splat's bounding box covers tile column tx
   iff tx is in [floor(((u - rx) - 1/2) / tile_w), floor(((u + rx) - 1/2) / tile_w)] (likewise for rows
   with ry), clipped to the tile grid;
-* a tile of that box is covered iff the maximum of q' over the box of its pixel centres reaches
-  Tm = T' - (0.01 + 0.001 |T'|), T' = log2(alpha_min) - L. The maximum of a concave quadratic on a box is
-  0 if the box contains the mean, else it is the largest of the four edge maxima, each at the vertex of
-  the quadratic along that edge clamped to the edge. Boxes of more than 256 tiles are taken whole;
+* binning keeps the ellipse q'(d) >= Tm = T' - (0.01 + 0.001 |T'|), T' = log2(alpha_min) - L. Within tile
+  row ty of the box, the row's band of pixel centres is dy in [ty h + 1/2 - v, ty h + h - 1/2 - v],
+  clipped to the ellipse's half height; over it the ellipse reaches x from its left boundary at the
+  clamped height of its leftmost point to its right boundary at the clamped height of its rightmost point
+  (the right boundary is concave in dy, the left convex); the row's tiles are the columns that x-range
+  reaches, clipped to the box;
 * every operation is one FP32 rounding in a fixed order (tile sizes are powers of two, so the division by
   the tile size is an exact multiply);
 * each covered tile t = ty * tiles_x + tx gives one pair (key, value) = ((t << 32) | bits(z), g), emitted
-  in Gaussian order and row-major over the box, then sorted stably by key, so equal keys keep Gaussian
-  order: the front-to-back order of Sec. 3 within each tile.
+  in Gaussian order, then sorted stably by key, so equal keys keep Gaussian order: the front-to-back order
+  of Sec. 3 within each tile.
 """
 from __future__ import annotations
 
 import numpy as np
 
 F = np.float32
-MAX_TESTED = 256
 
 
 def tile_box(u, v, rx, ry, tile_w, tile_h, width, height):
@@ -48,30 +49,46 @@ def tile_box(u, v, rx, ry, tile_w, tile_h, width, height):
     return x0, x1, y0, y1, ok, tiles_x, tiles_y
 
 
-def _edge_max(A, B, C, d, lo, hi):
-    """max over t in [lo, hi] of A d^2 + B d t + C t^2 (C < 0), FP32 operation by operation."""
-    Bd = F(B * d)
-    t = -F(Bd / F(F(2.0) * C))
-    t = min(max(t, lo), hi)
-    return F(F(F(F(A * d) * d) + F(Bd * t)) + F(F(C * t) * t))
+def _sqrt(x):
+    return F(np.sqrt(F(max(x, F(0.0)))))
 
 
-def tile_hit(rec_row, log2_amin, tx, ty, tile_w, tile_h):
-    u, v, A, B = (F(x) for x in rec_row[0:4])
-    C, L = F(rec_row[4]), F(rec_row[5])
-    Tp = F(F(log2_amin) - L)
-    Tm = F(Tp - F(F(0.01) + F(F(0.001) * abs(Tp))))
-    x0 = F(F(F(tx * tile_w) + F(0.5)) - u)
-    x1 = F(F(F(tx * tile_w + tile_w) - F(0.5)) - u)
-    y0 = F(F(F(ty * tile_h) + F(0.5)) - v)
-    y1 = F(F(F(ty * tile_h + tile_h) - F(0.5)) - v)
-    if x0 <= 0 and x1 >= 0 and y0 <= 0 and y1 >= 0:
-        return True
-    m = _edge_max(A, B, C, x0, y0, y1)
-    m = max(m, _edge_max(A, B, C, x1, y0, y1))
-    m = max(m, _edge_max(C, B, A, y0, x0, x1))
-    m = max(m, _edge_max(C, B, A, y1, x0, x1))
-    return bool(m >= Tm)
+class _Ellipse:
+    """The ellipse q' >= Tm of one record, with the constants the row spans need (FP32)."""
+
+    def __init__(self, rec_row, log2_amin):
+        self.u, self.v, self.A, self.B = (F(x) for x in rec_row[0:4])
+        self.C, L = F(rec_row[4]), F(rec_row[5])
+        Tp = F(F(log2_amin) - L)
+        self.Tm = F(Tp - F(F(0.01) + F(F(0.001) * abs(Tp))))
+        delta = F(F(F(F(4.0) * self.A) * self.C) - F(self.B * self.B))
+        four_tm = F(F(4.0) * self.Tm)
+        self.dymax = _sqrt(F(F(four_tm * self.A) / delta))
+        dxmax = _sqrt(F(F(four_tm * self.C) / delta))
+        self.dyr = -F(F(self.B * dxmax) / F(F(2.0) * self.C))
+
+    def x_at(self, t, sign):
+        Bt = F(self.B * t)
+        D = F(F(Bt * Bt) - F(F(F(4.0) * self.A) * F(F(F(self.C * t) * t) - self.Tm)))
+        r = _sqrt(D)
+        return F(F(-Bt + F(F(sign) * r)) / F(F(2.0) * self.A))
+
+    def row_span(self, ty, x0, x1, tile_w, tile_h):
+        a = F(F(F(ty * tile_h) + F(0.5)) - self.v)
+        c = F(F(F(ty * tile_h + tile_h) - F(0.5)) - self.v)
+        a = max(a, -self.dymax)
+        c = min(c, self.dymax)
+        if not (a <= c):
+            return None
+        xl = self.x_at(min(max(-self.dyr, a), c), 1.0)
+        xr = self.x_at(min(max(self.dyr, a), c), -1.0)
+        itw = F(1.0 / tile_w)
+        f0 = np.floor(F(F(F(self.u + xl) - F(0.5)) * itw))
+        f1 = np.floor(F(F(F(self.u + xr) - F(0.5)) * itw))
+        if not (f0 <= x1 and f1 >= x0):
+            return None
+        t0, t1 = int(max(f0, x0)), int(min(f1, x1))
+        return (t0, t1) if t0 <= t1 else None
 
 
 def covered_tiles(rec, log2_amin, tile_w, tile_h, width, height):
@@ -80,15 +97,15 @@ def covered_tiles(rec, log2_amin, tile_w, tile_h, width, height):
     x0, x1, y0, y1, ok, tiles_x, tiles_y = tile_box(rec[:, 0], rec[:, 1], rec[:, 10], rec[:, 11], tile_w, tile_h,
                                                      width, height)
     out = []
-    with np.errstate(over="ignore", invalid="ignore"):
+    with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
         for g in range(rec.shape[0]):
             tiles = []
             if ok[g]:
-                box = (x1[g] - x0[g] + 1) * (y1[g] - y0[g] + 1)
+                e = _Ellipse(rec[g], log2_amin)
                 for ty in range(y0[g], y1[g] + 1):
-                    for tx in range(x0[g], x1[g] + 1):
-                        if box > MAX_TESTED or tile_hit(rec[g], log2_amin, tx, ty, tile_w, tile_h):
-                            tiles.append(ty * tiles_x + tx)
+                    span = e.row_span(ty, x0[g], x1[g], tile_w, tile_h)
+                    if span:
+                        tiles.extend(ty * tiles_x + tx for tx in range(span[0], span[1] + 1))
             out.append(tiles)
     return out, tiles_x, tiles_y
 

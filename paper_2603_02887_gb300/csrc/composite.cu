@@ -17,8 +17,9 @@
 //                Theta_{-1} = A - E_k taubar_k (A = sum_{i<k} E_i alpha_i saved by the forward pass);
 //                dL0/dE_i = pbar_i; dL0/dalpha_k = 0;
 //   exponential: dL0/dalpha_i = T_i E_i - R_i / (1 - alpha_i), R_i = L0 - sum_{j<=i} E_j pbar_j;
-// then the chain through alpha_i = 2^(L + q'(p)) to the splat record, a warp-shuffle reduction over the
-// warp's pixels and one atomic-add instruction per warp and splat into the per-Gaussian gradient buffer.
+// then w = dL/d(log2 alpha) and its moments w, w dx, w dy, w dx^2, w dx dy, w dy^2 (which determine the
+// gradient of the splat record, see the projection backward) and dL/dE, reduced over the warp's pixels with
+// shuffles and added to the per-Gaussian buffer with one atomic-add instruction per warp and splat.
 #include "ngs_internal.cuh"
 
 namespace ngs {
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(TW* TH) composite_backward_kernel(const float4
             acc0 = fmaf(E0, w, acc0);
             acc1 = fmaf(E1, w, acc1);
             acc2 = fmaf(E2, w, acc2);
-            float ia = 1.0f / (1.0f - alpha);
+            float ia = __frcp_rn(1.0f - alpha);
             float d0 = T * E0 - (Ek0 - acc0) * ia;
             float d1 = T * E1 - (Ek1 - acc1) * ia;
             float d2 = T * E2 - (Ek2 - acc2) * ia;
@@ -299,14 +300,17 @@ __global__ void __launch_bounds__(TW* TH) composite_backward_kernel(const float4
             gE2 = g2 * w;
             T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
           }
-          // alpha = 2^e with e = L + dx (A' dx + B' dy) + C' dy^2, unless clamped at alpha_max
+          // alpha = 2^e with e = L + dx (A' dx + B' dy) + C' dy^2, unless clamped at alpha_max. With
+          // w = dL/de, de/dA' = dx^2, de/dB' = dx dy, de/dC' = dy^2, de/dL = 1 and de/du = -(2A' dx + B' dy),
+          // de/dv = -(B' dx + 2C' dy): the per-splat sums of w, w dx, w dy, w dx^2, w dx dy, w dy^2 carry
+          // everything; the projection backward applies the per-splat A', B', C' once.
           float wgt = raw >= amax ? 0.f : dLda * alpha * kLn2;
           gL = wgt;
-          gA = wgt * dx * dx;
-          gB = wgt * dx * dy;
-          gC = wgt * dy * dy;
-          gu = -wgt * fmaf(2.f * r0.z, dx, r0.w * dy);
-          gv = -wgt * fmaf(r0.w, dx, 2.f * r1.x * dy);
+          gu = wgt * dx;
+          gv = wgt * dy;
+          gA = gu * dx;
+          gB = gu * dy;
+          gC = gv * dy;
         }
         if (__any_sync(kFull, on)) {
           const float v[9] = {gu, gv, gA, gB, gC, gL, gE0, gE1, gE2};

@@ -129,7 +129,27 @@ struct ProjState {
   float Y[K];
 };
 
-template <int DEG>
+// SH coefficients of Gaussian i: 3K floats. VEC: the block starts on a 16-byte boundary and 3K is a multiple
+// of 4 (degree 1 or 3 with an aligned base), so it is read with 16-byte loads.
+template <int K, bool VEC>
+__device__ __forceinline__ void load_sh(const float* sh, float (&c)[3 * K]) {
+  if constexpr (VEC) {
+    const float4* p = reinterpret_cast<const float4*>(sh);
+#pragma unroll
+    for (int k = 0; k < 3 * K / 4; ++k) {
+      float4 t = p[k];
+      c[4 * k] = t.x;
+      c[4 * k + 1] = t.y;
+      c[4 * k + 2] = t.z;
+      c[4 * k + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3 * K; ++k) c[k] = sh[k];
+  }
+}
+
+template <int DEG, bool VEC = false>
 __device__ __forceinline__ void forward_map(const ngs_gaussians& g, const CamParams& cam, const RenderParams& rp,
                                             int i, ProjState<DEG>& st) {
   constexpr int K = ProjState<DEG>::K;
@@ -186,7 +206,8 @@ __device__ __forceinline__ void forward_map(const ngs_gaussians& g, const CamPar
   st.dir[1] = d1 * idn;
   st.dir[2] = d2 * idn;
   sh_basis(DEG, st.dir[0], st.dir[1], st.dir[2], st.Y);
-  const float* sh = g.sh + (int64_t)i * K * 3;
+  float sh[3 * K];
+  load_sh<K, VEC>(g.sh + (int64_t)i * K * 3, sh);
   float e0 = 0.5f, e1 = 0.5f, e2 = 0.5f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -200,21 +221,20 @@ __device__ __forceinline__ void forward_map(const ngs_gaussians& g, const CamPar
 }
 
 // ---- tile binning --------------------------------------------------------------------------------
-// A splat reaches pixel p iff L + q'(p - mu) >= log2(alpha_min) with the concave q' of the record
-// (the compositing kernels' test). Its tiles are those of the bounding box of that ellipse (half
-// extents rx, ry from the record) for which the maximum of q' over the tile's box of pixel centres
-// reaches T' - margin, T' = log2(alpha_min) - L. The maximum of a concave quadratic over a box is 0
-// at the mean if the box contains it, else it lies on an edge, at the clamped vertex of the quadratic
-// along that edge. Every operation is one FP32 rounding in a fixed order, so the count (projection)
-// and the emission agree, and so does the tile-binning oracle. Boxes of more than kMaxTested tiles
-// are taken whole.
-constexpr int kMaxTested = 256;
-
+// A splat reaches pixel p iff L + q'(p - mu) >= log2(alpha_min), q'(d) = A' dx^2 + B' dx dy + C' dy^2 the
+// concave exponent of the record (the compositing kernels' test). Binning keeps the ellipse
+// q'(d) >= Tm = T' - (0.01 + 0.001 |T'|), T' = log2(alpha_min) - L (a margin over the per-pixel test), and
+// for every tile row of its bounding box takes the tiles that the ellipse's x-extent over the row's band of
+// pixel centres reaches. Along the band the right boundary of the ellipse is concave in dy, so its maximum
+// sits at the ellipse's rightmost point clamped to the band (the left boundary is convex: minimum at the
+// clamped leftmost point, its mirror image). Every operation is one FP32 rounding in a fixed order, so the
+// count (projection), the emission and the tile-binning oracle agree.
 struct SplatBin {
-  float u, v, A, B, C, Tm, rx, ry;
+  float u, v, A, B, C, Tm;
+  float dymax, dyr;  // half height of the ellipse; dy of its rightmost point
 };
 
-__device__ __forceinline__ SplatBin splat_bin(float4 r0, float4 r1, float4 r2, float log2_amin) {
+__device__ __forceinline__ SplatBin splat_bin(float4 r0, float4 r1, float log2_amin) {
   SplatBin b;
   b.u = r0.x;
   b.v = r0.y;
@@ -223,30 +243,41 @@ __device__ __forceinline__ SplatBin splat_bin(float4 r0, float4 r1, float4 r2, f
   b.C = r1.x;
   float Tp = __fsub_rn(log2_amin, r1.y);
   b.Tm = __fsub_rn(Tp, __fadd_rn(0.01f, __fmul_rn(0.001f, fabsf(Tp))));
-  b.rx = r2.z;
-  b.ry = r2.w;
+  // delta = 4 A' C' - B'^2 > 0; the ellipse spans |dy| <= sqrt(4 A' Tm / delta), |dx| <= sqrt(4 C' Tm / delta)
+  float delta = __fsub_rn(__fmul_rn(__fmul_rn(4.0f, b.A), b.C), __fmul_rn(b.B, b.B));
+  float four_tm = __fmul_rn(4.0f, b.Tm);
+  b.dymax = __fsqrt_rn(fmaxf(__fdiv_rn(__fmul_rn(four_tm, b.A), delta), 0.0f));
+  float dxmax = __fsqrt_rn(fmaxf(__fdiv_rn(__fmul_rn(four_tm, b.C), delta), 0.0f));
+  b.dyr = -__fdiv_rn(__fmul_rn(b.B, dxmax), __fmul_rn(2.0f, b.C));
   return b;
 }
 
-// max over t in [lo, hi] of q'(d, t) = A d^2 + B d t + C t^2 (d fixed; C < 0)
-__device__ __forceinline__ float edge_max(float A, float B, float C, float d, float lo, float hi) {
-  float Bd = __fmul_rn(B, d);
-  float t = -__fdiv_rn(Bd, __fmul_rn(2.0f, C));
-  t = fminf(fmaxf(t, lo), hi);
-  return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, d), d), __fmul_rn(Bd, t)), __fmul_rn(__fmul_rn(C, t), t));
+// Roots in dx of A' dx^2 + (B' t) dx + (C' t^2 - Tm) = 0 at height t (A' < 0): left (sign = +1) and right
+// (sign = -1) boundary of the ellipse.
+__device__ __forceinline__ float ellipse_x(const SplatBin& b, float t, float sign) {
+  float Bt = __fmul_rn(b.B, t);
+  float D = __fsub_rn(__fmul_rn(Bt, Bt), __fmul_rn(__fmul_rn(4.0f, b.A), __fsub_rn(__fmul_rn(__fmul_rn(b.C, t), t), b.Tm)));
+  float r = __fsqrt_rn(fmaxf(D, 0.0f));
+  return __fdiv_rn(__fadd_rn(-Bt, __fmul_rn(sign, r)), __fmul_rn(2.0f, b.A));
 }
 
-__device__ __forceinline__ bool tile_hit(const SplatBin& b, const RenderParams& rp, int tx, int ty) {
-  float x0 = __fsub_rn((float)(tx * rp.tile_w) + 0.5f, b.u);
-  float x1 = __fsub_rn((float)(tx * rp.tile_w + rp.tile_w) - 0.5f, b.u);
-  float y0 = __fsub_rn((float)(ty * rp.tile_h) + 0.5f, b.v);
-  float y1 = __fsub_rn((float)(ty * rp.tile_h + rp.tile_h) - 0.5f, b.v);
-  if (x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f) return true;
-  float m = edge_max(b.A, b.B, b.C, x0, y0, y1);               // left edge: dx fixed, maximise over dy
-  m = fmaxf(m, edge_max(b.A, b.B, b.C, x1, y0, y1));           // right edge
-  m = fmaxf(m, edge_max(b.C, b.B, b.A, y0, x0, x1));           // top edge: dy fixed, maximise over dx
-  m = fmaxf(m, edge_max(b.C, b.B, b.A, y1, x0, x1));           // bottom edge
-  return m >= b.Tm;
+// Tile columns [tx0, tx1] of tile row ty reached by the ellipse, clipped to [x0, x1]; false if none.
+__device__ __forceinline__ bool row_span(const SplatBin& b, const RenderParams& rp, int ty, int x0, int x1, int& tx0,
+                                         int& tx1) {
+  float a = __fsub_rn((float)(ty * rp.tile_h) + 0.5f, b.v);
+  float c = __fsub_rn((float)(ty * rp.tile_h + rp.tile_h) - 0.5f, b.v);
+  a = fmaxf(a, -b.dymax);
+  c = fminf(c, b.dymax);
+  if (!(a <= c)) return false;
+  float xl = ellipse_x(b, fminf(fmaxf(-b.dyr, a), c), 1.0f);
+  float xr = ellipse_x(b, fminf(fmaxf(b.dyr, a), c), -1.0f);
+  float itw = 1.0f / (float)rp.tile_w;  // power of two: exact
+  float f0 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(b.u, xl), 0.5f), itw));
+  float f1 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(b.u, xr), 0.5f), itw));
+  if (!(f0 <= (float)x1 && f1 >= (float)x0)) return false;
+  tx0 = (int)fmaxf(f0, (float)x0);
+  tx1 = (int)fminf(f1, (float)x1);
+  return tx0 <= tx1;
 }
 
 // Tile bounding box of the splat (u, v) with half extents (rx, ry): identical arithmetic everywhere.
@@ -267,18 +298,19 @@ __device__ __forceinline__ bool tile_rect(float u, float v, float rx, float ry, 
   return true;
 }
 
-__device__ __forceinline__ uint32_t count_tiles(const SplatBin& b, const RenderParams& rp) {
+__device__ __forceinline__ uint32_t count_tiles(float4 r0, float4 r1, float4 r2, const RenderParams& rp) {
   int x0, x1, y0, y1;
-  if (!tile_rect(b.u, b.v, b.rx, b.ry, rp, x0, x1, y0, y1)) return 0;
-  uint32_t box = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
-  if (box > (uint32_t)kMaxTested) return box;
+  if (!tile_rect(r0.x, r0.y, r2.z, r2.w, rp, x0, x1, y0, y1)) return 0;
+  SplatBin b = splat_bin(r0, r1, rp.log2_alpha_min);
   uint32_t c = 0;
-  for (int ty = y0; ty <= y1; ++ty)
-    for (int tx = x0; tx <= x1; ++tx) c += tile_hit(b, rp, tx, ty) ? 1u : 0u;
+  for (int ty = y0; ty <= y1; ++ty) {
+    int t0, t1;
+    if (row_span(b, rp, ty, x0, x1, t0, t1)) c += (uint32_t)(t1 - t0 + 1);
+  }
   return c;
 }
 
-template <int DEG>
+template <int DEG, bool VEC>
 __global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, CamParams cam, RenderParams rp, float4* rec,
                                                       uint32_t* depth_key, uint32_t* tile_count, uint32_t* order) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -289,7 +321,7 @@ __global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, CamParams
   uint32_t count = 0;
   if (z > rp.near_plane) {
     ProjState<DEG> st;
-    forward_map<DEG>(g, cam, rp, i, st);
+    forward_map<DEG, VEC>(g, cam, rp, i, st);
     float det = st.s00 * st.s11 - st.s01 * st.s01;
     if (det > 0.f && st.aleph >= rp.alpha_min && isfinite(st.A) && isfinite(st.C)) {
       float u = cam.fx * st.x * st.iz + cam.cx;
@@ -305,7 +337,7 @@ __global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, CamParams
       r0 = make_float4(u, v, kConicScale * st.A, 2.f * kConicScale * st.B);
       r1 = make_float4(kConicScale * st.C, L, E0, E1);
       r2 = make_float4(E2, z, rx, ry);
-      count = count_tiles(splat_bin(r0, r1, r2, rp.log2_alpha_min), rp);
+      count = count_tiles(r0, r1, r2, rp);
     }
   }
   rec[3 * (int64_t)i] = r0;
@@ -325,22 +357,22 @@ __global__ void __launch_bounds__(256) emit_keys_kernel(const float4* rec, const
   if (off == end) return;
   uint32_t id = order[s];
   float4 r0 = rec[3 * (int64_t)id], r1 = rec[3 * (int64_t)id + 1], r2 = rec[3 * (int64_t)id + 2];
-  SplatBin b = splat_bin(r0, r1, r2, rp.log2_alpha_min);
   int x0, x1, y0, y1;
-  if (!tile_rect(b.u, b.v, b.rx, b.ry, rp, x0, x1, y0, y1)) return;
-  bool test = (x1 - x0 + 1) * (y1 - y0 + 1) <= kMaxTested;
+  if (!tile_rect(r0.x, r0.y, r2.z, r2.w, rp, x0, x1, y0, y1)) return;
+  SplatBin b = splat_bin(r0, r1, rp.log2_alpha_min);
   uint64_t zb = (uint64_t)__float_as_uint(r2.y);
-  for (int ty = y0; ty <= y1 && off < end; ++ty)
-    for (int tx = x0; tx <= x1 && off < end; ++tx) {
-      if (test && !tile_hit(b, rp, tx, ty)) continue;
-      uint64_t tile = (uint64_t)(ty * rp.tiles_x + tx);
+  for (int ty = y0; ty <= y1 && off < end; ++ty) {
+    int t0, t1;
+    if (!row_span(b, rp, ty, x0, x1, t0, t1)) continue;
+    uint64_t tile = (uint64_t)(ty * rp.tiles_x + t0);
+    for (int tx = t0; tx <= t1 && off < end; ++tx, ++tile, ++off) {
       keys[off] = (tile << 32) | zb;
       vals[off] = id;
-      ++off;
     }
+  }
 }
 
-template <int DEG>
+template <int DEG, bool VEC>
 __global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, CamParams cam, RenderParams rp,
                                                                const uint32_t* tile_count, const float4* grad2d,
                                                                ngs_grads out) {
@@ -357,15 +389,22 @@ __global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, 
 #pragma unroll
     for (int k = 0; k < 4; ++k) dq[k] = 0.f;
     out.d_opacity_logits[i] = 0.f;
+    if constexpr (VEC) {
 #pragma unroll
-    for (int k = 0; k < 3 * K; ++k) dsh[k] = 0.f;
+      for (int k = 0; k < 3 * K / 4; ++k) reinterpret_cast<float4*>(dsh)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3 * K; ++k) dsh[k] = 0.f;
+    }
     return;
   }
   float4 g0 = grad2d[3 * (int64_t)i], g1 = grad2d[3 * (int64_t)i + 1], g2 = grad2d[3 * (int64_t)i + 2];
   ProjState<DEG> st;
-  forward_map<DEG>(g, cam, rp, i, st);
-  // record -> natural quantities
-  float du = g0.x, dv = g0.y;
+  forward_map<DEG, VEC>(g, cam, rp, i, st);
+  // moments -> record gradient (the record's A', B', C' are these same products) -> natural quantities
+  const float Ap = kConicScale * st.A, Bp = 2.f * kConicScale * st.B, Cp = kConicScale * st.C;
+  float du = -(2.f * Ap * g0.x + Bp * g0.y);
+  float dv = -(Bp * g0.x + 2.f * Cp * g0.y);
   float dA = g0.z * kConicScale, dB = g0.w * 2.f * kConicScale, dC = g1.x * kConicScale;
   float dE[3] = {g1.z, g1.w, g2.x};
   out.d_opacity_logits[i] = g1.y * (1.f - st.aleph) / kLn2;  // L = log2(sigmoid(logit))
@@ -438,17 +477,26 @@ __global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, 
 #pragma unroll
   for (int k = 0; k < 4; ++k) dq[k] = (dqn[k] - st.qn[k] * dot) * iq;
   // emission: dE/dsh = Y (unclamped channels); direction term into the mean
-  const float* sh = g.sh + (int64_t)i * K * 3;
+  float sh[3 * K];
+  load_sh<K, VEC>(g.sh + (int64_t)i * K * 3, sh);
   float d0 = st.e[0] < 0.f ? 0.f : dE[0];
   float d1 = st.e[1] < 0.f ? 0.f : dE[1];
   float d2 = st.e[2] < 0.f ? 0.f : dE[2];
-  float wk[K];
+  float wk[K], gsh[3 * K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    dsh[3 * k] = d0 * st.Y[k];
-    dsh[3 * k + 1] = d1 * st.Y[k];
-    dsh[3 * k + 2] = d2 * st.Y[k];
+    gsh[3 * k] = d0 * st.Y[k];
+    gsh[3 * k + 1] = d1 * st.Y[k];
+    gsh[3 * k + 2] = d2 * st.Y[k];
     wk[k] = d0 * sh[3 * k] + d1 * sh[3 * k + 1] + d2 * sh[3 * k + 2];
+  }
+  if constexpr (VEC) {
+#pragma unroll
+    for (int k = 0; k < 3 * K / 4; ++k)
+      reinterpret_cast<float4*>(dsh)[k] = make_float4(gsh[4 * k], gsh[4 * k + 1], gsh[4 * k + 2], gsh[4 * k + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3 * K; ++k) dsh[k] = gsh[k];
   }
   float gdx, gdy, gdz;
   sh_basis_grad(DEG, st.dir[0], st.dir[1], st.dir[2], wk, gdx, gdy, gdz);
@@ -467,11 +515,18 @@ void launch_project(const ngs_gaussians& g, const CamParams& cam, const RenderPa
                     uint32_t* depth_key, uint32_t* tile_count, uint32_t* order, cudaStream_t s) {
   if (g.n == 0) return;
   int blocks = (int)((g.n + 255) / 256);
+  bool vec = ((uintptr_t)g.sh & 15) == 0;
   switch (rp.sh_degree) {
-    case 0: project_kernel<0><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order); break;
-    case 1: project_kernel<1><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order); break;
-    case 2: project_kernel<2><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order); break;
-    default: project_kernel<3><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order); break;
+    case 0: project_kernel<0, false><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order); break;
+    case 1:
+      if (vec) project_kernel<1, true><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order);
+      else project_kernel<1, false><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order);
+      break;
+    case 2: project_kernel<2, false><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order); break;
+    default:
+      if (vec) project_kernel<3, true><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order);
+      else project_kernel<3, false><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order);
+      break;
   }
 }
 
@@ -486,11 +541,18 @@ void launch_project_backward(const ngs_gaussians& g, const CamParams& cam, const
                              cudaStream_t s) {
   if (g.n == 0) return;
   int blocks = (int)((g.n + 127) / 128);
+  bool vec = ((uintptr_t)g.sh & 15) == 0 && ((uintptr_t)out.d_sh & 15) == 0;
   switch (rp.sh_degree) {
-    case 0: project_backward_kernel<0><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out); break;
-    case 1: project_backward_kernel<1><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out); break;
-    case 2: project_backward_kernel<2><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out); break;
-    default: project_backward_kernel<3><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out); break;
+    case 0: project_backward_kernel<0, false><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out); break;
+    case 1:
+      if (vec) project_backward_kernel<1, true><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out);
+      else project_backward_kernel<1, false><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out);
+      break;
+    case 2: project_backward_kernel<2, false><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out); break;
+    default:
+      if (vec) project_backward_kernel<3, true><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out);
+      else project_backward_kernel<3, false><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out);
+      break;
   }
 }
 

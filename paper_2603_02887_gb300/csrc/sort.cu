@@ -47,7 +47,7 @@ __device__ __forceinline__ T block_exclusive_sum(T v, T* s_warp, T* total) {
 }
 
 constexpr int kThreads = 256;
-constexpr int kItems = 16;
+constexpr int kItems = 8;
 constexpr int kTile = kThreads * kItems;  // items per block
 constexpr int kWarps = kThreads / 32;
 constexpr int kDigits = 256;
