@@ -210,30 +210,27 @@ __global__ void __launch_bounds__(TW* TH) composite_backward_kernel(const float4
   uint2 range = ranges[tile];
   uint32_t last = range.x;  // replay entries [range.x, last)
   float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-  float Ek0 = 0.f, Ek1 = 0.f, Ek2 = 0.f;      // quadratic: E_k; exponential: L0
-  float Th0 = 0.f, Th1 = 0.f, Th2 = 0.f;      // quadratic: Theta
-  bool sat = false;
+  // everything the adjoint needs is a dot product with g: quadratic keeps g.E_k and g.Theta, exponential
+  // keeps g.L0 and the running g.sum_{j<=i} E_j pbar_j
+  float gEk = 0.f, gTh = 0.f, gL0 = 0.f;
   if (inside) {
     size_t pix = (size_t)y * W + x;
     float4 s0 = state[2 * pix], s1 = state[2 * pix + 1];
     uint32_t nbits = __float_as_uint(s0.x);
     last = range.x + (nbits & 0x7FFFFFFFu);
-    sat = (nbits >> 31) != 0;
-    Ek0 = s0.y;
-    Ek1 = s0.z;
-    Ek2 = s0.w;
     g0 = dl_dimage[3 * pix];
     g1 = dl_dimage[3 * pix + 1];
     g2 = dl_dimage[3 * pix + 2];
     if (KIND == NGS_MODEL_QUAD) {
-      Th0 = s1.x - Ek0 * s1.w;
-      Th1 = s1.y - Ek1 * s1.w;
-      Th2 = s1.z - Ek2 * s1.w;
+      gEk = g0 * s0.y + g1 * s0.z + g2 * s0.w;
+      // Theta_{-1} = A - E_k taubar_k
+      gTh = g0 * (s1.x - s0.y * s1.w) + g1 * (s1.y - s0.z * s1.w) + g2 * (s1.z - s0.w * s1.w);
+    } else {
+      gL0 = g0 * s0.y + g1 * s0.z + g2 * s0.w;
     }
     if (g0 == 0.f && g1 == 0.f && g2 == 0.f) last = range.x;
   }
-  (void)sat;
-  float S = 0.f, tau = 0.f, T = 1.f, acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+  float S = 0.f, tau = 0.f, T = 1.f, gacc = 0.f;
   const float amax = rp.alpha_max, l2min = rp.log2_alpha_min, c = rp.c;
   // the warp walks entries up to the largest stop of its lanes
   const uint32_t warp_last = __reduce_max_sync(kFull, last);
@@ -262,6 +259,7 @@ __global__ void __launch_bounds__(TW* TH) composite_backward_kernel(const float4
           float raw = fast_exp2(e);
           float alpha = fminf(amax, raw);
           float E0 = r1.z, E1 = r1.w, E2 = s_e2[j];
+          float gE = fmaf(g2, E2, fmaf(g1, E1, g0 * E0));  // g.E_i
           float dLda;
           if (KIND == NGS_MODEL_QUAD) {
             float pt = quad_slope(alpha, c, tau);
@@ -273,12 +271,10 @@ __global__ void __launch_bounds__(TW* TH) composite_backward_kernel(const float4
               gE2 = g2 * pk;
               dLda = 0.f;
             } else {
-              float d0 = E0 - Ek0, d1 = E1 - Ek1, d2 = E2 - Ek2;
-              Th0 = fmaf(-d0, alpha, Th0);
-              Th1 = fmaf(-d1, alpha, Th1);
-              Th2 = fmaf(-d2, alpha, Th2);
-              float f = fmaf(c, tau, 1.0f);
-              dLda = g0 * fmaf(d0, f, c * Th0) + g1 * fmaf(d1, f, c * Th1) + g2 * fmaf(d2, f, c * Th2);
+              // g.dL0/dalpha_i = g.DeltaE_i (1 + c taubar_i) + c g.Theta_i, Theta_i = Theta_{i-1} - DeltaE_i alpha_i
+              float gd = gE - gEk;
+              gTh = fmaf(-gd, alpha, gTh);
+              dLda = fmaf(gd, fmaf(c, tau, 1.0f), c * gTh);
               gE0 = g0 * pt;
               gE1 = g1 * pt;
               gE2 = g2 * pt;
@@ -286,15 +282,10 @@ __global__ void __launch_bounds__(TW* TH) composite_backward_kernel(const float4
               tau = __fadd_rn(tau, alpha);
             }
           } else {
+            // g.dL0/dalpha_i = T_i g.E_i - (g.L0 - g.sum_{j<=i} E_j pbar_j) / (1 - alpha_i)
             float w = alpha * T;
-            acc0 = fmaf(E0, w, acc0);
-            acc1 = fmaf(E1, w, acc1);
-            acc2 = fmaf(E2, w, acc2);
-            float ia = __frcp_rn(1.0f - alpha);
-            float d0 = T * E0 - (Ek0 - acc0) * ia;
-            float d1 = T * E1 - (Ek1 - acc1) * ia;
-            float d2 = T * E2 - (Ek2 - acc2) * ia;
-            dLda = g0 * d0 + g1 * d1 + g2 * d2;
+            gacc = fmaf(gE, w, gacc);
+            dLda = fmaf(T, gE, -__frcp_rn(1.0f - alpha) * (gL0 - gacc));
             gE0 = g0 * w;
             gE1 = g1 * w;
             gE2 = g2 * w;
@@ -304,7 +295,7 @@ __global__ void __launch_bounds__(TW* TH) composite_backward_kernel(const float4
           // w = dL/de, de/dA' = dx^2, de/dB' = dx dy, de/dC' = dy^2, de/dL = 1 and de/du = -(2A' dx + B' dy),
           // de/dv = -(B' dx + 2C' dy): the per-splat sums of w, w dx, w dy, w dx^2, w dx dy, w dy^2 carry
           // everything; the projection backward applies the per-splat A', B', C' once.
-          float wgt = raw >= amax ? 0.f : dLda * alpha * kLn2;
+          float wgt = raw >= amax ? 0.f : dLda * alpha;  // dL/de / ln 2 (the projection backward applies ln 2)
           gL = wgt;
           gu = wgt * dx;
           gv = wgt * dy;
@@ -312,9 +303,19 @@ __global__ void __launch_bounds__(TW* TH) composite_backward_kernel(const float4
           gB = gu * dy;
           gC = gv * dy;
         }
-        if (__any_sync(kFull, on)) {
-          const float v[9] = {gu, gv, gA, gB, gC, gL, gE0, gE1, gE2};
-          warp_reduce9_add(v, reinterpret_cast<float*>(grad2d + 3 * (size_t)s_id[j]), lane);
+        const uint32_t mask = __ballot_sync(kFull, on);
+        if (mask) {
+          float4* dst = grad2d + 3 * (size_t)s_id[j];
+          if (__popc(mask) <= 4) {  // few lanes: add their values directly
+            if (on) {
+              atomicAdd(dst, make_float4(gu, gv, gA, gB));
+              atomicAdd(dst + 1, make_float4(gC, gL, gE0, gE1));
+              atomicAdd(reinterpret_cast<float*>(dst + 2), gE2);
+            }
+          } else {
+            const float v[9] = {gu, gv, gA, gB, gC, gL, gE0, gE1, gE2};
+            warp_reduce9_add(v, reinterpret_cast<float*>(dst), lane);
+          }
         }
       }
     }

@@ -44,7 +44,8 @@ constexpr float kConicScale = -0.5f * 1.4426950408889634f;
 
 // Per-Gaussian gradient buffer written by the replay (3 float4 per Gaussian): with w = dL/d(log2 alpha) at
 // each pixel and (dx, dy) = p - (u, v), the sums over pixels of
-//   (w dx, w dy, w dx^2, w dx dy, w dy^2, w, dL/dE0, dL/dE1, dL/dE2, 0, 0, 0).
+//   (w dx, w dy, w dx^2, w dx dy, w dy^2, w, dL/dE0, dL/dE1, dL/dE2, 0, 0, 0),
+// the first six divided by ln 2 (the projection backward multiplies it back).
 // The record gradient follows: dA' = sum w dx^2, dB' = sum w dx dy, dC' = sum w dy^2, dL = sum w,
 // du = -(2A' sum w dx + B' sum w dy), dv = -(B' sum w dx + 2C' sum w dy).
 

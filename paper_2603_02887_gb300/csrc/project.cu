@@ -399,6 +399,10 @@ __global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, 
     return;
   }
   float4 g0 = grad2d[3 * (int64_t)i], g1 = grad2d[3 * (int64_t)i + 1], g2 = grad2d[3 * (int64_t)i + 2];
+  // the replay accumulates w / ln 2 (w = dL/d(log2 alpha)): restore the factor on the six moments
+  g0 = make_float4(g0.x * kLn2, g0.y * kLn2, g0.z * kLn2, g0.w * kLn2);
+  g1.x *= kLn2;
+  g1.y *= kLn2;
   ProjState<DEG> st;
   forward_map<DEG, VEC>(g, cam, rp, i, st);
   // moments -> record gradient (the record's A', B', C' are these same products) -> natural quantities
