@@ -39,7 +39,9 @@ extern "C" {
 #define NGS_ERR_INVALID_ARG (-1)   /* a pointer, size or option is out of its documented range      */
 #define NGS_ERR_OUT_OF_MEMORY (-2) /* device allocation of internal buffers failed                  */
 #define NGS_ERR_CUDA (-3)          /* a CUDA runtime call failed (message in ngs_last_error)       */
-#define NGS_ERR_DEVICE_CHECK (-5)  /* a kernel's own bounds check fired; its output is not valid   */
+#define NGS_ERR_DEVICE_CHECK (-5)  /* a kernel's own bounds check fired (in this or an earlier call   */
+                                   /* on the context; reported at the next render); that output was  */
+                                   /* not valid                                                       */
 
 /* ---- transmittance models (Table 1) ----------------------------------------------------------- */
 #define NGS_MODEL_EXP 0  /* T = exp(-tau): pbar_i = alpha_i prod_{j<i}(1 - alpha_j) (standard 3DGS)      */

@@ -117,7 +117,7 @@ NGS_API int ngs_create(ngs_ctx** out) {
   if (!ctx) return NGS_ERR_OUT_OF_MEMORY;
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_total, sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_total, 2 * sizeof(uint64_t));
   if (e != cudaSuccess) {
     cudaGetLastError();
     delete ctx;
@@ -233,6 +233,7 @@ NGS_API int ngs_render(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const
   rp.tiles_y = (cam->height + o->tile_h - 1) / o->tile_h;
   rp.max_splats = o->max_splats;
   rp.sh_degree = g->sh_degree;
+  rp.n_gaussians = (uint32_t)g->n;
   uint32_t n = (uint32_t)g->n;
   uint32_t ntiles = (uint32_t)rp.tiles_x * (uint32_t)rp.tiles_y;
   size_t npix = (size_t)cam->width * cam->height;
@@ -247,7 +248,11 @@ NGS_API int ngs_render(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const
   NGS_TRY(ensure(ctx, f->ranges, sizeof(uint2) * (size_t)ntiles));
   NGS_TRY(ensure(ctx, f->state, sizeof(float4) * 2 * npix));
   NGS_TRY(ensure(ctx, ctx->scan_tmp, sizeof(uint64_t) * scan_tmp_words(n)));
-  NGS_TRY(ensure(ctx, ctx->total, sizeof(uint64_t)));
+  if (!ctx->total.p) {
+    NGS_TRY(ensure(ctx, ctx->total, 2 * sizeof(uint64_t)));
+    cudaMemsetAsync(ctx->total.p, 0, 2 * sizeof(uint64_t), s);
+  }
+  rp.check = reinterpret_cast<uint32_t*>(ctx->total.as<uint64_t>() + 1);
   NGS_TRY(ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(std::max(n, 1u))));
 
   cudaEvent_t ev;
@@ -274,9 +279,14 @@ NGS_API int ngs_render(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const
   launch_scan_counts(f->tile_count.as<uint32_t>(), order, n, f->offsets.as<uint32_t>(), ctx->scan_tmp.as<uint64_t>(),
                      ctx->total.as<uint64_t>(), s, &launches);
   NGS_TRY(check_launch(ctx, "scan"));
-  cudaError_t e = cudaMemcpyAsync(ctx->h_total, ctx->total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaMemcpyAsync(ctx->h_total, ctx->total.p, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("reading the pair count: ") + cudaGetErrorString(e));
+  if (ctx->h_total[1] != 0) {  // a bounds check fired in an earlier call on this context
+    cudaMemsetAsync(ctx->total.as<uint64_t>() + 1, 0, sizeof(uint64_t), s);
+    return fail(ctx, NGS_ERR_DEVICE_CHECK, "a kernel bounds check fired in an earlier call on this context; its "
+                                           "output was not valid");
+  }
   uint64_t P = *ctx->h_total;
   if (P >= (1ull << 31)) return fail(ctx, NGS_ERR_INVALID_ARG, "more than 2^31 (tile, Gaussian) pairs");
   uint32_t np = (uint32_t)P;

@@ -1,8 +1,9 @@
 // Per-tile front-to-back compositing (forward) and its path-replay adjoint (backward).
 //
-// One CTA per screen tile, one thread per pixel; warps cover 8 x 4 pixel blocks so that the pixels of a
-// warp are close and tend to saturate together. The tile's depth-sorted splat list is walked in chunks:
-// each thread stages one splat record (48 B) in shared memory, then every pixel walks the chunk.
+// One CTA per screen tile. Forward: one thread per pixel, warps on 8 x 4 pixel blocks whose pixels are close
+// and tend to saturate together. Replay: two pixels per thread, (x, y) and (x, y + 4), so that a warp covers
+// an 8 x 8 block and reduces the sum of both pixels' contributions once per 64 pixels. The tile's
+// depth-sorted splat list is walked in chunks of one record (48 B) per pixel staged in shared memory.
 //
 // Forward, per pixel (Eq. generalized_gaussian with pbar_i from Eq. nexp_p and Table 1):
 //   alpha_i = min(alpha_max, aleph_i K_i(p)), skipped when alpha_i < alpha_min;
@@ -27,17 +28,44 @@ namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
-template <int TW, int TH>
+// Stage the splat record of Gaussian `id` in shared memory. An index outside [0, n) (which a correct
+// binning never produces) is not read: the entry gets log2(aleph) = -inf, so no pixel composites it, and
+// the device error word records the event.
+__device__ __forceinline__ void stage_record(const float4* __restrict__ rec, uint32_t id, const RenderParams& rp,
+                                             float4& r0, float4& r1, float& e2) {
+  if (id < rp.n_gaussians) {
+    r0 = rec[3 * (size_t)id];
+    r1 = rec[3 * (size_t)id + 1];
+    e2 = rec[3 * (size_t)id + 2].x;
+  } else {
+    r0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    r1 = make_float4(0.f, -INFINITY, 0.f, 0.f);
+    e2 = 0.f;
+    atomicOr(rp.check, kCheckIndex);
+  }
+}
+
+template <int TW, int TH, int PPT>
 struct TileGeom {
-  static constexpr int kThreads = TW * TH;
+  static constexpr int kPix = PPT;  // pixels per thread
+  static constexpr int kThreads = TW * TH / kPix;
+  static constexpr int kChunk = TW * TH;  // records staged per chunk (kPix per thread)
   static constexpr int kWarpsX = TW / 8;
-  static_assert(TW % 8 == 0 && TH % 4 == 0, "tile must be a multiple of 8 x 4");
-  __device__ static void pixel(int tid, int tile_x0, int tile_y0, int& x, int& y) {
+  static_assert(TW % 8 == 0 && TH % (4 * PPT) == 0, "tile must be a multiple of 8 x (4 PPT)");
+  // warp w covers the 8 x (4 PPT) block (w % kWarpsX, w / kWarpsX) of the tile; lane l owns its pixels
+  // (l & 7, (l >> 3) + 4 k), k < PPT
+  __device__ static void pixel(int tid, int k, int tile_x0, int tile_y0, int& x, int& y) {
     int warp = tid >> 5, lane = tid & 31;
     x = tile_x0 + (warp % kWarpsX) * 8 + (lane & 7);
-    y = tile_y0 + (warp / kWarpsX) * 4 + (lane >> 3);
+    y = tile_y0 + (warp / kWarpsX) * 4 * PPT + (lane >> 3) + 4 * k;
   }
 };
+
+// The forward keeps one pixel per thread (a thread retires with its pixel); the replay takes two, so that
+// the warp reduces once per 64 pixels.
+constexpr int kBwdPix = 2;
+
+// ---- forward ---------------------------------------------------------------------------------------
 
 template <int TW, int TH, int KIND>
 __global__ void __launch_bounds__(TW* TH) composite_forward_kernel(const float4* __restrict__ rec,
@@ -46,7 +74,7 @@ __global__ void __launch_bounds__(TW* TH) composite_forward_kernel(const float4*
                                                                    int W, int H, float* __restrict__ image,
                                                                    int32_t* __restrict__ overdraw,
                                                                    float4* __restrict__ state) {
-  using G = TileGeom<TW, TH>;
+  using G = TileGeom<TW, TH, 1>;
   constexpr int B = G::kThreads;
   __shared__ float4 s_r0[B];
   __shared__ float4 s_r1[B];
@@ -55,7 +83,7 @@ __global__ void __launch_bounds__(TW* TH) composite_forward_kernel(const float4*
   int tx = tile % rp.tiles_x, ty = tile / rp.tiles_x;
   int tid = threadIdx.x;
   int x, y;
-  G::pixel(tid, tx * TW, ty * TH, x, y);
+  G::pixel(tid, 0, tx * TW, ty * TH, x, y);
   bool inside = x < W && y < H;
   float px = (float)x + 0.5f, py = (float)y + 0.5f;
   uint2 range = ranges[tile];
@@ -72,12 +100,7 @@ __global__ void __launch_bounds__(TW* TH) composite_forward_kernel(const float4*
   for (uint32_t base = range.x; base < range.y; base += B) {
     if (__syncthreads_count(done) == B) break;
     uint32_t i = base + tid;
-    if (i < range.y) {
-      uint32_t id = ids[i];
-      s_r0[tid] = rec[3 * (size_t)id];
-      s_r1[tid] = rec[3 * (size_t)id + 1];
-      s_e2[tid] = rec[3 * (size_t)id + 2].x;
-    }
+    if (i < range.y) stage_record(rec, ids[i], rp, s_r0[tid], s_r1[tid], s_e2[tid]);
     __syncthreads();
     int cnt = (int)min((uint32_t)B, range.y - base);
     if (__any_sync(kFull, !done)) {
@@ -153,6 +176,16 @@ __global__ void __launch_bounds__(TW* TH) composite_forward_kernel(const float4*
   }
 }
 
+// ---- backward (path replay) --------------------------------------------------------------------------
+
+struct BwdPixel {
+  float px, py;
+  uint32_t last;        // replay entries [range.x, last)
+  float g0, g1, g2;
+  float gEk, gTh, gL0;  // quadratic: g.E_k, g.Theta; exponential: g.L0
+  float S, tau, T, gacc;
+};
+
 // Sum nine per-lane values over the warp and add the totals to dst[0..8] with one atomic instruction.
 // Values 0..7 go through a transposing butterfly: at each of three steps a lane keeps half of the values
 // it carries and sends the other half to its partner, so after xor 16, 8, 4 (and two plain xor 2, 1
@@ -187,133 +220,144 @@ __device__ __forceinline__ void warp_reduce9_add(const float (&v)[9], float* dst
     atomicAdd(dst + 8, e);
 }
 
-template <int TW, int TH, int KIND>
-__global__ void __launch_bounds__(TW* TH) composite_backward_kernel(const float4* __restrict__ rec,
-                                                                    const uint32_t* __restrict__ ids,
-                                                                    const uint2* __restrict__ ranges, RenderParams rp,
-                                                                    int W, int H, const float* __restrict__ dl_dimage,
-                                                                    const float4* __restrict__ state,
-                                                                    float4* __restrict__ grad2d) {
-  using G = TileGeom<TW, TH>;
-  constexpr int B = G::kThreads;
-  __shared__ float4 s_r0[B];
-  __shared__ float4 s_r1[B];
-  __shared__ float s_e2[B];
-  __shared__ uint32_t s_id[B];
-  int tile = blockIdx.x;
-  int tx = tile % rp.tiles_x, ty = tile / rp.tiles_x;
-  int tid = threadIdx.x, lane = tid & 31;
-  int x, y;
-  G::pixel(tid, tx * TW, ty * TH, x, y);
-  bool inside = x < W && y < H;
-  float px = (float)x + 0.5f, py = (float)y + 0.5f;
-  uint2 range = ranges[tile];
-  uint32_t last = range.x;  // replay entries [range.x, last)
-  float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-  // everything the adjoint needs is a dot product with g: quadratic keeps g.E_k and g.Theta, exponential
-  // keeps g.L0 and the running g.sum_{j<=i} E_j pbar_j
-  float gEk = 0.f, gTh = 0.f, gL0 = 0.f;
-  if (inside) {
-    size_t pix = (size_t)y * W + x;
-    float4 s0 = state[2 * pix], s1 = state[2 * pix + 1];
-    uint32_t nbits = __float_as_uint(s0.x);
-    last = range.x + (nbits & 0x7FFFFFFFu);
-    g0 = dl_dimage[3 * pix];
-    g1 = dl_dimage[3 * pix + 1];
-    g2 = dl_dimage[3 * pix + 2];
-    if (KIND == NGS_MODEL_QUAD) {
-      gEk = g0 * s0.y + g1 * s0.z + g2 * s0.w;
-      // Theta_{-1} = A - E_k taubar_k
-      gTh = g0 * (s1.x - s0.y * s1.w) + g1 * (s1.y - s0.z * s1.w) + g2 * (s1.z - s0.w * s1.w);
+// One list entry for one pixel of the replay: adds the pixel's contributions to v (the 9 per-splat sums)
+// and returns whether the splat was composited at this pixel.
+template <int KIND>
+__device__ __forceinline__ bool bwd_step(BwdPixel& p, float4 r0, float4 r1, const float& e2, uint32_t pos,
+                                         const RenderParams& rp, float (&v)[9]) {
+  if (pos >= p.last) return false;
+  float dx, dy;
+  float e = splat_log2_alpha(p.px, p.py, r0, r1, dx, dy);
+  if (e < rp.log2_alpha_min) return false;
+  float raw = fast_exp2(e);
+  float alpha = fminf(rp.alpha_max, raw);
+  float E0 = r1.z, E1 = r1.w, E2 = e2;
+  float gE = fmaf(p.g2, E2, fmaf(p.g1, E1, p.g0 * E0));  // g.E_i
+  float dLda, wE;
+  if (KIND == NGS_MODEL_QUAD) {
+    float pt = quad_slope(alpha, rp.c, p.tau);
+    float Sn = __fadd_rn(p.S, pt);
+    if (Sn >= 1.0f) {  // the saturating splat k: pbar_k = 1 - S, no dependence on alpha_k
+      wE = 1.0f - p.S;
+      dLda = 0.f;
     } else {
-      gL0 = g0 * s0.y + g1 * s0.z + g2 * s0.w;
+      // g.dL0/dalpha_i = g.DeltaE_i (1 + c taubar_i) + c g.Theta_i, Theta_i = Theta_{i-1} - DeltaE_i alpha_i
+      float gd = gE - p.gEk;
+      p.gTh = fmaf(-gd, alpha, p.gTh);
+      dLda = fmaf(gd, fmaf(rp.c, p.tau, 1.0f), rp.c * p.gTh);
+      wE = pt;
+      p.S = Sn;
+      p.tau = __fadd_rn(p.tau, alpha);
     }
-    if (g0 == 0.f && g1 == 0.f && g2 == 0.f) last = range.x;
+  } else {
+    // g.dL0/dalpha_i = T_i g.E_i - (g.L0 - g.sum_{j<=i} E_j pbar_j) / (1 - alpha_i)
+    wE = alpha * p.T;
+    p.gacc = fmaf(gE, wE, p.gacc);
+    dLda = fmaf(p.T, gE, -__frcp_rn(1.0f - alpha) * (p.gL0 - p.gacc));
+    p.T = __fmul_rn(p.T, __fsub_rn(1.0f, alpha));
   }
-  float S = 0.f, tau = 0.f, T = 1.f, gacc = 0.f;
-  const float amax = rp.alpha_max, l2min = rp.log2_alpha_min, c = rp.c;
-  // the warp walks entries up to the largest stop of its lanes
-  const uint32_t warp_last = __reduce_max_sync(kFull, last);
-  for (uint32_t base = range.x; base < range.y; base += B) {
-    bool done = base >= last;
+  // alpha = 2^e with e = L + dx (A' dx + B' dy) + C' dy^2, unless clamped at alpha_max. With
+  // w = dL/de, de/dA' = dx^2, de/dB' = dx dy, de/dC' = dy^2, de/dL = 1 and de/du = -(2A' dx + B' dy),
+  // de/dv = -(B' dx + 2C' dy): the per-splat sums of w, w dx, w dy, w dx^2, w dx dy, w dy^2 carry
+  // everything; the projection backward applies the per-splat A', B', C' (and ln 2) once.
+  float wgt = raw >= rp.alpha_max ? 0.f : dLda * alpha;  // dL/de / ln 2
+  float wdx = wgt * dx, wdy = wgt * dy;
+  v[0] += wdx;
+  v[1] += wdy;
+  v[2] = fmaf(wdx, dx, v[2]);
+  v[3] = fmaf(wdx, dy, v[3]);
+  v[4] = fmaf(wdy, dy, v[4]);
+  v[5] += wgt;
+  v[6] = fmaf(p.g0, wE, v[6]);
+  v[7] = fmaf(p.g1, wE, v[7]);
+  v[8] = fmaf(p.g2, wE, v[8]);
+  return true;
+}
+
+template <int TW, int TH, int KIND>
+__global__ void __launch_bounds__(TW* TH / kBwdPix) composite_backward_kernel(const float4* __restrict__ rec,
+                                                                        const uint32_t* __restrict__ ids,
+                                                                        const uint2* __restrict__ ranges,
+                                                                        RenderParams rp, int W, int H,
+                                                                        const float* __restrict__ dl_dimage,
+                                                                        const float4* __restrict__ state,
+                                                                        float4* __restrict__ grad2d) {
+  using G = TileGeom<TW, TH, kBwdPix>;
+  constexpr int B = G::kThreads, CH = G::kChunk;
+  static_assert(kBwdPix == 2, "the replay below is written for two pixels per thread");
+  __shared__ float4 s_r0[CH];
+  __shared__ float4 s_r1[CH];
+  __shared__ float s_e2[CH];
+  __shared__ uint32_t s_id[CH];
+  const int tile = blockIdx.x;
+  const int tx = tile % rp.tiles_x, ty = tile / rp.tiles_x;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint2 range = ranges[tile];
+  BwdPixel p[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    int x, y;
+    G::pixel(tid, k, tx * TW, ty * TH, x, y);
+    BwdPixel& q = p[k];
+    q.px = (float)x + 0.5f;
+    q.py = (float)y + 0.5f;
+    q.last = range.x;
+    q.g0 = q.g1 = q.g2 = 0.f;
+    // everything the adjoint needs is a dot product with g: quadratic keeps g.E_k and g.Theta,
+    // exponential keeps g.L0 and the running g.sum_{j<=i} E_j pbar_j
+    q.gEk = q.gTh = q.gL0 = 0.f;
+    q.S = q.tau = q.gacc = 0.f;
+    q.T = 1.f;
+    if (x < W && y < H) {
+      size_t pix = (size_t)y * W + x;
+      float4 s0 = state[2 * pix], s1 = state[2 * pix + 1];
+      q.last = range.x + (__float_as_uint(s0.x) & 0x7FFFFFFFu);
+      q.g0 = dl_dimage[3 * pix];
+      q.g1 = dl_dimage[3 * pix + 1];
+      q.g2 = dl_dimage[3 * pix + 2];
+      if (KIND == NGS_MODEL_QUAD) {
+        q.gEk = q.g0 * s0.y + q.g1 * s0.z + q.g2 * s0.w;
+        // Theta_{-1} = A - E_k taubar_k
+        q.gTh = q.g0 * (s1.x - s0.y * s1.w) + q.g1 * (s1.y - s0.z * s1.w) + q.g2 * (s1.z - s0.w * s1.w);
+      } else {
+        q.gL0 = q.g0 * s0.y + q.g1 * s0.z + q.g2 * s0.w;
+      }
+      if (q.g0 == 0.f && q.g1 == 0.f && q.g2 == 0.f) q.last = range.x;
+    }
+  }
+  // the warp walks entries up to the largest stop of its pixels
+  const uint32_t warp_last = __reduce_max_sync(kFull, max(p[0].last, p[1].last));
+  for (uint32_t base = range.x; base < range.y; base += CH) {
+    const bool done = base >= max(p[0].last, p[1].last);
     if (__syncthreads_count(done) == B) break;
-    uint32_t i = base + tid;
-    if (i < range.y) {
-      uint32_t id = ids[i];
-      s_id[tid] = id;
-      s_r0[tid] = rec[3 * (size_t)id];
-      s_r1[tid] = rec[3 * (size_t)id + 1];
-      s_e2[tid] = rec[3 * (size_t)id + 2].x;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      uint32_t i = base + k * B + tid;
+      if (i < range.y) {
+        uint32_t id = ids[i];
+        s_id[k * B + tid] = id < rp.n_gaussians ? id : 0u;
+        stage_record(rec, id, rp, s_r0[k * B + tid], s_r1[k * B + tid], s_e2[k * B + tid]);
+      }
     }
     __syncthreads();
     if (base < warp_last) {
-      int cnt = (int)(min(warp_last, min(base + (uint32_t)B, range.y)) - base);
+      const int cnt = (int)(min(warp_last, min(base + (uint32_t)CH, range.y)) - base);
       for (int j = 0; j < cnt; ++j) {
-        uint32_t pos = base + j;
-        float4 r0 = s_r0[j], r1 = s_r1[j];
-        float dx, dy;
-        float e = splat_log2_alpha(px, py, r0, r1, dx, dy);
-        bool on = pos < last && e >= l2min;
-        float gu = 0.f, gv = 0.f, gA = 0.f, gB = 0.f, gC = 0.f, gL = 0.f, gE0 = 0.f, gE1 = 0.f, gE2 = 0.f;
-        if (on) {
-          float raw = fast_exp2(e);
-          float alpha = fminf(amax, raw);
-          float E0 = r1.z, E1 = r1.w, E2 = s_e2[j];
-          float gE = fmaf(g2, E2, fmaf(g1, E1, g0 * E0));  // g.E_i
-          float dLda;
-          if (KIND == NGS_MODEL_QUAD) {
-            float pt = quad_slope(alpha, c, tau);
-            float Sn = __fadd_rn(S, pt);
-            if (Sn >= 1.0f) {  // the saturating splat k: pbar_k = 1 - S, no dependence on alpha_k
-              float pk = 1.0f - S;
-              gE0 = g0 * pk;
-              gE1 = g1 * pk;
-              gE2 = g2 * pk;
-              dLda = 0.f;
-            } else {
-              // g.dL0/dalpha_i = g.DeltaE_i (1 + c taubar_i) + c g.Theta_i, Theta_i = Theta_{i-1} - DeltaE_i alpha_i
-              float gd = gE - gEk;
-              gTh = fmaf(-gd, alpha, gTh);
-              dLda = fmaf(gd, fmaf(c, tau, 1.0f), c * gTh);
-              gE0 = g0 * pt;
-              gE1 = g1 * pt;
-              gE2 = g2 * pt;
-              S = Sn;
-              tau = __fadd_rn(tau, alpha);
-            }
-          } else {
-            // g.dL0/dalpha_i = T_i g.E_i - (g.L0 - g.sum_{j<=i} E_j pbar_j) / (1 - alpha_i)
-            float w = alpha * T;
-            gacc = fmaf(gE, w, gacc);
-            dLda = fmaf(T, gE, -__frcp_rn(1.0f - alpha) * (gL0 - gacc));
-            gE0 = g0 * w;
-            gE1 = g1 * w;
-            gE2 = g2 * w;
-            T = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-          }
-          // alpha = 2^e with e = L + dx (A' dx + B' dy) + C' dy^2, unless clamped at alpha_max. With
-          // w = dL/de, de/dA' = dx^2, de/dB' = dx dy, de/dC' = dy^2, de/dL = 1 and de/du = -(2A' dx + B' dy),
-          // de/dv = -(B' dx + 2C' dy): the per-splat sums of w, w dx, w dy, w dx^2, w dx dy, w dy^2 carry
-          // everything; the projection backward applies the per-splat A', B', C' once.
-          float wgt = raw >= amax ? 0.f : dLda * alpha;  // dL/de / ln 2 (the projection backward applies ln 2)
-          gL = wgt;
-          gu = wgt * dx;
-          gv = wgt * dy;
-          gA = gu * dx;
-          gB = gu * dy;
-          gC = gv * dy;
-        }
+        const uint32_t pos = base + j;
+        const float4 r0 = s_r0[j], r1 = s_r1[j];
+        float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        bool on = bwd_step<KIND>(p[0], r0, r1, s_e2[j], pos, rp, v);
+        on |= bwd_step<KIND>(p[1], r0, r1, s_e2[j], pos, rp, v);
         const uint32_t mask = __ballot_sync(kFull, on);
         if (mask) {
           float4* dst = grad2d + 3 * (size_t)s_id[j];
           if (__popc(mask) <= 4) {  // few lanes: add their values directly
             if (on) {
-              atomicAdd(dst, make_float4(gu, gv, gA, gB));
-              atomicAdd(dst + 1, make_float4(gC, gL, gE0, gE1));
-              atomicAdd(reinterpret_cast<float*>(dst + 2), gE2);
+              atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
+              atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
+              atomicAdd(reinterpret_cast<float*>(dst + 2), v[8]);
             }
           } else {
-            const float v[9] = {gu, gv, gA, gB, gC, gL, gE0, gE1, gE2};
             warp_reduce9_add(v, reinterpret_cast<float*>(dst), lane);
           }
         }
@@ -326,11 +370,12 @@ template <int TW, int TH>
 void forward_for_tile(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp, int W,
                       int H, float* image, int32_t* overdraw, float4* state, cudaStream_t s) {
   int ntiles = rp.tiles_x * rp.tiles_y;
+  constexpr int threads = TileGeom<TW, TH, 1>::kThreads;
   if (rp.kind == NGS_MODEL_QUAD)
-    composite_forward_kernel<TW, TH, NGS_MODEL_QUAD><<<ntiles, TW * TH, 0, s>>>(rec, ids, ranges, rp, W, H, image,
+    composite_forward_kernel<TW, TH, NGS_MODEL_QUAD><<<ntiles, threads, 0, s>>>(rec, ids, ranges, rp, W, H, image,
                                                                                   overdraw, state);
   else
-    composite_forward_kernel<TW, TH, NGS_MODEL_EXP><<<ntiles, TW * TH, 0, s>>>(rec, ids, ranges, rp, W, H, image,
+    composite_forward_kernel<TW, TH, NGS_MODEL_EXP><<<ntiles, threads, 0, s>>>(rec, ids, ranges, rp, W, H, image,
                                                                                  overdraw, state);
 }
 
@@ -338,11 +383,12 @@ template <int TW, int TH>
 void backward_for_tile(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp, int W,
                        int H, const float* dl, const float4* state, float4* grad2d, cudaStream_t s) {
   int ntiles = rp.tiles_x * rp.tiles_y;
+  constexpr int threads = TileGeom<TW, TH, kBwdPix>::kThreads;
   if (rp.kind == NGS_MODEL_QUAD)
-    composite_backward_kernel<TW, TH, NGS_MODEL_QUAD><<<ntiles, TW * TH, 0, s>>>(rec, ids, ranges, rp, W, H, dl,
+    composite_backward_kernel<TW, TH, NGS_MODEL_QUAD><<<ntiles, threads, 0, s>>>(rec, ids, ranges, rp, W, H, dl,
                                                                                    state, grad2d);
   else
-    composite_backward_kernel<TW, TH, NGS_MODEL_EXP><<<ntiles, TW * TH, 0, s>>>(rec, ids, ranges, rp, W, H, dl,
+    composite_backward_kernel<TW, TH, NGS_MODEL_EXP><<<ntiles, threads, 0, s>>>(rec, ids, ranges, rp, W, H, dl,
                                                                                   state, grad2d);
 }
 

@@ -30,7 +30,11 @@ struct RenderParams {
   int tile_w, tile_h, tiles_x, tiles_y;
   int max_splats;
   int sh_degree;
+  uint32_t n_gaussians;
+  uint32_t* check;       // device error word: kernels OR in a kCheck* bit when a bounds check fires
 };
+
+constexpr uint32_t kCheckIndex = 1u;  // a sorted pair named a Gaussian index >= n
 
 // Splat record: 3 float4 per Gaussian.
 //   r0 = (u, v, A', B'), r1 = (C', L, E0, E1), r2 = (E2, z, rx, ry)
@@ -95,8 +99,8 @@ struct ngs_ctx {
   ngs::DevBuf hist;      // radix histograms
   ngs::DevBuf scan_tmp;  // block sums of scans
   ngs::DevBuf grad2d;    // per-Gaussian splat-record gradients (backward)
-  ngs::DevBuf total;     // device-side pair count (uint64)
-  uint64_t* h_total = nullptr;  // pinned mirror of `total`
+  ngs::DevBuf total;     // device-side pair count (uint64) and error word (uint64)
+  uint64_t* h_total = nullptr;  // pinned mirror of `total` (2 words)
   bool timing = false;
   struct Pending { cudaEvent_t a, b; int stage; };
   std::vector<Pending> pending;

@@ -65,10 +65,14 @@ __global__ void __launch_bounds__(kThreads) upsweep_kernel(const K* __restrict__
   for (int i = tid; i < kWarps * kDigits; i += kThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
   uint32_t base = blockIdx.x * (uint32_t)kTile;
+  const int lane = tid & 31;
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
     uint32_t idx = base + j * kThreads + tid;
-    if (idx < n) atomicAdd(&s_hist[warp][digit_of(keys[idx], shift)], 1u);
+    uint32_t d = idx < n ? digit_of(keys[idx], shift) : (uint32_t)kDigits;
+    // one shared-memory atomic per distinct digit of the warp (neighbouring keys often share digits)
+    uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    if (d < (uint32_t)kDigits && lane == __ffs(peers) - 1) atomicAdd(&s_hist[warp][d], (uint32_t)__popc(peers));
   }
   __syncthreads();
   for (int d = tid; d < kDigits; d += kThreads) {
