@@ -119,9 +119,10 @@ struct ProjState {
   float qn[4], qnorm;      // normalised quaternion and the raw norm
   float Rq[9], S[3];       // rotation and scales
   float M[9];              // Rq diag(S)
-  float Sig[9];            // world covariance (full symmetric)
   float T[6];              // J W
-  float s00, s01, s11;     // 2D covariance incl. dilation
+  float U[6];              // T M: column i is the projected axis i, S_i T Rq e_i
+  float s00, s01, s11;     // 2D covariance U U^T + dilation I
+  float det;               // its determinant
   float A, B, C;           // conic
   float aleph;
   float dir[3], dnorm;     // unit direction from the camera centre, |p - campos|
@@ -172,11 +173,6 @@ __device__ __forceinline__ void forward_map(const ngs_gaussians& g, const CamPar
   for (int r = 0; r < 3; ++r)
 #pragma unroll
     for (int c = 0; c < 3; ++c) st.M[3 * r + c] = st.Rq[3 * r + c] * st.S[c];
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      st.Sig[3 * r + c] = st.M[3 * r] * st.M[3 * c] + st.M[3 * r + 1] * st.M[3 * c + 1] + st.M[3 * r + 2] * st.M[3 * c + 2];
   float j00 = cam.fx * st.iz, j02 = -cam.fx * st.x * st.iz * st.iz;
   float j11 = cam.fy * st.iz, j12 = -cam.fy * st.y * st.iz * st.iz;
 #pragma unroll
@@ -184,17 +180,24 @@ __device__ __forceinline__ void forward_map(const ngs_gaussians& g, const CamPar
     st.T[c] = j00 * cam.R[c] + j02 * cam.R[6 + c];
     st.T[3 + c] = j11 * cam.R[3 + c] + j12 * cam.R[6 + c];
   }
-  float TS0[3], TS1[3];
+  // projected axes U = T M; Sigma' = U U^T + dilation I. Its determinant by Cauchy-Binet,
+  // det = sum_{i<j} (u_i x u_j)^2 + dilation tr(U U^T) + dilation^2, has no cancellation when the splat is
+  // a thin needle (det(Sigma') as s00 s11 - s01^2 would lose most of its digits).
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    TS0[c] = st.T[0] * st.Sig[c] + st.T[1] * st.Sig[3 + c] + st.T[2] * st.Sig[6 + c];
-    TS1[c] = st.T[3] * st.Sig[c] + st.T[4] * st.Sig[3 + c] + st.T[5] * st.Sig[6 + c];
+    st.U[c] = st.T[0] * st.M[c] + st.T[1] * st.M[3 + c] + st.T[2] * st.M[6 + c];
+    st.U[3 + c] = st.T[3] * st.M[c] + st.T[4] * st.M[3 + c] + st.T[5] * st.M[6 + c];
   }
-  st.s00 = TS0[0] * st.T[0] + TS0[1] * st.T[1] + TS0[2] * st.T[2] + rp.dilation;
-  st.s01 = TS0[0] * st.T[3] + TS0[1] * st.T[4] + TS0[2] * st.T[5];
-  st.s11 = TS1[0] * st.T[3] + TS1[1] * st.T[4] + TS1[2] * st.T[5] + rp.dilation;
-  float det = st.s00 * st.s11 - st.s01 * st.s01;
-  float idet = 1.f / det;
+  float t00 = st.U[0] * st.U[0] + st.U[1] * st.U[1] + st.U[2] * st.U[2];
+  float t11 = st.U[3] * st.U[3] + st.U[4] * st.U[4] + st.U[5] * st.U[5];
+  st.s00 = t00 + rp.dilation;
+  st.s01 = st.U[0] * st.U[3] + st.U[1] * st.U[4] + st.U[2] * st.U[5];
+  st.s11 = t11 + rp.dilation;
+  float m01 = st.U[0] * st.U[4] - st.U[1] * st.U[3];
+  float m02 = st.U[0] * st.U[5] - st.U[2] * st.U[3];
+  float m12 = st.U[1] * st.U[5] - st.U[2] * st.U[4];
+  st.det = m01 * m01 + m02 * m02 + m12 * m12 + rp.dilation * (t00 + t11) + rp.dilation * rp.dilation;
+  float idet = 1.f / st.det;
   st.A = st.s11 * idet;
   st.B = -st.s01 * idet;
   st.C = st.s00 * idet;
@@ -322,8 +325,7 @@ __global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, CamParams
   if (z > rp.near_plane) {
     ProjState<DEG> st;
     forward_map<DEG, VEC>(g, cam, rp, i, st);
-    float det = st.s00 * st.s11 - st.s01 * st.s01;
-    if (det > 0.f && st.aleph >= rp.alpha_min && isfinite(st.A) && isfinite(st.C)) {
+    if (st.det > 0.f && st.aleph >= rp.alpha_min && isfinite(st.A) && isfinite(st.C)) {
       float u = cam.fx * st.x * st.iz + cam.cx;
       float v = cam.fy * st.y * st.iz + cam.cy;
       float L = log2f(st.aleph);
@@ -412,37 +414,42 @@ __global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, 
   float dA = g0.z * kConicScale, dB = g0.w * 2.f * kConicScale, dC = g1.x * kConicScale;
   float dE[3] = {g1.z, g1.w, g2.x};
   out.d_opacity_logits[i] = g1.y * (1.f - st.aleph) / kLn2;  // L = log2(sigmoid(logit))
-  // conic Q = Sigma2^-1: dLoss/dSigma2 = -Q G Q, G = [[dA, dB/2], [dB/2, dC]]
-  float QG00 = st.A * dA + st.B * 0.5f * dB, QG01 = st.A * 0.5f * dB + st.B * dC;
-  float QG10 = st.B * dA + st.C * 0.5f * dB, QG11 = st.B * 0.5f * dB + st.C * dC;
-  float H00 = -(QG00 * st.A + QG01 * st.B);
-  float H01 = -(QG00 * st.B + QG01 * st.C);
-  float H11 = -(QG10 * st.B + QG11 * st.C);
-  float H[4] = {H00, H01, H01, H11};
-  // Sigma2 = T Sig T^T: dSig = T^T H T, dT = 2 H T Sig
-  float dSig[9];
+  // conic Q = Sigma'^-1 with Sigma' = U U^T + dilation I: dLoss/dSigma' = -Q G Q, G = [[dA, dB/2], [dB/2, dC]].
+  // Every term of the chain is needed only as Hs u_i = -Q G Q u_i for the projected axes u_i (columns of U):
+  //   dLoss/dM (column i) = 2 T^T Hs u_i,   dLoss/dT = 2 sum_i (Hs u_i) M_i^T.
+  // Q u_i is formed by Sherman-Morrison from R_i = Sigma' - u_i u_i^T (the other two axes plus dilation):
+  //   Q u_i = R_i^-1 u_i / (1 + u_i^T R_i^-1 u_i),
+  // which stays accurate for thin needles, where Q u_i along the long axis is a small difference of large
+  // terms if formed directly.
+  const float dil = rp.dilation;
+  const float hG01 = 0.5f * dB;
+  float HU[6];  // [2][3]: Hs u_i
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int j = ax == 0 ? 1 : 0, k = ax == 2 ? 1 : 2;
+    const float ui0 = st.U[ax], ui1 = st.U[3 + ax];
+    const float uj0 = st.U[j], uj1 = st.U[3 + j], uk0 = st.U[k], uk1 = st.U[3 + k];
+    const float r00 = uj0 * uj0 + uk0 * uk0 + dil, r01 = uj0 * uj1 + uk0 * uk1, r11 = uj1 * uj1 + uk1 * uk1 + dil;
+    const float mjk = uj0 * uk1 - uk0 * uj1;
+    const float detR = mjk * mjk + dil * (uj0 * uj0 + uj1 * uj1 + uk0 * uk0 + uk1 * uk1) + dil * dil;
+    const float a0 = (r11 * ui0 - r01 * ui1) / detR, a1 = (r00 * ui1 - r01 * ui0) / detR;
+    const float den = 1.f + ui0 * a0 + ui1 * a1;
+    const float q0 = a0 / den, q1 = a1 / den;           // Q u_i
+    const float g0 = dA * q0 + hG01 * q1, g1 = hG01 * q0 + dC * q1;  // G Q u_i
+    HU[ax] = -(st.A * g0 + st.B * g1);
+    HU[3 + ax] = -(st.B * g0 + st.C * g1);
+  }
+  float dM[9];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float acc = 0.f;
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) acc += st.T[3 * a + r] * H[2 * a + b] * st.T[3 * b + c];
-      dSig[3 * r + c] = acc;
-    }
-  float HT[6];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) HT[3 * a + c] = H[2 * a] * st.T[c] + H[2 * a + 1] * st.T[3 + c];
+    for (int c = 0; c < 3; ++c) dM[3 * r + c] = 2.f * (st.T[r] * HU[c] + st.T[3 + r] * HU[3 + c]);
   float dT[6];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      dT[3 * a + c] = 2.f * (HT[3 * a] * st.Sig[c] + HT[3 * a + 1] * st.Sig[3 + c] + HT[3 * a + 2] * st.Sig[6 + c]);
+      dT[3 * a + c] = 2.f * (HU[3 * a] * st.M[3 * c] + HU[3 * a + 1] * st.M[3 * c + 1] + HU[3 * a + 2] * st.M[3 * c + 2]);
   // T = J W: dJ = dT W^T (only the four nonzero entries of J)
   float dJ00 = dT[0] * cam.R[0] + dT[1] * cam.R[1] + dT[2] * cam.R[2];
   float dJ02 = dT[0] * cam.R[6] + dT[1] * cam.R[7] + dT[2] * cam.R[8];
@@ -456,15 +463,14 @@ __global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, 
   float gm[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) gm[c] = cam.R[c] * dvx + cam.R[3 + c] * dvy + cam.R[6 + c] * dvz;
-  // Sig = M M^T: dM = 2 dSig M; M = Rq diag(S)
+  // M = Rq diag(S)
   float dRq[9], dS[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      float dMrc = 2.f * (dSig[3 * r] * st.M[c] + dSig[3 * r + 1] * st.M[3 + c] + dSig[3 * r + 2] * st.M[6 + c]);
-      dRq[3 * r + c] = dMrc * st.S[c];
-      dS[c] += dMrc * st.Rq[3 * r + c];
+      dRq[3 * r + c] = dM[3 * r + c] * st.S[c];
+      dS[c] += dM[3 * r + c] * st.Rq[3 * r + c];
     }
 #pragma unroll
   for (int c = 0; c < 3; ++c) dls[c] = dS[c] * st.S[c];
