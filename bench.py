@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--width", type=int, default=1920)
     p.add_argument("--height", type=int, default=1080)
     p.add_argument("--tile", default="16x16")
+    p.add_argument("--chunk", type=int, default=0, help="records staged per round (0: tile pixels)")
+    p.add_argument("--schedule", default="tiles", choices=["tiles", "persistent"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-crop", type=int, default=0, help="oracle crop side (0: sized automatically)")
@@ -144,7 +146,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     tw, th = (int(v) for v in args.tile.split("x"))
-    opts = dict(tile_w=tw, tile_h=th)
+    opts = dict(tile_w=tw, tile_h=th, chunk=args.chunk, schedule=args.schedule)
 
     scene, cam = workload(args, rank)
     H, W = cam["height"], cam["width"]
@@ -241,7 +243,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "gaussians": args.gaussians, "width": W, "height": H, "sh_degree": 3,
                    "models": {"exp": "exponential", "sub": "quadratic c=-0.5", "lin": "quadratic c=0",
                               "sup": "quadratic c=+0.5"},
-                   "tile": args.tile, "step": "per model: render + path-replay backward",
+                   "tile": args.tile, "chunk": args.chunk, "schedule": args.schedule, "step": "per model: render + path-replay backward",
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"views x{world}",
                    "pairs_per_view": int(frames["exp"].view()["n_pairs"])},
         "per_model": per_model,

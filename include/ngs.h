@@ -92,8 +92,15 @@ typedef struct {
   int32_t tile_w, tile_h; /* screen tile: 8x8, 16x16 (default) or 16x32; the image does not depend on it */
   int32_t max_splats;  /* 0 = unlimited, else at most this many splats composited per pixel (the    */
                        /* paper's ray tracer caps at 128, Sec. 5.1 "Renderer")                       */
-  int32_t reserved;    /* must be 0                                                                  */
-} ngs_options;
+  int32_t chunk;       /* splat records staged in shared memory per round of a tile's list walk:      */
+                       /* 0 = the tile's pixel count (default), else half, equal to or twice it       */
+  int32_t schedule;    /* NGS_SCHEDULE_TILES (default) or NGS_SCHEDULE_PERSISTENT                     */
+} ngs_options;         /* tile shape, chunk and schedule change the speed, never the results          */
+
+/* Composite schedules: one CTA per screen tile in tile order, or one wave of persistent CTAs that take
+ * tiles from a list ordered by descending (tile, splat) pair count, so that the longest tiles start first. */
+#define NGS_SCHEDULE_TILES 0
+#define NGS_SCHEDULE_PERSISTENT 1
 
 /* Gradient outputs of ngs_render_backward, same shapes as ngs_gaussians' arrays. OVERWRITTEN. */
 typedef struct {
@@ -104,22 +111,28 @@ typedef struct {
   float* d_sh;
 } ngs_grads;
 
-/* Read-only view of a frame's device buffers (valid until the frame's next render or destruction). */
+/* Read-only view of a frame's buffers (valid until the frame's next render or destruction). A frame
+ * rendered from n_views cameras (ngs_render_batch) packs its views one after the other: splat record
+ * r = v n + i belongs to view v and Gaussian i; view v's tiles have the global indices
+ * [view_tile_base[v], view_tile_base[v + 1]) (local tile ty * tiles_x_v + tx), and its pixels the packed
+ * indices [view_pixel_base[v], view_pixel_base[v + 1]) (local pixel y * width_v + x). */
 typedef struct {
   int64_t n_gaussians;
-  int64_t n_pairs;          /* number of (tile, Gaussian) pairs after binning                         */
-  int32_t tiles_x, tiles_y;
-  int32_t width, height;
+  int64_t n_pairs;          /* number of (tile, splat record) pairs after binning                     */
+  int32_t tiles_x, tiles_y; /* of view 0                                                              */
+  int32_t width, height;    /* of view 0                                                              */
   float log2_alpha_min;     /* FP32 threshold of the alpha test on the exponent                       */
-  int32_t reserved;
-  const float* records;     /* [n][12] splat records: u, v, A', B', C', L, E0, E1, E2, z, rx, ry with  */
-                            /*   (A', B', C') = -log2(e)/2 (A, 2B, C) of the conic, L = log2 aleph, z  */
-                            /*   the FP32 view depth, (rx, ry) the half extents of the alpha >= alpha_min */
-                            /*   ellipse's bounding box (0: no tile)                                  */
-  const uint64_t* keys;     /* [n_pairs] sorted keys (tile << 32) | bits(z)                           */
-  const uint32_t* values;   /* [n_pairs] Gaussian index of each key                                   */
-  const uint32_t* ranges;   /* [tiles][2] [start, end) of each tile's pairs                           */
-  const float* pixel_state; /* [height][width][8] replay state written by the forward pass            */
+  int32_t n_views;
+  const float* records;     /* device [n_views n][12] splat records: u, v, A', B', C', L, E0, E1, E2,  */
+                            /*   z, rx, ry with (A', B', C') = -log2(e)/2 (A, 2B, C) of the conic,      */
+                            /*   L = log2 aleph, z the FP32 view depth, (rx, ry) the half extents of   */
+                            /*   the alpha >= alpha_min ellipse's bounding box (0: no tile)            */
+  const uint64_t* keys;     /* device [n_pairs] sorted keys (global tile << 32) | bits(z)             */
+  const uint32_t* values;   /* device [n_pairs] splat record index of each key                        */
+  const uint32_t* ranges;   /* device [tiles][2] [start, end) of each global tile's pairs             */
+  const float* pixel_state; /* device [pixels][8] replay state written by the forward pass            */
+  const int64_t* view_pixel_base; /* HOST [n_views + 1]                                               */
+  const uint32_t* view_tile_base; /* HOST [n_views + 1]                                               */
 } ngs_frame_view;
 
 /* Fill `out` with the default options above. */
@@ -150,10 +163,25 @@ NGS_API void ngs_frame_destroy(ngs_frame* frame);
  * memory; overdraw may be NULL. The frame is overwritten. One host synchronisation happens after
  * binning, to read the number of (tile, Gaussian) pairs and size the sort buffers.
  * Errors: NGS_ERR_INVALID_ARG for NULL pointers, n < 0, sh_degree outside 0..3, width/height outside
- * 1..16384, an unsupported tile shape, kind/param outside the table above, nonzero `reserved`. */
+ * 1..16384, an unsupported tile shape, chunk or schedule, kind/param outside the table above. */
 NGS_API int ngs_render(ngs_ctx* ctx, ngs_frame* frame, const ngs_gaussians* g, const ngs_camera* cam,
                        const ngs_model* model, const ngs_options* opt, float* image, int32_t* overdraw,
                        void* stream);
+
+/* Render one set of Gaussians from n_views cameras (1 <= n_views <= 4096) of any sizes in one pass of the
+ * pipeline: one projection launch for all (view, Gaussian) pairs, in which the views of a block of
+ * Gaussians run side by side so the parameters are read from HBM once; one segmented depth sort; one
+ * binning into global tiles (view v's tiles follow those of views 0..v-1); one tile sort; one composite
+ * launch over the tiles of all views. Each view's image and overdraw are bit-identical to ngs_render of
+ * that camera alone with the same options (the same per-tile splat lists and arithmetic).
+ * `cams` is a HOST array [n_views]. `images` packs the views one after the other: view v occupies pixels
+ * [P_v, P_v + H_v W_v) with P_v = sum_{u<v} H_u W_u, so images is [sum H_v W_v][3] and overdraw (may be
+ * NULL) [sum H_v W_v]. One host synchronisation, as in ngs_render. n * n_views must be below 2^32.
+ * ngs_render_backward of a batch frame takes dl_dimage packed the same way and writes the gradient of the
+ * sum over the views. Errors: those of ngs_render, and n_views out of range. */
+NGS_API int ngs_render_batch(ngs_ctx* ctx, ngs_frame* frame, const ngs_gaussians* g, const ngs_camera* cams,
+                             int32_t n_views, const ngs_model* model, const ngs_options* opt, float* images,
+                             int32_t* overdraw, void* stream);
 
 /* Path-replay backward of the frame's last render (App. C: recursive adjoints computed front to back by
  * replaying each pixel's splat list, recomputing alpha_i and taubar_i instead of storing per-splat state).
@@ -169,14 +197,16 @@ NGS_API int ngs_render_backward(ngs_ctx* ctx, const ngs_frame* frame, const ngs_
  * synchronise the device). The paper has no counterpart: this is an interface addition. Same arguments
  * and results as ngs_render_backward, but the per-Gaussian scratch lives in one static device array of
  * 12 MiB that every GPU loading the library holds until the process exits, and nothing is allocated.
- * Limits: at most 262,144 Gaussians (larger frames return NGS_ERR_INVALID_ARG with a message naming the
- * limit). All calls on a device share the array; each call clears what it uses first, and calls that
+ * Limits: at most 262,144 splat records, Gaussians x views (larger frames return NGS_ERR_INVALID_ARG with
+ * a message naming the limit). All calls on a device share the array; each call clears what it uses first, and calls that
  * overlap on the GPU (unordered streams or threads) race on it. The first call on a device, with that
  * device current, looks up the array's address (cudaGetSymbolAddress); make it before any stream capture. */
 NGS_API int ngs_render_backward_static(ngs_ctx* ctx, const ngs_frame* frame, const ngs_gaussians* g,
                                        const float* dl_dimage, const ngs_grads* out, void* stream);
 
-/* Fill `out` with device pointers into the frame (for tests and diagnostics). */
+/* Fill `out` with pointers into the frame (for tests and diagnostics). The render path sorts 32-bit tile
+ * indices only (the splats are already in depth order); this call composes the 64-bit keys from them and
+ * the records, and synchronises the device to do so. */
 NGS_API int ngs_frame_view_get(const ngs_frame* frame, ngs_frame_view* out);
 
 /* Stage timing. When enabled, every render/backward records CUDA events on its stream around each

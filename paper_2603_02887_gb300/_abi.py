@@ -16,6 +16,8 @@ NGS_ERR_CUDA = -3
 NGS_ERR_DEVICE_CHECK = -5
 NGS_MODEL_EXP = 0
 NGS_MODEL_QUAD = 1
+NGS_SCHEDULE_TILES = 0
+NGS_SCHEDULE_PERSISTENT = 1
 NGS_NUM_STAGES = 8
 STAGES = ("project", "depth_sort", "scan_emit", "tile_sort", "tile_ranges", "composite_fwd", "composite_bwd",
           "project_bwd")
@@ -38,7 +40,7 @@ class Model(C.Structure):
 class Options(C.Structure):
     _fields_ = [("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_eps", C.c_float), ("dilation", C.c_float),
                 ("near_plane", C.c_float), ("background", C.c_float * 3), ("tile_w", C.c_int32),
-                ("tile_h", C.c_int32), ("max_splats", C.c_int32), ("reserved", C.c_int32)]
+                ("tile_h", C.c_int32), ("max_splats", C.c_int32), ("chunk", C.c_int32), ("schedule", C.c_int32)]
 
 
 class Grads(C.Structure):
@@ -48,9 +50,10 @@ class Grads(C.Structure):
 
 class FrameView(C.Structure):
     _fields_ = [("n_gaussians", C.c_int64), ("n_pairs", C.c_int64), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32),
-                ("width", C.c_int32), ("height", C.c_int32), ("log2_alpha_min", C.c_float), ("reserved", C.c_int32),
+                ("width", C.c_int32), ("height", C.c_int32), ("log2_alpha_min", C.c_float), ("n_views", C.c_int32),
                 ("records", C.c_void_p), ("keys", C.c_void_p),
-                ("values", C.c_void_p), ("ranges", C.c_void_p), ("pixel_state", C.c_void_p)]
+                ("values", C.c_void_p), ("ranges", C.c_void_p), ("pixel_state", C.c_void_p),
+                ("view_pixel_base", C.c_void_p), ("view_tile_base", C.c_void_p)]
 
 
 #: every function declared in include/ngs.h, with its ctypes signature
@@ -63,6 +66,8 @@ SIGNATURES = {
     "ngs_frame_destroy": (None, [C.c_void_p]),
     "ngs_render": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.POINTER(Camera), C.POINTER(Model),
                              C.POINTER(Options), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ngs_render_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.POINTER(Camera), C.c_int32,
+                                   C.POINTER(Model), C.POINTER(Options), C.c_void_p, C.c_void_p, C.c_void_p]),
     "ngs_render_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.c_void_p, C.POINTER(Grads),
                                       C.c_void_p]),
     "ngs_render_backward_static": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.c_void_p,

@@ -79,6 +79,8 @@ static int check_launch(ngs_ctx* ctx, const char* what) {
   return NGS_OK;
 }
 
+constexpr int kMaxViews = 4096;
+
 static int tile_bits(uint32_t ntiles) {
   int b = 0;
   while (b < 32 && (1ull << b) < ntiles) ++b;
@@ -157,25 +159,32 @@ NGS_API int ngs_frame_create(ngs_ctx* ctx, ngs_frame** out) {
 NGS_API void ngs_frame_destroy(ngs_frame* f) {
   if (!f) return;
   cudaDeviceSynchronize();
-  DevBuf* bufs[] = {&f->rec, &f->tile_count, &f->gkeys[0], &f->gkeys[1], &f->gvals[0], &f->gvals[1],
-                    &f->offsets, &f->pkeys[0], &f->pkeys[1], &f->pvals[0], &f->pvals[1], &f->ranges, &f->state};
+  DevBuf* bufs[] = {&f->rec,     &f->tile_count, &f->gkeys[0], &f->gkeys[1], &f->gvals[0], &f->gvals[1],
+                    &f->offsets, &f->ptile[0],   &f->ptile[1], &f->pvals[0], &f->pvals[1], &f->ranges,
+                    &f->state,   &f->views,      &f->keys64,   &f->work,     &f->sched};
   for (DevBuf* b : bufs) free_buf(*b);
+  if (f->h_views) cudaFreeHost(f->h_views);
+  if (f->views_uploaded) cudaEventDestroy(f->views_uploaded);
   delete f;
 }
 
-static int check_inputs(ngs_ctx* ctx, const ngs_gaussians* g, const ngs_camera* cam, const ngs_model* model,
-                        const ngs_options* o) {
-  if (!g || !cam || !model || !o) return fail(ctx, NGS_ERR_INVALID_ARG, "null argument");
-  if (g->n < 0 || g->n >= (1ll << 31)) return fail(ctx, NGS_ERR_INVALID_ARG, "n out of range [0, 2^31)");
-  if (g->sh_degree < 0 || g->sh_degree > 3) return fail(ctx, NGS_ERR_INVALID_ARG, "sh_degree must be 0..3");
-  if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
-    return fail(ctx, NGS_ERR_INVALID_ARG, "null Gaussian parameter array");
+static int check_camera(ngs_ctx* ctx, const ngs_camera* cam) {
+  if (!cam) return fail(ctx, NGS_ERR_INVALID_ARG, "null camera");
   if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
     return fail(ctx, NGS_ERR_INVALID_ARG, "image size out of range 1..16384");
   if (!(cam->fx > 0) || !(cam->fy > 0) || !isfinite(cam->cx) || !isfinite(cam->cy))
     return fail(ctx, NGS_ERR_INVALID_ARG, "invalid intrinsics");
   for (int i = 0; i < 12; ++i)
     if (!isfinite(cam->viewmat[i])) return fail(ctx, NGS_ERR_INVALID_ARG, "non-finite view matrix");
+  return NGS_OK;
+}
+
+static int check_inputs(ngs_ctx* ctx, const ngs_gaussians* g, const ngs_model* model, const ngs_options* o) {
+  if (!g || !model || !o) return fail(ctx, NGS_ERR_INVALID_ARG, "null argument");
+  if (g->n < 0 || g->n >= (1ll << 31)) return fail(ctx, NGS_ERR_INVALID_ARG, "n out of range [0, 2^31)");
+  if (g->sh_degree < 0 || g->sh_degree > 3) return fail(ctx, NGS_ERR_INVALID_ARG, "sh_degree must be 0..3");
+  if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+    return fail(ctx, NGS_ERR_INVALID_ARG, "null Gaussian parameter array");
   if (model->kind == NGS_MODEL_QUAD) {
     if (!(model->param >= -0.5f) || !isfinite(model->param))
       return fail(ctx, NGS_ERR_INVALID_ARG, "quadratic model needs c >= -0.5");
@@ -188,23 +197,19 @@ static int check_inputs(ngs_ctx* ctx, const ngs_gaussians* g, const ngs_camera* 
   if (!(o->alpha_min > 0.f && o->alpha_min < 1.f) || !(o->alpha_max > o->alpha_min && o->alpha_max <= 1.f))
     return fail(ctx, NGS_ERR_INVALID_ARG, "need 0 < alpha_min < alpha_max <= 1");
   if (!(o->t_eps >= 0.f && o->t_eps < 1.f) || !(o->dilation >= 0.f) || !(o->near_plane > 0.f) ||
-      o->max_splats < 0 || o->reserved != 0)
+      o->max_splats < 0)
     return fail(ctx, NGS_ERR_INVALID_ARG, "invalid option value");
+  const int P = o->tile_w * o->tile_h;
+  if (o->chunk != 0 && o->chunk != P / 2 && o->chunk != P && o->chunk != 2 * P)
+    return fail(ctx, NGS_ERR_INVALID_ARG, "chunk must be 0 or half, once or twice the tile's pixel count");
+  if (o->schedule != NGS_SCHEDULE_TILES && o->schedule != NGS_SCHEDULE_PERSISTENT)
+    return fail(ctx, NGS_ERR_INVALID_ARG, "unknown schedule");
   for (int i = 0; i < 3; ++i)
     if (!isfinite(o->background[i])) return fail(ctx, NGS_ERR_INVALID_ARG, "non-finite background");
   return NGS_OK;
 }
 
-NGS_API int ngs_render(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const ngs_camera* cam,
-                       const ngs_model* model, const ngs_options* o, float* image, int32_t* overdraw, void* stream) {
-  if (!ctx) return NGS_ERR_INVALID_ARG;
-  if (!f || f->ctx != ctx) return fail(ctx, NGS_ERR_INVALID_ARG, "frame missing or from another context");
-  NGS_TRY(check_inputs(ctx, g, cam, model, o));
-  if (!image) return fail(ctx, NGS_ERR_INVALID_ARG, "null image");
-  cudaStream_t s = (cudaStream_t)stream;
-  f->has_render = false;
-
-  CamParams cp;
+static void camera_params(const ngs_camera* cam, CamParams& cp) {
   for (int r = 0; r < 3; ++r) {
     for (int c = 0; c < 3; ++c) cp.R[3 * r + c] = cam->viewmat[4 * r + c];
     cp.t[r] = cam->viewmat[4 * r + 3];
@@ -217,7 +222,76 @@ NGS_API int ngs_render(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const
   cp.cy = cam->cy;
   cp.W = cam->width;
   cp.H = cam->height;
+}
+
+// Upload the frame's view table through its pinned staging buffer. The staging is rewritten only after
+// the previous upload from it has completed.
+static int upload_views(ngs_ctx* ctx, ngs_frame* f, cudaStream_t s) {
+  size_t bytes = sizeof(ViewParams) * f->view_host.size();
+  if (f->views_uploaded) {
+    cudaError_t e = cudaEventSynchronize(f->views_uploaded);
+    if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("view table upload: ") + cudaGetErrorString(e));
+  } else if (cudaEventCreateWithFlags(&f->views_uploaded, cudaEventDisableTiming) != cudaSuccess) {
+    f->views_uploaded = nullptr;
+    return fail(ctx, NGS_ERR_CUDA, "cudaEventCreate failed");
+  }
+  if (f->h_views_cap < f->view_host.size()) {
+    if (f->h_views) cudaFreeHost(f->h_views);
+    f->h_views = nullptr;
+    f->h_views_cap = 0;
+    if (cudaMallocHost((void**)&f->h_views, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      f->h_views = nullptr;
+      return fail(ctx, NGS_ERR_OUT_OF_MEMORY, "pinned allocation of the view table failed");
+    }
+    f->h_views_cap = f->view_host.size();
+  }
+  NGS_TRY(ensure(ctx, f->views, bytes));
+  memcpy(f->h_views, f->view_host.data(), bytes);
+  cudaError_t e = cudaMemcpyAsync(f->views.p, f->h_views, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(f->views_uploaded, s);
+  if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("view table upload: ") + cudaGetErrorString(e));
+  return NGS_OK;
+}
+
+// The render pipeline for n_views cameras of one set of Gaussians (n_views = 1 for ngs_render).
+static int render_views(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const ngs_camera* cams, int n_views,
+                        const ngs_model* model, const ngs_options* o, float* image, int32_t* overdraw,
+                        cudaStream_t s) {
+  if (!f || f->ctx != ctx) return fail(ctx, NGS_ERR_INVALID_ARG, "frame missing or from another context");
+  NGS_TRY(check_inputs(ctx, g, model, o));
+  if (!cams) return fail(ctx, NGS_ERR_INVALID_ARG, "null camera");
+  if (n_views < 1 || n_views > kMaxViews) return fail(ctx, NGS_ERR_INVALID_ARG, "n_views out of range 1..4096");
+  for (int v = 0; v < n_views; ++v) NGS_TRY(check_camera(ctx, &cams[v]));
+  if (!image) return fail(ctx, NGS_ERR_INVALID_ARG, "null image");
+  f->has_render = false;
+
+  // views, packed: tiles and pixels of view v follow those of views 0..v-1
+  f->view_host.resize(n_views);
+  f->pix_base.assign(n_views + 1, 0);
+  f->tile_base.assign(n_views + 1, 0);
+  uint64_t tiles_total = 0, pix_total = 0;
+  for (int v = 0; v < n_views; ++v) {
+    ViewParams& vp = f->view_host[v];
+    memset(&vp, 0, sizeof vp);
+    camera_params(&cams[v], vp.cam);
+    vp.tiles_x = (cams[v].width + o->tile_w - 1) / o->tile_w;
+    vp.tiles_y = (cams[v].height + o->tile_h - 1) / o->tile_h;
+    vp.tile_base = (uint32_t)tiles_total;
+    vp.pix_base = pix_total;
+    f->tile_base[v] = (uint32_t)tiles_total;
+    f->pix_base[v] = (int64_t)pix_total;
+    tiles_total += (uint64_t)vp.tiles_x * vp.tiles_y;
+    pix_total += (uint64_t)cams[v].width * cams[v].height;
+    if (tiles_total >= (1ull << 31)) return fail(ctx, NGS_ERR_INVALID_ARG, "more than 2^31 tiles in the batch");
+  }
+  f->tile_base[n_views] = (uint32_t)tiles_total;
+  f->pix_base[n_views] = (int64_t)pix_total;
+  const uint64_t records64 = (uint64_t)g->n * (uint64_t)n_views;
+  if (records64 >= (1ull << 32)) return fail(ctx, NGS_ERR_INVALID_ARG, "n * n_views must be below 2^32");
+
   RenderParams rp;
+  memset(&rp, 0, sizeof rp);
   rp.alpha_min = o->alpha_min;
   rp.alpha_max = o->alpha_max;
   rp.t_eps = o->t_eps;
@@ -229,54 +303,62 @@ NGS_API int ngs_render(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const
   rp.kind = model->kind;
   rp.tile_w = o->tile_w;
   rp.tile_h = o->tile_h;
-  rp.tiles_x = (cam->width + o->tile_w - 1) / o->tile_w;
-  rp.tiles_y = (cam->height + o->tile_h - 1) / o->tile_h;
+  rp.tiles_x = f->view_host[0].tiles_x;
+  rp.tiles_y = f->view_host[0].tiles_y;
+  rp.width = cams[0].width;
+  rp.height = cams[0].height;
   rp.max_splats = o->max_splats;
+  rp.chunk = o->chunk ? o->chunk : o->tile_w * o->tile_h;
+  rp.schedule = o->schedule;
   rp.sh_degree = g->sh_degree;
   rp.n_gaussians = (uint32_t)g->n;
-  uint32_t n = (uint32_t)g->n;
-  uint32_t ntiles = (uint32_t)rp.tiles_x * (uint32_t)rp.tiles_y;
-  size_t npix = (size_t)cam->width * cam->height;
+  rp.n_views = (uint32_t)n_views;
+  rp.n_records = (uint32_t)records64;
+  rp.n_tiles = (uint32_t)tiles_total;
+  const uint32_t n = (uint32_t)g->n, R = rp.n_records, ntiles = rp.n_tiles;
 
-  NGS_TRY(ensure(ctx, f->rec, sizeof(float4) * 3 * (size_t)std::max(n, 1u)));
-  NGS_TRY(ensure(ctx, f->tile_count, sizeof(uint32_t) * (size_t)std::max(n, 1u)));
+  NGS_TRY(ensure(ctx, f->rec, sizeof(float4) * 3 * (size_t)std::max(R, 1u)));
+  NGS_TRY(ensure(ctx, f->tile_count, sizeof(uint32_t) * (size_t)std::max(R, 1u)));
   for (int k = 0; k < 2; ++k) {
-    NGS_TRY(ensure(ctx, f->gkeys[k], sizeof(uint32_t) * (size_t)std::max(n, 1u)));
-    NGS_TRY(ensure(ctx, f->gvals[k], sizeof(uint32_t) * (size_t)std::max(n, 1u)));
+    NGS_TRY(ensure(ctx, f->gkeys[k], sizeof(uint32_t) * (size_t)std::max(R, 1u)));
+    NGS_TRY(ensure(ctx, f->gvals[k], sizeof(uint32_t) * (size_t)std::max(R, 1u)));
   }
-  NGS_TRY(ensure(ctx, f->offsets, sizeof(uint32_t) * ((size_t)n + 1)));
+  NGS_TRY(ensure(ctx, f->offsets, sizeof(uint32_t) * ((size_t)R + 1)));
   NGS_TRY(ensure(ctx, f->ranges, sizeof(uint2) * (size_t)ntiles));
-  NGS_TRY(ensure(ctx, f->state, sizeof(float4) * 2 * npix));
-  NGS_TRY(ensure(ctx, ctx->scan_tmp, sizeof(uint64_t) * scan_tmp_words(n)));
+  NGS_TRY(ensure(ctx, f->state, sizeof(float4) * 2 * (size_t)pix_total));
+  NGS_TRY(ensure(ctx, ctx->scan_tmp, sizeof(uint64_t) * scan_tmp_words(R)));
   if (!ctx->total.p) {
     NGS_TRY(ensure(ctx, ctx->total, 2 * sizeof(uint64_t)));
     cudaMemsetAsync(ctx->total.p, 0, 2 * sizeof(uint64_t), s);
   }
   rp.check = reinterpret_cast<uint32_t*>(ctx->total.as<uint64_t>() + 1);
-  NGS_TRY(ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(std::max(n, 1u))));
+  NGS_TRY(ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(std::max(n, 1u), (uint32_t)n_views)));
+  NGS_TRY(upload_views(ctx, f, s));
+  const ViewParams* views = f->views.as<ViewParams>();
 
   cudaEvent_t ev;
-  // 1. projection: splat records, FP32 depth keys (all-ones for splats that take no tile), tile counts
+  // 1. projection of every (view, Gaussian): splat records, FP32 depth keys (all-ones for splats that take
+  //    no tile), tile counts
   stage_begin(ctx, s, 0, &ev);
-  launch_project(*g, cp, rp, f->rec.as<float4>(), f->gkeys[0].as<uint32_t>(), f->tile_count.as<uint32_t>(),
-                 f->gvals[0].as<uint32_t>(), s);
+  launch_project(*g, views, f->view_host[0].cam, rp, f->rec.as<float4>(), f->gkeys[0].as<uint32_t>(),
+                 f->tile_count.as<uint32_t>(), f->gvals[0].as<uint32_t>(), s);
   stage_end(ctx, s, 0, ev, n ? 1 : 0);
   NGS_TRY(check_launch(ctx, "project"));
-  // 2. stable sort of the Gaussians by FP32 depth (ties keep index order)
+  // 2. stable sort of each view's splats by FP32 depth (ties keep Gaussian order)
   stage_begin(ctx, s, 1, &ev);
   int launches = 0;
   {
     uint32_t* k2[2] = {f->gkeys[0].as<uint32_t>(), f->gkeys[1].as<uint32_t>()};
     uint32_t* v2[2] = {f->gvals[0].as<uint32_t>(), f->gvals[1].as<uint32_t>()};
-    f->g_final = radix_sort_u32(k2, v2, n, 0, 32, ctx->hist.as<uint32_t>(), ctx->hist.cap / 4, s, &launches);
+    f->g_final = radix_sort_u32(k2, v2, n, (uint32_t)n_views, nullptr, 0, 32, ctx->hist.as<uint32_t>(), s, &launches);
   }
   stage_end(ctx, s, 1, ev, launches);
   NGS_TRY(check_launch(ctx, "depth sort"));
-  // 3. exclusive scan of the tile counts in depth order; the pair count comes back to the host
+  // 3. exclusive scan of the tile counts in (view, depth) order; the pair count comes back to the host
   stage_begin(ctx, s, 2, &ev);
   launches = 0;
   const uint32_t* order = f->gvals[f->g_final].as<uint32_t>();
-  launch_scan_counts(f->tile_count.as<uint32_t>(), order, n, f->offsets.as<uint32_t>(), ctx->scan_tmp.as<uint64_t>(),
+  launch_scan_counts(f->tile_count.as<uint32_t>(), order, R, f->offsets.as<uint32_t>(), ctx->scan_tmp.as<uint64_t>(),
                      ctx->total.as<uint64_t>(), s, &launches);
   NGS_TRY(check_launch(ctx, "scan"));
   cudaError_t e = cudaMemcpyAsync(ctx->h_total, ctx->total.p, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
@@ -291,46 +373,69 @@ NGS_API int ngs_render(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const
   if (P >= (1ull << 31)) return fail(ctx, NGS_ERR_INVALID_ARG, "more than 2^31 (tile, Gaussian) pairs");
   uint32_t np = (uint32_t)P;
   for (int k = 0; k < 2; ++k) {
-    NGS_TRY(ensure(ctx, f->pkeys[k], sizeof(uint64_t) * (size_t)std::max(np, 1u)));
+    NGS_TRY(ensure(ctx, f->ptile[k], sizeof(uint32_t) * (size_t)std::max(np, 1u)));
     NGS_TRY(ensure(ctx, f->pvals[k], sizeof(uint32_t) * (size_t)std::max(np, 1u)));
   }
-  NGS_TRY(ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(std::max(np, 1u))));
-  launch_emit_keys(f->rec.as<float4>(), order, f->offsets.as<uint32_t>(), n, rp, cam->width, cam->height,
-                   f->pkeys[0].as<uint64_t>(), f->pvals[0].as<uint32_t>(), s);
-  stage_end(ctx, s, 2, ev, launches + (n ? 1 : 0));
+  NGS_TRY(ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(std::max(np, 1u), 1)));
+  launch_emit_pairs(f->rec.as<float4>(), order, f->offsets.as<uint32_t>(), views, rp, f->ptile[0].as<uint32_t>(),
+                    f->pvals[0].as<uint32_t>(), s);
+  stage_end(ctx, s, 2, ev, launches + (R ? 1 : 0));
   NGS_TRY(check_launch(ctx, "emit keys"));
-  // 4. stable sort of the pairs by tile: the depth order inside each tile is kept, so the result is the
-  //    order of the full 64-bit (tile << 32 | depth) keys
+  // 4. stable sort of the pairs by global tile: the depth order inside each tile is kept, so the result is
+  //    the order of the full 64-bit (tile << 32 | depth) keys
   stage_begin(ctx, s, 3, &ev);
   launches = 0;
   {
-    uint64_t* k2[2] = {f->pkeys[0].as<uint64_t>(), f->pkeys[1].as<uint64_t>()};
+    uint32_t* k2[2] = {f->ptile[0].as<uint32_t>(), f->ptile[1].as<uint32_t>()};
     uint32_t* v2[2] = {f->pvals[0].as<uint32_t>(), f->pvals[1].as<uint32_t>()};
     int tb = tile_bits(ntiles);
-    f->p_final = radix_sort_u64(k2, v2, np, 32, 32 + tb, ctx->hist.as<uint32_t>(), ctx->hist.cap / 4, s, &launches);
+    f->p_final = radix_sort_u32(k2, v2, np, 1, nullptr, 0, tb, ctx->hist.as<uint32_t>(), s, &launches);
   }
   stage_end(ctx, s, 3, ev, launches);
   NGS_TRY(check_launch(ctx, "tile sort"));
-  // 5. per-tile [start, end)
+  // 5. per-tile [start, end); for the persistent schedule, the tiles by descending pair count
   stage_begin(ctx, s, 4, &ev);
-  launch_tile_ranges(f->pkeys[f->p_final].as<uint64_t>(), np, ntiles, f->ranges.as<uint2>(), s);
-  stage_end(ctx, s, 4, ev, np ? 1 : 0);
+  launches = np ? 1 : 0;
+  launch_tile_ranges(f->ptile[f->p_final].as<uint32_t>(), np, nullptr, ntiles, f->ranges.as<uint2>(), s);
+  const uint32_t* work = nullptr;
+  uint32_t* counter = nullptr;
+  if (rp.schedule == NGS_SCHEDULE_PERSISTENT) {
+    NGS_TRY(ensure(ctx, f->work, sizeof(uint32_t) * (size_t)ntiles));
+    NGS_TRY(ensure(ctx, f->sched, sizeof(uint32_t) * kSchedWords));
+    cudaMemsetAsync(f->sched.p, 0, sizeof(uint32_t) * kSchedWords, s);
+    launch_tile_order(f->ranges.as<uint2>(), ntiles, f->sched.as<uint32_t>(), f->work.as<uint32_t>(), s, &launches);
+    work = f->work.as<uint32_t>();
+    counter = f->sched.as<uint32_t>();
+  }
+  stage_end(ctx, s, 4, ev, launches);
   NGS_TRY(check_launch(ctx, "tile ranges"));
-  // 6. composite
+  // 6. composite every tile of every view
   stage_begin(ctx, s, 5, &ev);
-  launch_composite_forward(f->rec.as<float4>(), f->pvals[f->p_final].as<uint32_t>(), f->ranges.as<uint2>(), rp,
-                           cam->width, cam->height, image, overdraw, f->state.as<float4>(), s);
+  launch_composite_forward(f->rec.as<float4>(), f->pvals[f->p_final].as<uint32_t>(), f->ranges.as<uint2>(), rp, views,
+                           image, overdraw, f->state.as<float4>(), work, counter, ctx->num_sms, s);
   stage_end(ctx, s, 5, ev, 1);
   NGS_TRY(check_launch(ctx, "composite"));
 
   f->n = n;
   f->pairs = np;
-  f->W = cam->width;
-  f->H = cam->height;
-  f->cam = cp;
+  f->n_views = n_views;
+  f->n_pixels = (int64_t)pix_total;
   f->rp = rp;
   f->has_render = true;
   return NGS_OK;
+}
+
+NGS_API int ngs_render(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const ngs_camera* cam,
+                       const ngs_model* model, const ngs_options* o, float* image, int32_t* overdraw, void* stream) {
+  if (!ctx) return NGS_ERR_INVALID_ARG;
+  return render_views(ctx, f, g, cam, 1, model, o, image, overdraw, (cudaStream_t)stream);
+}
+
+NGS_API int ngs_render_batch(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const ngs_camera* cams,
+                             int32_t n_views, const ngs_model* model, const ngs_options* o, float* images,
+                             int32_t* overdraw, void* stream) {
+  if (!ctx) return NGS_ERR_INVALID_ARG;
+  return render_views(ctx, f, g, cams, n_views, model, o, images, overdraw, (cudaStream_t)stream);
 }
 
 NGS_API int ngs_render_backward(ngs_ctx* ctx, const ngs_frame* f, const ngs_gaussians* g, const float* dl_dimage,
@@ -343,36 +448,59 @@ NGS_API int ngs_render_backward(ngs_ctx* ctx, const ngs_frame* f, const ngs_gaus
   if (g->n > 0 && (!out->d_means || !out->d_log_scales || !out->d_quats || !out->d_opacity_logits || !out->d_sh))
     return fail(ctx, NGS_ERR_INVALID_ARG, "null gradient array");
   cudaStream_t s = (cudaStream_t)stream;
-  uint32_t n = (uint32_t)f->n;
-  NGS_TRY(ensure(ctx, ctx->grad2d, sizeof(float4) * 3 * (size_t)std::max(n, 1u)));
-  cudaMemsetAsync(ctx->grad2d.p, 0, sizeof(float4) * 3 * (size_t)n, s);
+  const uint32_t R = f->rp.n_records;
+  NGS_TRY(ensure(ctx, ctx->grad2d, sizeof(float4) * 3 * (size_t)std::max(R, 1u)));
+  cudaMemsetAsync(ctx->grad2d.p, 0, sizeof(float4) * 3 * (size_t)R, s);
+  const ViewParams* views = f->views.as<ViewParams>();
+  const uint32_t* work = nullptr;
+  uint32_t* counter = nullptr;
+  if (f->rp.schedule == NGS_SCHEDULE_PERSISTENT) {
+    work = f->work.as<uint32_t>();
+    counter = f->sched.as<uint32_t>() + 1;
+    cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+  }
   cudaEvent_t ev;
   stage_begin(ctx, s, 6, &ev);
   launch_composite_backward(f->rec.as<float4>(), f->pvals[f->p_final].as<uint32_t>(), f->ranges.as<uint2>(), f->rp,
-                            f->W, f->H, dl_dimage, f->state.as<float4>(), ctx->grad2d.as<float4>(), s);
+                            views, dl_dimage, f->state.as<float4>(), ctx->grad2d.as<float4>(), work, counter,
+                            ctx->num_sms, s);
   stage_end(ctx, s, 6, ev, 1);
   NGS_TRY(check_launch(ctx, "composite backward"));
   stage_begin(ctx, s, 7, &ev);
-  launch_project_backward(*g, f->cam, f->rp, f->rec.as<float4>(), f->tile_count.as<uint32_t>(),
-                          ctx->grad2d.as<float4>(), *out, s);
-  stage_end(ctx, s, 7, ev, n ? 1 : 0);
+  launch_project_backward(*g, views, f->view_host[0].cam, f->rp, f->tile_count.as<uint32_t>(), ctx->grad2d.as<float4>(), *out, s);
+  stage_end(ctx, s, 7, ev, g->n ? 1 : 0);
   NGS_TRY(check_launch(ctx, "projection backward"));
   return NGS_OK;
 }
 
-NGS_API int ngs_frame_view_get(const ngs_frame* f, ngs_frame_view* out) {
-  if (!f || !out) return NGS_ERR_INVALID_ARG;
+NGS_API int ngs_frame_view_get(const ngs_frame* fc, ngs_frame_view* out) {
+  if (!fc || !out) return NGS_ERR_INVALID_ARG;
   memset(out, 0, sizeof(*out));
-  if (!f->has_render) return NGS_ERR_INVALID_ARG;
+  if (!fc->has_render) return NGS_ERR_INVALID_ARG;
+  // the hot path sorts 32-bit tile indices; the 64-bit keys are composed here, after the device is idle
+  ngs_frame* f = const_cast<ngs_frame*>(fc);
+  uint32_t np = (uint32_t)f->pairs;
+  if (ensure(f->ctx, f->keys64, sizeof(uint64_t) * (size_t)std::max(np, 1u)) != NGS_OK) return NGS_ERR_OUT_OF_MEMORY;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) {
+    launch_compose_keys(f->ptile[f->p_final].as<uint32_t>(), f->pvals[f->p_final].as<uint32_t>(), f->rec.as<float4>(),
+                        np, f->keys64.as<uint64_t>(), nullptr);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+  if (e != cudaSuccess) return fail(f->ctx, NGS_ERR_CUDA, std::string("composing keys: ") + cudaGetErrorString(e));
   out->n_gaussians = f->n;
   out->n_pairs = f->pairs;
-  out->tiles_x = f->rp.tiles_x;
-  out->tiles_y = f->rp.tiles_y;
-  out->width = f->W;
-  out->height = f->H;
+  out->tiles_x = f->view_host[0].tiles_x;
+  out->tiles_y = f->view_host[0].tiles_y;
+  out->width = f->view_host[0].cam.W;
+  out->height = f->view_host[0].cam.H;
+  out->n_views = f->n_views;
+  out->view_pixel_base = f->pix_base.data();
+  out->view_tile_base = f->tile_base.data();
   out->log2_alpha_min = f->rp.log2_alpha_min;
   out->records = f->rec.as<float>();
-  out->keys = f->pkeys[f->p_final].as<uint64_t>();
+  out->keys = f->keys64.as<uint64_t>();
   out->values = f->pvals[f->p_final].as<uint32_t>();
   out->ranges = f->ranges.as<uint32_t>();
   out->pixel_state = f->state.as<float>();

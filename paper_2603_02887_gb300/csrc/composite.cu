@@ -1,6 +1,7 @@
 // Per-tile front-to-back compositing (forward) and its path-replay adjoint (backward).
 //
-// One CTA per screen tile. Forward: one thread per pixel, warps on 8 x 4 pixel blocks whose pixels are close
+// One CTA per screen tile of any view of the batch (global tile index -> view by binary search over the
+// views' first tiles). Forward: one thread per pixel, warps on 8 x 4 pixel blocks whose pixels are close
 // and tend to saturate together. Replay: two pixels per thread, (x, y) and (x, y + 4), so that a warp covers
 // an 8 x 8 block and reduces the sum of both pixels' contributions once per 64 pixels. The tile's
 // depth-sorted splat list is walked in chunks of one record (48 B) per pixel staged in shared memory.
@@ -21,6 +22,8 @@
 // then w = dL/d(log2 alpha) and its moments w, w dx, w dy, w dx^2, w dx dy, w dy^2 (which determine the
 // gradient of the splat record, see the projection backward) and dL/dE, reduced over the warp's pixels with
 // shuffles and added to the per-Gaussian buffer with one atomic-add instruction per warp and splat.
+#include <algorithm>
+
 #include "ngs_internal.cuh"
 
 namespace ngs {
@@ -28,12 +31,12 @@ namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
-// Stage the splat record of Gaussian `id` in shared memory. An index outside [0, n) (which a correct
-// binning never produces) is not read: the entry gets log2(aleph) = -inf, so no pixel composites it, and
+// Stage splat record `id` in shared memory. An index outside [0, n_records) (which a correct binning never
+// produces) is not read: the entry gets log2(aleph) = -inf, so no pixel composites it, and
 // the device error word records the event.
 __device__ __forceinline__ void stage_record(const float4* __restrict__ rec, uint32_t id, const RenderParams& rp,
                                              float4& r0, float4& r1, float& e2) {
-  if (id < rp.n_gaussians) {
+  if (id < rp.n_records) {
     r0 = rec[3 * (size_t)id];
     r1 = rec[3 * (size_t)id + 1];
     e2 = rec[3 * (size_t)id + 2].x;
@@ -49,7 +52,6 @@ template <int TW, int TH, int PPT>
 struct TileGeom {
   static constexpr int kPix = PPT;  // pixels per thread
   static constexpr int kThreads = TW * TH / kPix;
-  static constexpr int kChunk = TW * TH;  // records staged per chunk (kPix per thread)
   static constexpr int kWarpsX = TW / 8;
   static_assert(TW % 8 == 0 && TH % (4 * PPT) == 0, "tile must be a multiple of 8 x (4 PPT)");
   // warp w covers the 8 x (4 PPT) block (w % kWarpsX, w / kWarpsX) of the tile; lane l owns its pixels
@@ -67,20 +69,53 @@ constexpr int kBwdPix = 2;
 
 // ---- forward ---------------------------------------------------------------------------------------
 
-template <int TW, int TH, int KIND>
-__global__ void __launch_bounds__(TW* TH) composite_forward_kernel(const float4* __restrict__ rec,
-                                                                   const uint32_t* __restrict__ ids,
-                                                                   const uint2* __restrict__ ranges, RenderParams rp,
-                                                                   int W, int H, float* __restrict__ image,
-                                                                   int32_t* __restrict__ overdraw,
-                                                                   float4* __restrict__ state) {
+// Shared-memory staging of one chunk of CH splat records.
+template <int CH>
+struct StageBuf {
+  float4 r0[CH];
+  float4 r1[CH];
+  float e2[CH];
+};
+
+// Stage list entries [base, base + CH) of the tile (those below `end`): slot k by thread k mod B.
+template <int B, int CH>
+__device__ __forceinline__ void stage_chunk(const float4* __restrict__ rec, const uint32_t* __restrict__ ids,
+                                            const RenderParams& rp, uint32_t base, uint32_t end, StageBuf<CH>& sb,
+                                            uint32_t* s_id) {
+#pragma unroll
+  for (int k = 0; k < (CH + B - 1) / B; ++k) {
+    const int slot = k * B + (int)threadIdx.x;
+    const uint32_t i = base + (uint32_t)slot;
+    if (slot < CH && i < end) {
+      const uint32_t id = ids[i];
+      if (s_id) s_id[slot] = id < rp.n_records ? id : 0u;
+      stage_record(rec, id, rp, sb.r0[slot], sb.r1[slot], sb.e2[slot]);
+    }
+  }
+}
+
+// Persistent schedule: the next tile of a CTA, the next entry of the work list taken with one atomic per
+// CTA. Returns n_tiles when none is left.
+__device__ __forceinline__ uint32_t next_tile(const uint32_t* __restrict__ work, uint32_t* counter, uint32_t n_tiles,
+                                              uint32_t* s_next) {
+  __syncthreads();  // every thread has read the previous s_next and is done with the staging buffers
+  if (threadIdx.x == 0) *s_next = atomicAdd(counter, 1u);
+  __syncthreads();
+  const uint32_t w = *s_next;
+  return w < n_tiles ? (work ? work[w] : w) : n_tiles;
+}
+
+template <int TW, int TH, int KIND, int CH>
+__device__ __forceinline__ void forward_tile(const float4* __restrict__ rec, const uint32_t* __restrict__ ids,
+                                             const uint2* __restrict__ ranges, const RenderParams& rp,
+                                             const ViewParams* __restrict__ views, float* __restrict__ image,
+                                             int32_t* __restrict__ overdraw, float4* __restrict__ state,
+                                             uint32_t tile, StageBuf<CH>& sb) {
   using G = TileGeom<TW, TH, 1>;
   constexpr int B = G::kThreads;
-  __shared__ float4 s_r0[B];
-  __shared__ float4 s_r1[B];
-  __shared__ float s_e2[B];
-  int tile = blockIdx.x;
-  int tx = tile % rp.tiles_x, ty = tile / rp.tiles_x;
+  const TileView tv = tile_view(rp, views, (uint32_t)tile);
+  const int W = tv.W, H = tv.H;
+  const int tx = tv.local % tv.tiles_x, ty = tv.local / tv.tiles_x;
   int tid = threadIdx.x;
   int x, y;
   G::pixel(tid, 0, tx * TW, ty * TH, x, y);
@@ -97,20 +132,19 @@ __global__ void __launch_bounds__(TW* TH) composite_forward_kernel(const float4*
   // exponential state
   float T = 1.f;
   const float amax = rp.alpha_max, l2min = rp.log2_alpha_min, c = rp.c;
-  for (uint32_t base = range.x; base < range.y; base += B) {
+  for (uint32_t base = range.x; base < range.y; base += CH) {
     if (__syncthreads_count(done) == B) break;
-    uint32_t i = base + tid;
-    if (i < range.y) stage_record(rec, ids[i], rp, s_r0[tid], s_r1[tid], s_e2[tid]);
+    stage_chunk<B, CH>(rec, ids, rp, base, range.y, sb, nullptr);
     __syncthreads();
-    int cnt = (int)min((uint32_t)B, range.y - base);
+    int cnt = (int)min((uint32_t)CH, range.y - base);
     if (__any_sync(kFull, !done)) {
       for (int j = 0; j < cnt && !done; ++j) {
-        float4 r0 = s_r0[j], r1 = s_r1[j];
+        float4 r0 = sb.r0[j], r1 = sb.r1[j];
         float dx, dy;
         float e = splat_log2_alpha(px, py, r0, r1, dx, dy);
         if (e < l2min) continue;
         float alpha = fminf(amax, fast_exp2(e));
-        float E0 = r1.z, E1 = r1.w, E2 = s_e2[j];
+        float E0 = r1.z, E1 = r1.w, E2 = sb.e2[j];
         if (KIND == NGS_MODEL_QUAD) {
           float pt = quad_slope(alpha, c, tau);
           float Sn = __fadd_rn(S, pt);
@@ -158,8 +192,8 @@ __global__ void __launch_bounds__(TW* TH) composite_forward_kernel(const float4*
       }
     }
   }
-  if (!inside) return;
-  size_t pix = (size_t)y * W + x;
+  if (!inside) return;  // (the caller's next barrier is reached by every thread)
+  size_t pix = tv.pix_base + (size_t)y * W + x;
   float Tend = KIND == NGS_MODEL_QUAD ? (saturated ? 0.f : 1.f - S) : T;
   float L0 = C0 + rp.bg[0] * Tend, L1 = C1 + rp.bg[1] * Tend, L2 = C2 + rp.bg[2] * Tend;
   image[3 * pix] = L0;
@@ -173,6 +207,29 @@ __global__ void __launch_bounds__(TW* TH) composite_forward_kernel(const float4*
   } else {
     state[2 * pix] = make_float4(__uint_as_float(nbits), L0, L1, L2);
     state[2 * pix + 1] = make_float4(Tend, 0.f, 0.f, 0.f);
+  }
+}
+
+template <int TW, int TH, int KIND, int CH, bool PERSIST>
+__global__ void __launch_bounds__(TW* TH) composite_forward_kernel(const float4* __restrict__ rec,
+                                                                   const uint32_t* __restrict__ ids,
+                                                                   const uint2* __restrict__ ranges, RenderParams rp,
+                                                                   const ViewParams* __restrict__ views,
+                                                                   float* __restrict__ image,
+                                                                   int32_t* __restrict__ overdraw,
+                                                                   float4* __restrict__ state,
+                                                                   const uint32_t* __restrict__ work,
+                                                                   uint32_t* counter) {
+  __shared__ StageBuf<CH> sb;
+  if constexpr (PERSIST) {
+    __shared__ uint32_t s_next;
+    for (;;) {
+      const uint32_t tile = next_tile(work, counter, rp.n_tiles, &s_next);
+      if (tile >= rp.n_tiles) break;
+      forward_tile<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, image, overdraw, state, tile, sb);
+    }
+  } else {
+    forward_tile<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, image, overdraw, state, blockIdx.x, sb);
   }
 }
 
@@ -274,23 +331,20 @@ __device__ __forceinline__ bool bwd_step(BwdPixel& p, float4 r0, float4 r1, cons
   return true;
 }
 
-template <int TW, int TH, int KIND>
-__global__ void __launch_bounds__(TW* TH / kBwdPix) composite_backward_kernel(const float4* __restrict__ rec,
-                                                                        const uint32_t* __restrict__ ids,
-                                                                        const uint2* __restrict__ ranges,
-                                                                        RenderParams rp, int W, int H,
-                                                                        const float* __restrict__ dl_dimage,
-                                                                        const float4* __restrict__ state,
-                                                                        float4* __restrict__ grad2d) {
+template <int TW, int TH, int KIND, int CH>
+__device__ __forceinline__ void backward_tile(const float4* __restrict__ rec, const uint32_t* __restrict__ ids,
+                                              const uint2* __restrict__ ranges, const RenderParams& rp,
+                                              const ViewParams* __restrict__ views,
+                                              const float* __restrict__ dl_dimage, const float4* __restrict__ state,
+                                              float4* __restrict__ grad2d, uint32_t tile, StageBuf<CH>& sb,
+                                              uint32_t* s_id) {
   using G = TileGeom<TW, TH, kBwdPix>;
-  constexpr int B = G::kThreads, CH = G::kChunk;
+  constexpr int B = G::kThreads;
   static_assert(kBwdPix == 2, "the replay below is written for two pixels per thread");
-  __shared__ float4 s_r0[CH];
-  __shared__ float4 s_r1[CH];
-  __shared__ float s_e2[CH];
-  __shared__ uint32_t s_id[CH];
-  const int tile = blockIdx.x;
-  const int tx = tile % rp.tiles_x, ty = tile / rp.tiles_x;
+  const TileView tv = tile_view(rp, views, (uint32_t)tile);
+  const int W = tv.W, H = tv.H;
+  const size_t pix_base = tv.pix_base;
+  const int tx = tv.local % tv.tiles_x, ty = tv.local / tv.tiles_x;
   const int tid = threadIdx.x, lane = tid & 31;
   const uint2 range = ranges[tile];
   BwdPixel p[2];
@@ -309,7 +363,7 @@ __global__ void __launch_bounds__(TW* TH / kBwdPix) composite_backward_kernel(co
     q.S = q.tau = q.gacc = 0.f;
     q.T = 1.f;
     if (x < W && y < H) {
-      size_t pix = (size_t)y * W + x;
+      size_t pix = pix_base + (size_t)y * W + x;
       float4 s0 = state[2 * pix], s1 = state[2 * pix + 1];
       q.last = range.x + (__float_as_uint(s0.x) & 0x7FFFFFFFu);
       q.g0 = dl_dimage[3 * pix];
@@ -330,24 +384,16 @@ __global__ void __launch_bounds__(TW* TH / kBwdPix) composite_backward_kernel(co
   for (uint32_t base = range.x; base < range.y; base += CH) {
     const bool done = base >= max(p[0].last, p[1].last);
     if (__syncthreads_count(done) == B) break;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      uint32_t i = base + k * B + tid;
-      if (i < range.y) {
-        uint32_t id = ids[i];
-        s_id[k * B + tid] = id < rp.n_gaussians ? id : 0u;
-        stage_record(rec, id, rp, s_r0[k * B + tid], s_r1[k * B + tid], s_e2[k * B + tid]);
-      }
-    }
+    stage_chunk<B, CH>(rec, ids, rp, base, range.y, sb, s_id);
     __syncthreads();
     if (base < warp_last) {
       const int cnt = (int)(min(warp_last, min(base + (uint32_t)CH, range.y)) - base);
       for (int j = 0; j < cnt; ++j) {
         const uint32_t pos = base + j;
-        const float4 r0 = s_r0[j], r1 = s_r1[j];
+        const float4 r0 = sb.r0[j], r1 = sb.r1[j];
         float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        bool on = bwd_step<KIND>(p[0], r0, r1, s_e2[j], pos, rp, v);
-        on |= bwd_step<KIND>(p[1], r0, r1, s_e2[j], pos, rp, v);
+        bool on = bwd_step<KIND>(p[0], r0, r1, sb.e2[j], pos, rp, v);
+        on |= bwd_step<KIND>(p[1], r0, r1, sb.e2[j], pos, rp, v);
         const uint32_t mask = __ballot_sync(kFull, on);
         if (mask) {
           float4* dst = grad2d + 3 * (size_t)s_id[j];
@@ -366,53 +412,139 @@ __global__ void __launch_bounds__(TW* TH / kBwdPix) composite_backward_kernel(co
   }
 }
 
-template <int TW, int TH>
-void forward_for_tile(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp, int W,
-                      int H, float* image, int32_t* overdraw, float4* state, cudaStream_t s) {
-  int ntiles = rp.tiles_x * rp.tiles_y;
+template <int TW, int TH, int KIND, int CH, bool PERSIST>
+__global__ void __launch_bounds__(TW* TH / kBwdPix) composite_backward_kernel(const float4* __restrict__ rec,
+                                                                        const uint32_t* __restrict__ ids,
+                                                                        const uint2* __restrict__ ranges,
+                                                                        RenderParams rp,
+                                                                        const ViewParams* __restrict__ views,
+                                                                        const float* __restrict__ dl_dimage,
+                                                                        const float4* __restrict__ state,
+                                                                        float4* __restrict__ grad2d,
+                                                                        const uint32_t* __restrict__ work,
+                                                                        uint32_t* counter) {
+  __shared__ StageBuf<CH> sb;
+  __shared__ uint32_t s_id[CH];
+  if constexpr (PERSIST) {
+    __shared__ uint32_t s_next;
+    for (;;) {
+      const uint32_t tile = next_tile(work, counter, rp.n_tiles, &s_next);
+      if (tile >= rp.n_tiles) break;
+      backward_tile<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, dl_dimage, state, grad2d, tile, sb, s_id);
+    }
+  } else {
+    backward_tile<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, dl_dimage, state, grad2d, blockIdx.x, sb, s_id);
+  }
+}
+
+// Launch configuration of a composite launch: chunk factor (records staged per round = tile pixels x
+// {1/2, 1, 2}) and schedule (one CTA per tile, or persistent CTAs over the work list).
+struct Launch {
+  int chunk_code;                   // 0: half, 1: equal, 2: double the tile's pixel count
+  const uint32_t* work;             // persistent schedule: tile order (null: identity)
+  uint32_t* counter;                // persistent schedule: zeroed work counter (null: one CTA per tile)
+  int num_sms;
+};
+
+// One CTA per tile, or one wave of persistent CTAs (SM count x resident CTAs per SM).
+template <typename Kernel>
+static unsigned grid_for(Kernel k, int threads, const Launch& L, uint32_t n_tiles) {
+  if (!L.counter) return n_tiles;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  return (unsigned)std::min<uint64_t>((uint64_t)per_sm * (uint64_t)L.num_sms, n_tiles);
+}
+
+template <int TW, int TH, int KIND, int CH>
+void forward_launch(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
+                    const ViewParams* views, float* image, int32_t* overdraw, float4* state, const Launch& L,
+                    cudaStream_t s) {
   constexpr int threads = TileGeom<TW, TH, 1>::kThreads;
-  if (rp.kind == NGS_MODEL_QUAD)
-    composite_forward_kernel<TW, TH, NGS_MODEL_QUAD><<<ntiles, threads, 0, s>>>(rec, ids, ranges, rp, W, H, image,
-                                                                                  overdraw, state);
-  else
-    composite_forward_kernel<TW, TH, NGS_MODEL_EXP><<<ntiles, threads, 0, s>>>(rec, ids, ranges, rp, W, H, image,
-                                                                                 overdraw, state);
+  auto k = L.counter ? composite_forward_kernel<TW, TH, KIND, CH, true> : composite_forward_kernel<TW, TH, KIND, CH, false>;
+  k<<<grid_for(k, threads, L, rp.n_tiles), threads, 0, s>>>(rec, ids, ranges, rp, views, image, overdraw, state,
+                                                             L.work, L.counter);
+}
+
+template <int TW, int TH, int KIND, int CH>
+void backward_launch(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
+                     const ViewParams* views, const float* dl, const float4* state, float4* grad2d, const Launch& L,
+                     cudaStream_t s) {
+  constexpr int threads = TileGeom<TW, TH, kBwdPix>::kThreads;
+  auto k =
+      L.counter ? composite_backward_kernel<TW, TH, KIND, CH, true> : composite_backward_kernel<TW, TH, KIND, CH, false>;
+  k<<<grid_for(k, threads, L, rp.n_tiles), threads, 0, s>>>(rec, ids, ranges, rp, views, dl, state, grad2d, L.work,
+                                                             L.counter);
+}
+
+template <int TW, int TH, int KIND>
+void forward_chunk(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
+                   const ViewParams* views, float* image, int32_t* overdraw, float4* state, const Launch& L,
+                   cudaStream_t s) {
+  constexpr int P = TW * TH;
+  if (L.chunk_code == 0) forward_launch<TW, TH, KIND, P / 2>(rec, ids, ranges, rp, views, image, overdraw, state, L, s);
+  else if (L.chunk_code == 2) forward_launch<TW, TH, KIND, 2 * P>(rec, ids, ranges, rp, views, image, overdraw, state, L, s);
+  else forward_launch<TW, TH, KIND, P>(rec, ids, ranges, rp, views, image, overdraw, state, L, s);
+}
+
+template <int TW, int TH, int KIND>
+void backward_chunk(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
+                    const ViewParams* views, const float* dl, const float4* state, float4* grad2d, const Launch& L,
+                    cudaStream_t s) {
+  constexpr int P = TW * TH;
+  if (L.chunk_code == 0) backward_launch<TW, TH, KIND, P / 2>(rec, ids, ranges, rp, views, dl, state, grad2d, L, s);
+  else if (L.chunk_code == 2) backward_launch<TW, TH, KIND, 2 * P>(rec, ids, ranges, rp, views, dl, state, grad2d, L, s);
+  else backward_launch<TW, TH, KIND, P>(rec, ids, ranges, rp, views, dl, state, grad2d, L, s);
 }
 
 template <int TW, int TH>
-void backward_for_tile(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp, int W,
-                       int H, const float* dl, const float4* state, float4* grad2d, cudaStream_t s) {
-  int ntiles = rp.tiles_x * rp.tiles_y;
-  constexpr int threads = TileGeom<TW, TH, kBwdPix>::kThreads;
+void forward_kind(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
+                  const ViewParams* views, float* image, int32_t* overdraw, float4* state, const Launch& L,
+                  cudaStream_t s) {
   if (rp.kind == NGS_MODEL_QUAD)
-    composite_backward_kernel<TW, TH, NGS_MODEL_QUAD><<<ntiles, threads, 0, s>>>(rec, ids, ranges, rp, W, H, dl,
-                                                                                   state, grad2d);
+    forward_chunk<TW, TH, NGS_MODEL_QUAD>(rec, ids, ranges, rp, views, image, overdraw, state, L, s);
   else
-    composite_backward_kernel<TW, TH, NGS_MODEL_EXP><<<ntiles, threads, 0, s>>>(rec, ids, ranges, rp, W, H, dl,
-                                                                                  state, grad2d);
+    forward_chunk<TW, TH, NGS_MODEL_EXP>(rec, ids, ranges, rp, views, image, overdraw, state, L, s);
+}
+
+template <int TW, int TH>
+void backward_kind(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
+                   const ViewParams* views, const float* dl, const float4* state, float4* grad2d, const Launch& L,
+                   cudaStream_t s) {
+  if (rp.kind == NGS_MODEL_QUAD)
+    backward_chunk<TW, TH, NGS_MODEL_QUAD>(rec, ids, ranges, rp, views, dl, state, grad2d, L, s);
+  else
+    backward_chunk<TW, TH, NGS_MODEL_EXP>(rec, ids, ranges, rp, views, dl, state, grad2d, L, s);
+}
+
+int chunk_code(const RenderParams& rp) {
+  const int P = rp.tile_w * rp.tile_h;
+  return rp.chunk == P / 2 ? 0 : rp.chunk == 2 * P ? 2 : 1;
 }
 
 }  // namespace
 
 void launch_composite_forward(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
-                              int W, int H, float* image, int32_t* overdraw, float4* state, cudaStream_t s) {
+                              const ViewParams* views, float* image, int32_t* overdraw, float4* state,
+                              const uint32_t* work, uint32_t* counter, int num_sms, cudaStream_t s) {
+  const Launch L{chunk_code(rp), work, counter, num_sms};
   if (rp.tile_w == 8 && rp.tile_h == 8)
-    forward_for_tile<8, 8>(rec, ids, ranges, rp, W, H, image, overdraw, state, s);
+    forward_kind<8, 8>(rec, ids, ranges, rp, views, image, overdraw, state, L, s);
   else if (rp.tile_w == 16 && rp.tile_h == 16)
-    forward_for_tile<16, 16>(rec, ids, ranges, rp, W, H, image, overdraw, state, s);
+    forward_kind<16, 16>(rec, ids, ranges, rp, views, image, overdraw, state, L, s);
   else
-    forward_for_tile<16, 32>(rec, ids, ranges, rp, W, H, image, overdraw, state, s);
+    forward_kind<16, 32>(rec, ids, ranges, rp, views, image, overdraw, state, L, s);
 }
 
 void launch_composite_backward(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
-                               int W, int H, const float* dl_dimage, const float4* state, float4* grad2d,
-                               cudaStream_t s) {
+                               const ViewParams* views, const float* dl_dimage, const float4* state, float4* grad2d,
+                               const uint32_t* work, uint32_t* counter, int num_sms, cudaStream_t s) {
+  const Launch L{chunk_code(rp), work, counter, num_sms};
   if (rp.tile_w == 8 && rp.tile_h == 8)
-    backward_for_tile<8, 8>(rec, ids, ranges, rp, W, H, dl_dimage, state, grad2d, s);
+    backward_kind<8, 8>(rec, ids, ranges, rp, views, dl_dimage, state, grad2d, L, s);
   else if (rp.tile_w == 16 && rp.tile_h == 16)
-    backward_for_tile<16, 16>(rec, ids, ranges, rp, W, H, dl_dimage, state, grad2d, s);
+    backward_kind<16, 16>(rec, ids, ranges, rp, views, dl_dimage, state, grad2d, L, s);
   else
-    backward_for_tile<16, 32>(rec, ids, ranges, rp, W, H, dl_dimage, state, grad2d, s);
+    backward_kind<16, 32>(rec, ids, ranges, rp, views, dl_dimage, state, grad2d, L, s);
 }
 
 }  // namespace ngs

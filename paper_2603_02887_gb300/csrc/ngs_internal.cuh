@@ -21,20 +21,78 @@ struct CamParams {
   int W, H;
 };
 
+// One view of a batch (a device array of these per frame). Views are packed one after the other: view v's
+// splat records are records [v n, (v + 1) n), its tiles have the global indices [tile_base, tile_base +
+// tiles_x tiles_y) and its pixels the packed-image indices [pix_base, pix_base + W H).
+struct ViewParams {
+  CamParams cam;
+  int tiles_x, tiles_y;
+  uint32_t tile_base;
+  uint32_t pad;
+  uint64_t pix_base;
+};
+
 struct RenderParams {
   float alpha_min, alpha_max, t_eps, dilation, near_plane;
   float log2_alpha_min;  // the alpha >= alpha_min test is made on log2(alpha)
   float bg[3];
   float c;               // quadratic parameter (NGS_MODEL_QUAD)
   int kind;
-  int tile_w, tile_h, tiles_x, tiles_y;
+  int tile_w, tile_h;
+  int tiles_x, tiles_y;  // of the view a kernel works on (kernels that see several views set them per view)
+  int width, height;     // of view 0
   int max_splats;
+  int chunk;             // records staged per round of a tile's list walk (tile pixels x 1/2, 1 or 2)
+  int schedule;          // NGS_SCHEDULE_*
   int sh_degree;
-  uint32_t n_gaussians;
+  uint32_t n_gaussians;  // n: Gaussians per view
+  uint32_t n_views;
+  uint32_t n_records;    // n_views * n: splat records (and valid pair values)
+  uint32_t n_tiles;      // tiles of all views
   uint32_t* check;       // device error word: kernels OR in a kCheck* bit when a bounds check fires
 };
 
-constexpr uint32_t kCheckIndex = 1u;  // a sorted pair named a Gaussian index >= n
+constexpr uint32_t kCheckIndex = 1u;  // a sorted pair named a splat record index >= n_records
+
+// Geometry of the view holding global tile t. A single view takes it from the kernel parameters (no
+// dependent load before the tile's work starts); a batch looks it up in the view table.
+struct TileView {
+  int W, H, tiles_x, local;  // image size, tiles per row, tile index within the view
+  size_t pix_base;           // first packed pixel of the view
+};
+
+__device__ __forceinline__ int view_of_tile(const ViewParams* __restrict__ views, int n_views, uint32_t t);
+
+__device__ __forceinline__ TileView tile_view(const RenderParams& rp, const ViewParams* __restrict__ views,
+                                              uint32_t t) {
+  TileView tv;
+  if (rp.n_views == 1) {
+    tv.W = rp.width;
+    tv.H = rp.height;
+    tv.tiles_x = rp.tiles_x;
+    tv.local = (int)t;
+    tv.pix_base = 0;
+  } else {
+    const int v = view_of_tile(views, (int)rp.n_views, t);
+    tv.W = __ldg(&views[v].cam.W);
+    tv.H = __ldg(&views[v].cam.H);
+    tv.tiles_x = __ldg(&views[v].tiles_x);
+    tv.local = (int)(t - __ldg(&views[v].tile_base));
+    tv.pix_base = (size_t)__ldg(reinterpret_cast<const unsigned long long*>(&views[v].pix_base));
+  }
+  return tv;
+}
+
+// The view whose global tiles contain tile t (views[0].tile_base = 0; tile bases ascend).
+__device__ __forceinline__ int view_of_tile(const ViewParams* __restrict__ views, int n_views, uint32_t t) {
+  int lo = 0, hi = n_views - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&views[mid].tile_base) <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 
 // Splat record: 3 float4 per Gaussian.
 //   r0 = (u, v, A', B'), r1 = (C', L, E0, E1), r2 = (E2, z, rx, ry)
@@ -113,15 +171,25 @@ struct ngs_ctx {
 struct ngs_frame {
   ngs_ctx* ctx = nullptr;
   bool has_render = false;
-  int64_t n = 0;
+  int64_t n = 0;             // Gaussians
   int64_t pairs = 0;
-  int W = 0, H = 0;
-  ngs::CamParams cam;
+  int n_views = 0;
+  int64_t n_pixels = 0;      // all views
   ngs::RenderParams rp;
+  std::vector<ngs::ViewParams> view_host;  // the views of the last render (host copy)
+  std::vector<int64_t> pix_base;           // [n_views + 1]
+  std::vector<uint32_t> tile_base;         // [n_views + 1]
+  ngs::ViewParams* h_views = nullptr;      // pinned staging of the view table
+  size_t h_views_cap = 0;
+  cudaEvent_t views_uploaded = nullptr;    // recorded after the last upload from h_views
+  ngs::DevBuf views;                       // device view table
   ngs::DevBuf rec, tile_count, gkeys[2], gvals[2], offsets;
-  ngs::DevBuf pkeys[2], pvals[2], ranges, state;
+  ngs::DevBuf ptile[2], pvals[2], ranges, state;
+  ngs::DevBuf keys64;  // 64-bit keys, materialised only for ngs_frame_view_get
+  ngs::DevBuf work;    // persistent schedule: tiles by descending pair count
+  ngs::DevBuf sched;   // persistent schedule: kSchedWords counters (see launch_tile_order)
   int g_final = 0;  // which gvals[] holds the depth-sorted Gaussian order
-  int p_final = 0;  // which pkeys[]/pvals[] hold the sorted pairs
+  int p_final = 0;  // which ptile[]/pvals[] hold the sorted pairs
 };
 
 namespace ngs {
@@ -133,31 +201,54 @@ void stage_begin(ngs_ctx* ctx, cudaStream_t s, int stage, cudaEvent_t* out);
 void stage_end(ngs_ctx* ctx, cudaStream_t s, int stage, cudaEvent_t start, int launches);
 
 // kernels' host launchers
-// writes records, depth keys (0xFFFFFFFF for splats without tiles), tile counts and order[i] = i
-void launch_project(const ngs_gaussians& g, const CamParams& cam, const RenderParams& rp, float4* rec,
-                    uint32_t* depth_key, uint32_t* tile_count, uint32_t* order, cudaStream_t s);
-void launch_project_backward(const ngs_gaussians& g, const CamParams& cam, const RenderParams& rp,
-                             const float4* rec, const uint32_t* tile_count, const float4* grad2d,
+// For every view v and Gaussian i, record r = v n + i: splat record, depth key (0xFFFFFFFF for splats
+// without tiles), tile count and order[r] = r.
+// cam0: the camera of view 0 (used when rp.n_views == 1).
+void launch_project(const ngs_gaussians& g, const ViewParams* views, const CamParams& cam0, const RenderParams& rp,
+                    float4* rec, uint32_t* depth_key, uint32_t* tile_count, uint32_t* order, cudaStream_t s);
+// Gradients w.r.t. the Gaussian parameters, summed over the views.
+// cam0: the camera of view 0 (the only one when rp.n_views == 1).
+void launch_project_backward(const ngs_gaussians& g, const ViewParams* views, const CamParams& cam0,
+                             const RenderParams& rp, const uint32_t* tile_count, const float4* grad2d,
                              const ngs_grads& out, cudaStream_t s);
-// radix sort of (key, value) pairs on bits [begin_bit, end_bit); returns the index (0/1) of the
-// buffer pair holding the result; launches counted into *launches
-int radix_sort_u32(uint32_t* keys[2], uint32_t* vals[2], uint32_t n, int begin_bit, int end_bit, uint32_t* hist,
-                   size_t hist_cap_words, cudaStream_t s, int* launches);
-int radix_sort_u64(uint64_t* keys[2], uint32_t* vals[2], uint32_t n, int begin_bit, int end_bit, uint32_t* hist,
-                   size_t hist_cap_words, cudaStream_t s, int* launches);
-size_t radix_hist_words(uint32_t n);
+// Stable radix sort of (key, value) pairs on bits [begin_bit, end_bit), independently within each of
+// `nseg` segments of seg_len items. If n_dev is not null, only the first min(*n_dev, seg_len) items of a
+// segment are sorted (a count known on the device only; seg_len is then the capacity). Returns the index
+// (0/1) of the buffer pair holding the result; launches counted into *launches.
+int radix_sort_u32(uint32_t* keys[2], uint32_t* vals[2], uint32_t seg_len, uint32_t nseg, const uint32_t* n_dev,
+                   int begin_bit, int end_bit, uint32_t* hist, cudaStream_t s, int* launches);
+size_t radix_hist_words(uint32_t seg_len, uint32_t nseg);
 // exclusive scan of tile_count[order[i]] into offsets[0..n] (offsets[n] = total) and the total into
 // *total (uint64, device)
 void launch_scan_counts(const uint32_t* tile_count, const uint32_t* order, uint32_t n, uint32_t* offsets,
                         uint64_t* block_sums, uint64_t* total, cudaStream_t s, int* launches);
 size_t scan_tmp_words(uint32_t n);
-void launch_emit_keys(const float4* rec, const uint32_t* order, const uint32_t* offsets, uint32_t n,
-                      const RenderParams& rp, int W, int H, uint64_t* keys, uint32_t* vals, cudaStream_t s);
-void launch_tile_ranges(const uint64_t* keys, uint32_t npairs, uint32_t ntiles, uint2* ranges, cudaStream_t s);
+// One (global tile, record index) pair per covered tile, in the order of `order` (n_records entries): the
+// records are in (view, depth) order, so sorting the pairs stably by tile alone gives the order of the
+// 64-bit keys (tile << 32 | depth bits).
+void launch_emit_pairs(const float4* rec, const uint32_t* order, const uint32_t* offsets, const ViewParams* views,
+                       const RenderParams& rp, uint32_t* tiles, uint32_t* vals, cudaStream_t s);
+// keys[i] = tiles[i] << 32 | bits(depth of record vals[i]) (diagnostics).
+void launch_compose_keys(const uint32_t* tiles, const uint32_t* vals, const float4* rec, uint32_t npairs,
+                         uint64_t* keys, cudaStream_t s);
+// [start, end) of every global tile's pairs (zero-length ranges stay (0, 0)); npairs_cap items are
+// covered by the grid, of which the first *npairs_dev are valid if npairs_dev is not null.
+void launch_tile_ranges(const uint32_t* tiles, uint32_t npairs_cap, const uint32_t* npairs_dev, uint32_t ntiles,
+                        uint2* ranges, cudaStream_t s);
+// Persistent schedule: work[] lists all tiles by descending pair count (buckets of floor(log2(pairs)),
+// any order within a bucket). `sched` holds kSchedWords zeroed words: [0] forward and [1] backward work
+// counters, then per-bucket counts and cursors.
+constexpr int kCostBuckets = 33;
+constexpr int kSchedWords = 2 + 2 * kCostBuckets;
+void launch_tile_order(const uint2* ranges, uint32_t ntiles, uint32_t* sched, uint32_t* work, cudaStream_t s,
+                       int* launches);
+// Composite launches. work/counter null: one CTA per tile; else persistent CTAs (num_sms x occupancy)
+// taking tiles from work[] through the zeroed counter.
 void launch_composite_forward(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
-                              int W, int H, float* image, int32_t* overdraw, float4* state, cudaStream_t s);
+                              const ViewParams* views, float* image, int32_t* overdraw, float4* state,
+                              const uint32_t* work, uint32_t* counter, int num_sms, cudaStream_t s);
 void launch_composite_backward(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
-                               int W, int H, const float* dl_dimage, const float4* state, float4* grad2d,
-                               cudaStream_t s);
+                               const ViewParams* views, const float* dl_dimage, const float4* state, float4* grad2d,
+                               const uint32_t* work, uint32_t* counter, int num_sms, cudaStream_t s);
 
 }  // namespace ngs

@@ -8,8 +8,8 @@
 // that scratch in a fixed static device array instead, and allocates nothing.
 //
 // Limits and behaviour:
-//  * at most kStaticMaxGaussians = 262,144 Gaussians per call (the array is 12 MiB); larger frames are
-//    rejected with NGS_ERR_INVALID_ARG and a message that names the limit;
+//  * at most kStaticMaxRecords = 262,144 splat records (Gaussians x views) per call (the array is 12 MiB);
+//    larger frames are rejected with NGS_ERR_INVALID_ARG and a message that names the limit;
 //  * every GPU that loads this library holds the array until the process exits;
 //  * all calls on a device share the one array and it keeps the previous call's contents, so each call
 //    clears the part it uses (cudaMemsetAsync) before use, and calls whose work overlaps on the GPU
@@ -23,10 +23,10 @@
 
 namespace {
 
-constexpr int64_t kStaticMaxGaussians = 262144;
+constexpr int64_t kStaticMaxRecords = 262144;
 constexpr int kMaxDevices = 64;
 
-static __device__ __align__(256) float4 g_static_grad2d[3 * kStaticMaxGaussians];
+static __device__ __align__(256) float4 g_static_grad2d[3 * kStaticMaxRecords];
 
 std::mutex g_mutex;
 void* g_device_ptr[kMaxDevices] = {};
@@ -59,10 +59,10 @@ extern "C" NGS_API int ngs_render_backward_static(ngs_ctx* ctx, const ngs_frame*
   if (!g || !dl_dimage || !out) return fail(ctx, NGS_ERR_INVALID_ARG, "null argument");
   if (g->n != f->n || g->sh_degree != f->rp.sh_degree)
     return fail(ctx, NGS_ERR_INVALID_ARG, "Gaussians do not match the rendered frame");
-  if (g->n > kStaticMaxGaussians)
+  if ((int64_t)f->rp.n_records > kStaticMaxRecords)
     return fail(ctx, NGS_ERR_INVALID_ARG,
-                "ngs_render_backward_static handles at most 262144 Gaussians (static scratch of 12 MiB); "
-                "use ngs_render_backward for larger scenes");
+                "ngs_render_backward_static handles at most 262144 splat records (Gaussians x views; static "
+                "scratch of 12 MiB); use ngs_render_backward for larger scenes");
   if (g->n > 0 && (!out->d_means || !out->d_log_scales || !out->d_quats || !out->d_opacity_logits || !out->d_sh))
     return fail(ctx, NGS_ERR_INVALID_ARG, "null gradient array");
   void* scratch = nullptr;
@@ -71,11 +71,19 @@ extern "C" NGS_API int ngs_render_backward_static(ngs_ctx* ctx, const ngs_frame*
   cudaStream_t s = (cudaStream_t)stream;
   size_t n = (size_t)f->n;
   float4* grad2d = reinterpret_cast<float4*>(scratch);
-  cudaError_t e = cudaMemsetAsync(grad2d, 0, sizeof(float4) * 3 * n, s);
+  cudaError_t e = cudaMemsetAsync(grad2d, 0, sizeof(float4) * 3 * (size_t)f->rp.n_records, s);
   if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("clearing the scratch: ") + cudaGetErrorString(e));
+  const ViewParams* views = f->views.as<ViewParams>();
+  const uint32_t* work = nullptr;
+  uint32_t* counter = nullptr;
+  if (f->rp.schedule == NGS_SCHEDULE_PERSISTENT) {  // the frame's own work list and counter (no allocation)
+    work = f->work.as<uint32_t>();
+    counter = f->sched.as<uint32_t>() + 1;
+    cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+  }
   launch_composite_backward(f->rec.as<float4>(), f->pvals[f->p_final].as<uint32_t>(), f->ranges.as<uint2>(), f->rp,
-                            f->W, f->H, dl_dimage, f->state.as<float4>(), grad2d, s);
-  launch_project_backward(*g, f->cam, f->rp, f->rec.as<float4>(), f->tile_count.as<uint32_t>(), grad2d, *out, s);
+                            views, dl_dimage, f->state.as<float4>(), grad2d, work, counter, ctx->num_sms, s);
+  launch_project_backward(*g, views, f->view_host[0].cam, f->rp, f->tile_count.as<uint32_t>(), grad2d, *out, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("backward launch: ") + cudaGetErrorString(e));
   ctx->launches += n ? 2 : 1;

@@ -150,6 +150,18 @@ __device__ __forceinline__ void load_sh(const float* sh, float (&c)[3 * K]) {
   }
 }
 
+template <int K, bool VEC>
+__device__ __forceinline__ void store_sh(float* dst, const float (&c)[3 * K]) {
+  if constexpr (VEC) {
+#pragma unroll
+    for (int k = 0; k < 3 * K / 4; ++k)
+      reinterpret_cast<float4*>(dst)[k] = make_float4(c[4 * k], c[4 * k + 1], c[4 * k + 2], c[4 * k + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3 * K; ++k) dst[k] = c[k];
+  }
+}
+
 template <int DEG, bool VEC = false>
 __device__ __forceinline__ void forward_map(const ngs_gaussians& g, const CamParams& cam, const RenderParams& rp,
                                             int i, ProjState<DEG>& st) {
@@ -313,11 +325,23 @@ __device__ __forceinline__ uint32_t count_tiles(float4 r0, float4 r1, float4 r2,
   return c;
 }
 
+// Block b works on view b % n_views and Gaussians [256 (b / n_views), +256): the views of one block of
+// Gaussians run side by side, so their parameters are read from HBM once and from L2 afterwards.
+// A single view takes its camera from the kernel parameters (cam0), a batch from the view table; the
+// arithmetic below is the same code either way.
 template <int DEG, bool VEC>
-__global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, CamParams cam, RenderParams rp, float4* rec,
+__global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, const ViewParams* __restrict__ views,
+                                                      CamParams cam0, RenderParams rp, float4* rec,
                                                       uint32_t* depth_key, uint32_t* tile_count, uint32_t* order) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t view = blockIdx.x % rp.n_views;
+  int i = (blockIdx.x / rp.n_views) * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
+  const CamParams cam = rp.n_views == 1 ? cam0 : views[view].cam;
+  if (rp.n_views != 1) {
+    rp.tiles_x = views[view].tiles_x;
+    rp.tiles_y = views[view].tiles_y;
+  }
+  const int64_t r = (int64_t)view * g.n + i;  // record index
   const float* m = g.means + 3 * (int64_t)i;
   float z = view_depth(cam, m[0], m[1], m[2]);
   float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = make_float4(0.f, z, 0.f, 0.f);
@@ -342,65 +366,57 @@ __global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, CamParams
       count = count_tiles(r0, r1, r2, rp);
     }
   }
-  rec[3 * (int64_t)i] = r0;
-  rec[3 * (int64_t)i + 1] = r1;
-  rec[3 * (int64_t)i + 2] = r2;
-  depth_key[i] = count ? __float_as_uint(z) : 0xFFFFFFFFu;
-  tile_count[i] = count;
-  order[i] = (uint32_t)i;
+  rec[3 * r] = r0;
+  rec[3 * r + 1] = r1;
+  rec[3 * r + 2] = r2;
+  depth_key[r] = count ? __float_as_uint(z) : 0xFFFFFFFFu;
+  tile_count[r] = count;
+  order[r] = (uint32_t)r;
 }
 
-__global__ void __launch_bounds__(256) emit_keys_kernel(const float4* rec, const uint32_t* order,
-                                                        const uint32_t* offsets, uint32_t n, RenderParams rp,
-                                                        uint64_t* keys, uint32_t* vals) {
+__global__ void __launch_bounds__(256) emit_pairs_kernel(const float4* rec, const uint32_t* order,
+                                                         const uint32_t* offsets, const ViewParams* __restrict__ views,
+                                                         RenderParams rp, uint32_t* tiles, uint32_t* vals) {
   uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
+  if (s >= rp.n_records) return;
   uint32_t off = offsets[s], end = offsets[s + 1];
   if (off == end) return;
   uint32_t id = order[s];
+  const uint32_t view = id / rp.n_gaussians;
+  rp.tiles_x = views[view].tiles_x;
+  rp.tiles_y = views[view].tiles_y;
+  const uint32_t tile_base = views[view].tile_base;
   float4 r0 = rec[3 * (int64_t)id], r1 = rec[3 * (int64_t)id + 1], r2 = rec[3 * (int64_t)id + 2];
   int x0, x1, y0, y1;
   if (!tile_rect(r0.x, r0.y, r2.z, r2.w, rp, x0, x1, y0, y1)) return;
   SplatBin b = splat_bin(r0, r1, rp.log2_alpha_min);
-  uint64_t zb = (uint64_t)__float_as_uint(r2.y);
   for (int ty = y0; ty <= y1 && off < end; ++ty) {
     int t0, t1;
     if (!row_span(b, rp, ty, x0, x1, t0, t1)) continue;
-    uint64_t tile = (uint64_t)(ty * rp.tiles_x + t0);
+    uint32_t tile = tile_base + (uint32_t)(ty * rp.tiles_x + t0);
     for (int tx = t0; tx <= t1 && off < end; ++tx, ++tile, ++off) {
-      keys[off] = (tile << 32) | zb;
+      tiles[off] = tile;
       vals[off] = id;
     }
   }
 }
 
-template <int DEG, bool VEC>
-__global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, CamParams cam, RenderParams rp,
-                                                               const uint32_t* tile_count, const float4* grad2d,
-                                                               ngs_grads out) {
-  constexpr int K = (DEG + 1) * (DEG + 1);
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.n) return;
-  float* dm = out.d_means + 3 * (int64_t)i;
-  float* dls = out.d_log_scales + 3 * (int64_t)i;
-  float* dq = out.d_quats + 4 * (int64_t)i;
-  float* dsh = out.d_sh + (int64_t)i * K * 3;
-  if (tile_count[i] == 0) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) dm[k] = dls[k] = 0.f;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) dq[k] = 0.f;
-    out.d_opacity_logits[i] = 0.f;
-    if constexpr (VEC) {
-#pragma unroll
-      for (int k = 0; k < 3 * K / 4; ++k) reinterpret_cast<float4*>(dsh)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    } else {
-#pragma unroll
-      for (int k = 0; k < 3 * K; ++k) dsh[k] = 0.f;
-    }
-    return;
-  }
-  float4 g0 = grad2d[3 * (int64_t)i], g1 = grad2d[3 * (int64_t)i + 1], g2 = grad2d[3 * (int64_t)i + 2];
+// Gradient of the loss w.r.t. one Gaussian's raw parameters, summed over views.
+template <int DEG>
+struct ParamGrad {
+  static constexpr int K = (DEG + 1) * (DEG + 1);
+  float m[3], ls[3], q[4], op, sh[3 * K];
+};
+
+// Adds view `cam`'s share of Gaussian i's parameter gradient (from its splat-record gradient `gr`) to acc.
+// DIRECT (a single view): each gradient is stored to `out` as soon as it is known instead, which keeps it
+// out of the registers live across the rest of the chain.
+template <int DEG, bool VEC, bool DIRECT>
+__device__ __forceinline__ void add_view_gradient(const ngs_gaussians& g, const CamParams& cam,
+                                                  const RenderParams& rp, int i, const float4* gr,
+                                                  ParamGrad<DEG>& acc, const ngs_grads& out) {
+  constexpr int K = ProjState<DEG>::K;
+  float4 g0 = gr[0], g1 = gr[1], g2 = gr[2];
   // the replay accumulates w / ln 2 (w = dL/d(log2 alpha)): restore the factor on the six moments
   g0 = make_float4(g0.x * kLn2, g0.y * kLn2, g0.z * kLn2, g0.w * kLn2);
   g1.x *= kLn2;
@@ -413,7 +429,9 @@ __global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, 
   float dv = -(Bp * g0.x + 2.f * Cp * g0.y);
   float dA = g0.z * kConicScale, dB = g0.w * 2.f * kConicScale, dC = g1.x * kConicScale;
   float dE[3] = {g1.z, g1.w, g2.x};
-  out.d_opacity_logits[i] = g1.y * (1.f - st.aleph) / kLn2;  // L = log2(sigmoid(logit))
+  const float gop = g1.y * (1.f - st.aleph) / kLn2;  // L = log2(sigmoid(logit))
+  if constexpr (DIRECT) out.d_opacity_logits[i] = gop;
+  else acc.op += gop;
   // conic Q = Sigma'^-1 with Sigma' = U U^T + dilation I: dLoss/dSigma' = -Q G Q, G = [[dA, dB/2], [dB/2, dC]].
   // Every term of the chain is needed only as Hs u_i = -Q G Q u_i for the projected axes u_i (columns of U):
   //   dLoss/dM (column i) = 2 T^T Hs u_i,   dLoss/dT = 2 sum_i (Hs u_i) M_i^T.
@@ -473,7 +491,10 @@ __global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, 
       dS[c] += dM[3 * r + c] * st.Rq[3 * r + c];
     }
 #pragma unroll
-  for (int c = 0; c < 3; ++c) dls[c] = dS[c] * st.S[c];
+  for (int c = 0; c < 3; ++c) {
+    if constexpr (DIRECT) out.d_log_scales[3 * (int64_t)i + c] = dS[c] * st.S[c];
+    else acc.ls[c] += dS[c] * st.S[c];
+  }
   // rotation matrix of the unit quaternion (w, a, b, c)
   float w = st.qn[0], a = st.qn[1], b = st.qn[2], c = st.qn[3];
   const float* D = dRq;
@@ -485,28 +506,35 @@ __global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, 
   float dot = st.qn[0] * dqn[0] + st.qn[1] * dqn[1] + st.qn[2] * dqn[2] + st.qn[3] * dqn[3];
   float iq = 1.f / st.qnorm;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) dq[k] = (dqn[k] - st.qn[k] * dot) * iq;
+  for (int k = 0; k < 4; ++k) {
+    if constexpr (DIRECT) out.d_quats[4 * (int64_t)i + k] = (dqn[k] - st.qn[k] * dot) * iq;
+    else acc.q[k] += (dqn[k] - st.qn[k] * dot) * iq;
+  }
   // emission: dE/dsh = Y (unclamped channels); direction term into the mean
   float sh[3 * K];
   load_sh<K, VEC>(g.sh + (int64_t)i * K * 3, sh);
   float d0 = st.e[0] < 0.f ? 0.f : dE[0];
   float d1 = st.e[1] < 0.f ? 0.f : dE[1];
   float d2 = st.e[2] < 0.f ? 0.f : dE[2];
-  float wk[K], gsh[3 * K];
+  float wk[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    gsh[3 * k] = d0 * st.Y[k];
-    gsh[3 * k + 1] = d1 * st.Y[k];
-    gsh[3 * k + 2] = d2 * st.Y[k];
-    wk[k] = d0 * sh[3 * k] + d1 * sh[3 * k + 1] + d2 * sh[3 * k + 2];
-  }
-  if constexpr (VEC) {
+  for (int k = 0; k < K; ++k) wk[k] = d0 * sh[3 * k] + d1 * sh[3 * k + 1] + d2 * sh[3 * k + 2];
+  if constexpr (DIRECT) {
+    float gsh[3 * K];
 #pragma unroll
-    for (int k = 0; k < 3 * K / 4; ++k)
-      reinterpret_cast<float4*>(dsh)[k] = make_float4(gsh[4 * k], gsh[4 * k + 1], gsh[4 * k + 2], gsh[4 * k + 3]);
+    for (int k = 0; k < K; ++k) {
+      gsh[3 * k] = d0 * st.Y[k];
+      gsh[3 * k + 1] = d1 * st.Y[k];
+      gsh[3 * k + 2] = d2 * st.Y[k];
+    }
+    store_sh<K, VEC>(out.d_sh + (int64_t)i * K * 3, gsh);
   } else {
 #pragma unroll
-    for (int k = 0; k < 3 * K; ++k) dsh[k] = gsh[k];
+    for (int k = 0; k < K; ++k) {
+      acc.sh[3 * k] += d0 * st.Y[k];
+      acc.sh[3 * k + 1] += d1 * st.Y[k];
+      acc.sh[3 * k + 2] += d2 * st.Y[k];
+    }
   }
   float gdx, gdy, gdz;
   sh_basis_grad(DEG, st.dir[0], st.dir[1], st.dir[2], wk, gdx, gdy, gdz);
@@ -516,52 +544,112 @@ __global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, 
   gm[1] += (gdy - st.dir[1] * rad) * idn;
   gm[2] += (gdz - st.dir[2] * rad) * idn;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) dm[k] = gm[k];
+  for (int k = 0; k < 3; ++k) {
+    if constexpr (DIRECT) out.d_means[3 * (int64_t)i + k] = gm[k];
+    else acc.m[k] += gm[k];
+  }
+}
+
+// One thread per Gaussian; MULTI: loop over the views of a batch (records v n + i), else the one view
+// `cam0`, passed by value so that its entries are constant-bank operands rather than registers.
+// Culled splats (no tile) contribute nothing; a Gaussian culled in every view gets zeros.
+template <int DEG, bool VEC, bool MULTI>
+__global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, const ViewParams* __restrict__ views,
+                                                               CamParams cam0, RenderParams rp,
+                                                               const uint32_t* tile_count, const float4* grad2d,
+                                                               ngs_grads out) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  ParamGrad<DEG> acc;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) acc.m[k] = acc.ls[k] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc.q[k] = 0.f;
+  acc.op = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3 * K; ++k) acc.sh[k] = 0.f;
+  if constexpr (!MULTI) {
+    if (tile_count[i] != 0) {
+      add_view_gradient<DEG, VEC, true>(g, cam0, rp, i, grad2d + 3 * (int64_t)i, acc, out);
+      return;
+    }
+  } else {
+    for (int v = 0; v < (int)rp.n_views; ++v) {
+      const int64_t r = (int64_t)v * g.n + i;
+      if (tile_count[r] == 0) continue;
+      const CamParams cam = views[v].cam;
+      add_view_gradient<DEG, VEC, false>(g, cam, rp, i, grad2d + 3 * r, acc, out);
+    }
+  }
+  // the sums over views (or zeros: culled in every view)
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    out.d_means[3 * (int64_t)i + k] = acc.m[k];
+    out.d_log_scales[3 * (int64_t)i + k] = acc.ls[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out.d_quats[4 * (int64_t)i + k] = acc.q[k];
+  out.d_opacity_logits[i] = acc.op;
+  store_sh<K, VEC>(out.d_sh + (int64_t)i * K * 3, acc.sh);
 }
 
 }  // namespace
 
-void launch_project(const ngs_gaussians& g, const CamParams& cam, const RenderParams& rp, float4* rec,
-                    uint32_t* depth_key, uint32_t* tile_count, uint32_t* order, cudaStream_t s) {
+void launch_project(const ngs_gaussians& g, const ViewParams* views, const CamParams& cam0, const RenderParams& rp,
+                    float4* rec, uint32_t* depth_key, uint32_t* tile_count, uint32_t* order, cudaStream_t s) {
   if (g.n == 0) return;
-  int blocks = (int)((g.n + 255) / 256);
+  unsigned blocks = (unsigned)((g.n + 255) / 256) * rp.n_views;
   bool vec = ((uintptr_t)g.sh & 15) == 0;
+#define NGS_PROJECT(D, V) project_kernel<D, V><<<blocks, 256, 0, s>>>(g, views, cam0, rp, rec, depth_key, tile_count, \
+                                                                    order)
   switch (rp.sh_degree) {
-    case 0: project_kernel<0, false><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order); break;
+    case 0: NGS_PROJECT(0, false); break;
     case 1:
-      if (vec) project_kernel<1, true><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order);
-      else project_kernel<1, false><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order);
+      if (vec) NGS_PROJECT(1, true);
+      else NGS_PROJECT(1, false);
       break;
-    case 2: project_kernel<2, false><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order); break;
+    case 2: NGS_PROJECT(2, false); break;
     default:
-      if (vec) project_kernel<3, true><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order);
-      else project_kernel<3, false><<<blocks, 256, 0, s>>>(g, cam, rp, rec, depth_key, tile_count, order);
+      if (vec) NGS_PROJECT(3, true);
+      else NGS_PROJECT(3, false);
       break;
   }
+#undef NGS_PROJECT
 }
 
-void launch_emit_keys(const float4* rec, const uint32_t* order, const uint32_t* offsets, uint32_t n,
-                      const RenderParams& rp, int, int, uint64_t* keys, uint32_t* vals, cudaStream_t s) {
-  if (n == 0) return;
-  emit_keys_kernel<<<(n + 255) / 256, 256, 0, s>>>(rec, order, offsets, n, rp, keys, vals);
+void launch_emit_pairs(const float4* rec, const uint32_t* order, const uint32_t* offsets, const ViewParams* views,
+                       const RenderParams& rp, uint32_t* tiles, uint32_t* vals, cudaStream_t s) {
+  if (rp.n_records == 0) return;
+  emit_pairs_kernel<<<(rp.n_records + 255) / 256, 256, 0, s>>>(rec, order, offsets, views, rp, tiles, vals);
 }
 
-void launch_project_backward(const ngs_gaussians& g, const CamParams& cam, const RenderParams& rp,
-                             const float4*, const uint32_t* tile_count, const float4* grad2d, const ngs_grads& out,
-                             cudaStream_t s) {
-  if (g.n == 0) return;
+template <int DEG, bool VEC>
+static void project_backward_views(const ngs_gaussians& g, const ViewParams* views, const CamParams& cam0,
+                                   const RenderParams& rp, const uint32_t* tile_count, const float4* grad2d,
+                                   const ngs_grads& out, cudaStream_t s) {
   int blocks = (int)((g.n + 127) / 128);
+  if (rp.n_views > 1)
+    project_backward_kernel<DEG, VEC, true><<<blocks, 128, 0, s>>>(g, views, cam0, rp, tile_count, grad2d, out);
+  else
+    project_backward_kernel<DEG, VEC, false><<<blocks, 128, 0, s>>>(g, views, cam0, rp, tile_count, grad2d, out);
+}
+
+void launch_project_backward(const ngs_gaussians& g, const ViewParams* views, const CamParams& cam0,
+                             const RenderParams& rp, const uint32_t* tile_count, const float4* grad2d,
+                             const ngs_grads& out, cudaStream_t s) {
+  if (g.n == 0) return;
   bool vec = ((uintptr_t)g.sh & 15) == 0 && ((uintptr_t)out.d_sh & 15) == 0;
   switch (rp.sh_degree) {
-    case 0: project_backward_kernel<0, false><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out); break;
+    case 0: project_backward_views<0, false>(g, views, cam0, rp, tile_count, grad2d, out, s); break;
     case 1:
-      if (vec) project_backward_kernel<1, true><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out);
-      else project_backward_kernel<1, false><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out);
+      if (vec) project_backward_views<1, true>(g, views, cam0, rp, tile_count, grad2d, out, s);
+      else project_backward_views<1, false>(g, views, cam0, rp, tile_count, grad2d, out, s);
       break;
-    case 2: project_backward_kernel<2, false><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out); break;
+    case 2: project_backward_views<2, false>(g, views, cam0, rp, tile_count, grad2d, out, s); break;
     default:
-      if (vec) project_backward_kernel<3, true><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out);
-      else project_backward_kernel<3, false><<<blocks, 128, 0, s>>>(g, cam, rp, tile_count, grad2d, out);
+      if (vec) project_backward_views<3, true>(g, views, cam0, rp, tile_count, grad2d, out, s);
+      else project_backward_views<3, false>(g, views, cam0, rp, tile_count, grad2d, out, s);
       break;
   }
 }

@@ -1,14 +1,18 @@
 // Device radix sort (stable LSD, 8-bit digits), exclusive scan of tile counts, and tile ranges.
 //
-// Each pass over n items runs three kernels:
-//   upsweep   per block of 4096 items: digit histogram -> hist[digit][block]
-//   scan      one block per digit: exclusive scan of hist[digit][*] in place, digit total -> totals[digit]
+// The sort works on `nseg` equal segments of seg_len items at once, each sorted on its own (the depth sort
+// of a batch sorts every view's Gaussians in one launch per kernel). Each pass runs three kernels:
+//   upsweep   per block of 2048 items of a segment: digit histogram -> hist[segment][digit][block]
+//   scan      one block per (segment, digit): exclusive scan of that row in place, total -> totals
 //   downsweep per block: stable rank of every item within the block (warp multi-split with
 //             __match_any_sync, warps in order), reorder in shared memory so that items of one digit
 //             are contiguous, then a coalesced scatter to
-//             base(digit) + hist[digit][block] + rank, base = exclusive scan of totals.
+//             segment start + base(digit) + hist[segment][digit][block] + rank, base = exclusive scan of
+//             the segment's digit totals.
 // Stability (equal digits keep their input order) makes the LSD passes a correct sort, and it is what
 // orders equal depths by Gaussian index (the pairs are emitted in index order within one depth).
+// A count known only on the device (the number of pairs, inside a captured graph) is read by every
+// kernel: blocks past it contribute empty histograms and move nothing.
 #include "ngs_internal.cuh"
 
 namespace ngs {
@@ -57,14 +61,23 @@ __device__ __forceinline__ uint32_t digit_of(K key, int shift) {
   return (uint32_t)(key >> shift) & 0xFFu;
 }
 
+__device__ __forceinline__ uint32_t segment_count(uint32_t seg_len, const uint32_t* n_dev) {
+  return n_dev ? min(*n_dev, seg_len) : seg_len;
+}
+
 template <typename K>
-__global__ void __launch_bounds__(kThreads) upsweep_kernel(const K* __restrict__ keys, uint32_t n, int shift,
+__global__ void __launch_bounds__(kThreads) upsweep_kernel(const K* __restrict__ keys, uint32_t seg_len,
+                                                           const uint32_t* __restrict__ n_dev, int shift,
                                                            uint32_t* __restrict__ hist, uint32_t nblocks) {
   __shared__ uint32_t s_hist[kWarps][kDigits];
   int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t seg = blockIdx.x / nblocks, blk = blockIdx.x - seg * nblocks;
+  const uint32_t n = segment_count(seg_len, n_dev);
+  keys += (size_t)seg * seg_len;
+  hist += (size_t)seg * kDigits * nblocks;
   for (int i = tid; i < kWarps * kDigits; i += kThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
-  uint32_t base = blockIdx.x * (uint32_t)kTile;
+  uint32_t base = blk * (uint32_t)kTile;
   const int lane = tid & 31;
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
@@ -79,12 +92,12 @@ __global__ void __launch_bounds__(kThreads) upsweep_kernel(const K* __restrict__
     uint32_t sum = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) sum += s_hist[w][d];
-    hist[(size_t)d * nblocks + blockIdx.x] = sum;
+    hist[(size_t)d * nblocks + blk] = sum;
   }
 }
 
-// One block per digit: exclusive scan of that digit's per-block counts; the digit's total goes to
-// totals[digit] (stored after the histogram).
+// One block per (segment, digit): exclusive scan of that digit's per-block counts; the digit's total goes
+// to totals[segment][digit] (stored after the histograms).
 __global__ void __launch_bounds__(1024) scan_digit_kernel(uint32_t* hist, uint32_t nblocks, uint32_t* totals) {
   __shared__ uint32_t s_warp[32];
   uint32_t* row = hist + (size_t)blockIdx.x * nblocks;
@@ -103,8 +116,21 @@ template <typename K>
 __global__ void __launch_bounds__(kThreads) downsweep_kernel(const K* __restrict__ keys_in,
                                                              const uint32_t* __restrict__ vals_in,
                                                              K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-                                                             uint32_t n, int shift, const uint32_t* __restrict__ hist,
+                                                             uint32_t seg_len, const uint32_t* __restrict__ n_dev,
+                                                             int shift, const uint32_t* __restrict__ hist,
                                                              const uint32_t* __restrict__ totals, uint32_t nblocks) {
+  const uint32_t seg = blockIdx.x / nblocks, blk = blockIdx.x - seg * nblocks;
+  const uint32_t n = segment_count(seg_len, n_dev);
+  if (blk * (uint32_t)kTile >= n) return;  // the whole block is past the segment's items
+  {
+    const size_t off = (size_t)seg * seg_len;
+    keys_in += off;
+    vals_in += off;
+    keys_out += off;
+    vals_out += off;
+    hist += (size_t)seg * kDigits * nblocks;
+    totals += (size_t)seg * kDigits;
+  }
   extern __shared__ __align__(16) unsigned char smem[];
   K* s_keys = reinterpret_cast<K*>(smem);
   uint32_t* s_vals = reinterpret_cast<uint32_t*>(smem + sizeof(K) * kTile);
@@ -117,7 +143,7 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(const K* __restrict
   for (int i = tid; i < kWarps * kDigits; i += kThreads) (&s_cnt[0][0])[i] = 0;
   __syncthreads();
 
-  uint32_t base = blockIdx.x * (uint32_t)kTile + warp * (kTile / kWarps);
+  uint32_t base = blk * (uint32_t)kTile + warp * (kTile / kWarps);
   K key[kItems];
   uint32_t val[kItems], rank[kItems], dig[kItems];
   uint32_t lt = (1u << lane) - 1u;
@@ -153,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(const K* __restrict
     // global digit base = exclusive scan of the digit totals; this block's run starts hist[d][b] into it
     uint32_t agg;
     uint32_t ex = block_exclusive_sum<kThreads>(totals[tid], s_warp, &agg);
-    s_global[tid] = ex + hist[(size_t)tid * nblocks + blockIdx.x];
+    s_global[tid] = ex + hist[(size_t)tid * nblocks + blk];
   }
   __syncthreads();
 #pragma unroll
@@ -165,7 +191,7 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(const K* __restrict
     }
   }
   __syncthreads();
-  uint32_t count = min((uint32_t)kTile, n - blockIdx.x * (uint32_t)kTile);
+  uint32_t count = min((uint32_t)kTile, n - blk * (uint32_t)kTile);
   for (uint32_t i = tid; i < count; i += kThreads) {
     K k = s_keys[i];
     uint32_t d = digit_of(k, shift);
@@ -176,24 +202,20 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(const K* __restrict
 }
 
 template <typename K>
-int radix_sort(K* keys[2], uint32_t* vals[2], uint32_t n, int begin_bit, int end_bit, uint32_t* hist, size_t cap,
-               cudaStream_t s, int* launches) {
+int radix_sort(K* keys[2], uint32_t* vals[2], uint32_t seg_len, uint32_t nseg, const uint32_t* n_dev, int begin_bit,
+               int end_bit, uint32_t* hist, cudaStream_t s, int* launches) {
   int cur = 0;
-  if (n <= 1 || begin_bit >= end_bit) return cur;
-  uint32_t nblocks = (n + kTile - 1) / kTile;
-  uint32_t* totals = hist + (size_t)kDigits * nblocks;
-  (void)cap;
+  if (seg_len <= 1 || nseg == 0 || begin_bit >= end_bit) return cur;
+  uint32_t nblocks = (seg_len + kTile - 1) / kTile;
+  uint32_t grid = nblocks * nseg;
+  uint32_t* totals = hist + (size_t)kDigits * nblocks * nseg;
+  // at most 24 KB of dynamic shared memory (for 64-bit keys), within the default limit without an opt-in
   size_t smem = (sizeof(K) + sizeof(uint32_t)) * kTile;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(downsweep_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_set = true;
-  }
   for (int shift = begin_bit; shift < end_bit; shift += 8) {
-    upsweep_kernel<K><<<nblocks, kThreads, 0, s>>>(keys[cur], n, shift, hist, nblocks);
-    scan_digit_kernel<<<kDigits, 1024, 0, s>>>(hist, nblocks, totals);
-    downsweep_kernel<K><<<nblocks, kThreads, smem, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift,
-                                                        hist, totals, nblocks);
+    upsweep_kernel<K><<<grid, kThreads, 0, s>>>(keys[cur], seg_len, n_dev, shift, hist, nblocks);
+    scan_digit_kernel<<<kDigits * nseg, 1024, 0, s>>>(hist, nblocks, totals);
+    downsweep_kernel<K><<<grid, kThreads, smem, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], seg_len,
+                                                     n_dev, shift, hist, totals, nblocks);
     cur ^= 1;
     *launches += 3;
   }
@@ -259,30 +281,87 @@ __global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const uint32_t
   }
 }
 
-__global__ void tile_ranges_kernel(const uint64_t* __restrict__ keys, uint32_t npairs, uint2* __restrict__ ranges) {
+__global__ void tile_ranges_kernel(const uint32_t* __restrict__ tiles, uint32_t npairs_cap,
+                                   const uint32_t* __restrict__ npairs_dev, uint2* __restrict__ ranges) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t npairs = npairs_dev ? min(*npairs_dev, npairs_cap) : npairs_cap;
+  if (i >= npairs) return;
+  uint32_t t = tiles[i];
+  if (i == 0 || tiles[i - 1] != t) ranges[t].x = i;
+  if (i == npairs - 1 || tiles[i + 1] != t) ranges[t].y = i + 1;
+}
+
+__global__ void compose_keys_kernel(const uint32_t* __restrict__ tiles, const uint32_t* __restrict__ vals,
+                                    const float4* __restrict__ rec, uint32_t npairs, uint64_t* __restrict__ keys) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npairs) return;
-  uint32_t t = (uint32_t)(keys[i] >> 32);
-  if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = i;
-  if (i == npairs - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = i + 1;
+  const float z = rec[3 * (size_t)vals[i] + 2].y;
+  keys[i] = ((uint64_t)tiles[i] << 32) | (uint64_t)__float_as_uint(z);
+}
+
+// ---- tile work order for the persistent composite: descending pair count ---------------------------
+
+__device__ __forceinline__ uint32_t cost_bucket(uint2 r) {
+  const uint32_t c = r.y - r.x;
+  return (uint32_t)(kCostBuckets - 1) - (c ? 32u - (uint32_t)__clz(c) : 0u);  // 0 = most pairs
+}
+
+__global__ void __launch_bounds__(256) tile_bucket_count_kernel(const uint2* __restrict__ ranges, uint32_t ntiles,
+                                                                uint32_t* __restrict__ counts) {
+  __shared__ uint32_t s_cnt[kCostBuckets];
+  if (threadIdx.x < kCostBuckets) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < ntiles) atomicAdd(&s_cnt[cost_bucket(ranges[t])], 1u);
+  __syncthreads();
+  if (threadIdx.x < kCostBuckets && s_cnt[threadIdx.x]) atomicAdd(&counts[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(256) tile_bucket_scatter_kernel(const uint2* __restrict__ ranges, uint32_t ntiles,
+                                                                  const uint32_t* __restrict__ counts,
+                                                                  uint32_t* __restrict__ cursors,
+                                                                  uint32_t* __restrict__ work) {
+  __shared__ uint32_t s_start[kCostBuckets];
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int b = 0; b < kCostBuckets; ++b) {
+      s_start[b] = run;
+      run += counts[b];
+    }
+  }
+  __syncthreads();
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t b = t < ntiles ? cost_bucket(ranges[t]) : (uint32_t)kCostBuckets;
+  const uint32_t peers = __match_any_sync(0xFFFFFFFFu, b);
+  const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (b < (uint32_t)kCostBuckets && lane == leader) base = atomicAdd(&cursors[b], (uint32_t)__popc(peers));
+  base = __shfl_sync(0xFFFFFFFFu, base, leader);
+  if (b < (uint32_t)kCostBuckets) work[s_start[b] + base + __popc(peers & ((1u << lane) - 1u))] = t;
 }
 
 }  // namespace
 
-size_t radix_hist_words(uint32_t n) {
-  uint32_t nblocks = (n + kTile - 1) / kTile;
-  return (size_t)kDigits * (nblocks + 1);
+void launch_tile_order(const uint2* ranges, uint32_t ntiles, uint32_t* sched, uint32_t* work, cudaStream_t s,
+                       int* launches) {
+  if (ntiles == 0) return;
+  const unsigned blocks = (ntiles + 255) / 256;
+  tile_bucket_count_kernel<<<blocks, 256, 0, s>>>(ranges, ntiles, sched + 2);
+  tile_bucket_scatter_kernel<<<blocks, 256, 0, s>>>(ranges, ntiles, sched + 2, sched + 2 + kCostBuckets, work);
+  *launches += 2;
 }
 
-int radix_sort_u32(uint32_t* keys[2], uint32_t* vals[2], uint32_t n, int begin_bit, int end_bit, uint32_t* hist,
-                   size_t cap, cudaStream_t s, int* launches) {
-  return radix_sort<uint32_t>(keys, vals, n, begin_bit, end_bit, hist, cap, s, launches);
+size_t radix_hist_words(uint32_t seg_len, uint32_t nseg) {
+  uint32_t nblocks = (seg_len + kTile - 1) / kTile;
+  return (size_t)kDigits * (nblocks + 1) * nseg;
 }
 
-int radix_sort_u64(uint64_t* keys[2], uint32_t* vals[2], uint32_t n, int begin_bit, int end_bit, uint32_t* hist,
-                   size_t cap, cudaStream_t s, int* launches) {
-  return radix_sort<uint64_t>(keys, vals, n, begin_bit, end_bit, hist, cap, s, launches);
+int radix_sort_u32(uint32_t* keys[2], uint32_t* vals[2], uint32_t seg_len, uint32_t nseg, const uint32_t* n_dev,
+                   int begin_bit, int end_bit, uint32_t* hist, cudaStream_t s, int* launches) {
+  return radix_sort<uint32_t>(keys, vals, seg_len, nseg, n_dev, begin_bit, end_bit, hist, s, launches);
 }
+
+
 
 size_t scan_tmp_words(uint32_t n) { return (size_t)(n + kScanTile - 1) / kScanTile + 1; }
 
@@ -300,10 +379,17 @@ void launch_scan_counts(const uint32_t* tile_count, const uint32_t* order, uint3
   *launches += 3;
 }
 
-void launch_tile_ranges(const uint64_t* keys, uint32_t npairs, uint32_t ntiles, uint2* ranges, cudaStream_t s) {
+void launch_tile_ranges(const uint32_t* tiles, uint32_t npairs_cap, const uint32_t* npairs_dev, uint32_t ntiles,
+                        uint2* ranges, cudaStream_t s) {
   cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, s);
+  if (npairs_cap == 0) return;
+  tile_ranges_kernel<<<(npairs_cap + 255) / 256, 256, 0, s>>>(tiles, npairs_cap, npairs_dev, ranges);
+}
+
+void launch_compose_keys(const uint32_t* tiles, const uint32_t* vals, const float4* rec, uint32_t npairs,
+                         uint64_t* keys, cudaStream_t s) {
   if (npairs == 0) return;
-  tile_ranges_kernel<<<(npairs + 255) / 256, 256, 0, s>>>(keys, npairs, ranges);
+  compose_keys_kernel<<<(npairs + 255) / 256, 256, 0, s>>>(tiles, vals, rec, npairs, keys);
 }
 
 }  // namespace ngs

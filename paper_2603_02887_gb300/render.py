@@ -35,7 +35,7 @@ def default_options(**overrides) -> dict:
     _abi.load().ngs_default_options(C.byref(o))
     d = dict(alpha_min=o.alpha_min, alpha_max=o.alpha_max, t_eps=o.t_eps, dilation=o.dilation,
              near_plane=o.near_plane, background=tuple(o.background), tile_w=o.tile_w, tile_h=o.tile_h,
-             max_splats=o.max_splats)
+             max_splats=o.max_splats, chunk=o.chunk, schedule=o.schedule)
     d.update(overrides)
     return d
 
@@ -47,7 +47,11 @@ def _options(opts) -> _abi.Options:
         setattr(o, k, float(d[k]))
     for i in range(3):
         o.background[i] = float(d["background"][i])
-    o.tile_w, o.tile_h, o.max_splats, o.reserved = int(d["tile_w"]), int(d["tile_h"]), int(d["max_splats"]), 0
+    o.tile_w, o.tile_h, o.max_splats = int(d["tile_w"]), int(d["tile_h"]), int(d["max_splats"])
+    sched = d["schedule"]
+    if isinstance(sched, str):
+        sched = {"tiles": _abi.NGS_SCHEDULE_TILES, "persistent": _abi.NGS_SCHEDULE_PERSISTENT}[sched]
+    o.chunk, o.schedule = int(d["chunk"]), int(sched)
     return o
 
 
@@ -97,11 +101,26 @@ class Frame:
         self.handle = C.c_void_p()
         _abi.check(_abi.load().ngs_frame_create(renderer.ctx, C.byref(self.handle)), renderer.ctx)
         self.width = self.height = 0
+        self.n_pixels = 0
+        self.sizes = []  # (height, width) per view of the last render
 
     def view(self) -> dict:
+        """The frame's buffers: device pointers, plus the per-view pixel and tile bases as numpy arrays."""
         v = _abi.FrameView()
         _abi.check(_abi.load().ngs_frame_view_get(self.handle, C.byref(v)), self.renderer.ctx)
-        return {f: getattr(v, f) for f, _ in _abi.FrameView._fields_}
+        d = {f: getattr(v, f) for f, _ in _abi.FrameView._fields_}
+        m = d["n_views"]
+        d["view_pixel_base"] = np.ctypeslib.as_array((C.c_int64 * (m + 1)).from_address(d["view_pixel_base"])).copy()
+        d["view_tile_base"] = np.ctypeslib.as_array((C.c_uint32 * (m + 1)).from_address(d["view_tile_base"])).copy()
+        return d
+
+    def split(self, packed: torch.Tensor) -> list:
+        """Per-view views [H_v, W_v, ...] of a tensor packed like the last render's images."""
+        out, base = [], 0
+        for h, w in self.sizes:
+            out.append(packed[base:base + h * w].view(h, w, *packed.shape[1:]))
+            base += h * w
+        return out
 
     def release(self):
         if self.handle:
@@ -169,16 +188,46 @@ class Renderer:
         rc = self.lib.ngs_render(self.ctx, frame.handle, C.byref(g), C.byref(cam), C.byref(m), C.byref(o),
                                  image.data_ptr(), overdraw.data_ptr(), stream)
         _abi.check(rc, self.ctx)
-        frame.width, frame.height = W, H
+        frame.width, frame.height, frame.n_pixels, frame.sizes = W, H, H * W, [(H, W)]
         del keep
         return image, overdraw, frame
+
+    def render_batch(self, params: dict, cameras: list, model="sup", options=None, frame: Frame | None = None,
+                     images: torch.Tensor | None = None, overdraw: torch.Tensor | None = None):
+        """Render ``params`` from all ``cameras`` (any sizes) in one pass of the pipeline. Returns (images
+        [sum H W, 3], overdraw [sum H W], frame), the views packed one after the other (``frame.split``
+        gives per-view [H, W, ...] views). Each view equals ``render`` of its camera alone, bit for bit."""
+        if len(cameras) == 0:
+            raise ValueError("no cameras")
+        g, keep = _gaussians(params, self.device)
+        cams = (_abi.Camera * len(cameras))(*(_camera(c) for c in cameras))
+        kind, param = model_spec(model)
+        m = _abi.Model(kind, param)
+        o = _options(options)
+        sizes = [(c.height, c.width) for c in cams]
+        npix = sum(h * w for h, w in sizes)
+        if images is None:
+            images = torch.empty((npix, 3), dtype=torch.float32, device=self.device)
+        if overdraw is None:
+            overdraw = torch.empty((npix,), dtype=torch.int32, device=self.device)
+        if images.numel() != 3 * npix or overdraw.numel() != npix:
+            raise ValueError("images / overdraw do not hold the packed pixels of all views")
+        frame = frame or self.frame()
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        rc = self.lib.ngs_render_batch(self.ctx, frame.handle, C.byref(g), cams, len(cameras), C.byref(m),
+                                       C.byref(o), images.data_ptr(), overdraw.data_ptr(), stream)
+        _abi.check(rc, self.ctx)
+        frame.width, frame.height = sizes[0][1], sizes[0][0]
+        frame.n_pixels, frame.sizes = npix, sizes
+        del keep
+        return images, overdraw, frame
 
     def backward(self, frame: Frame, params: dict, dl_dimage: torch.Tensor, out: dict | None = None) -> dict:
         """Path-replay gradients of the frame's render w.r.t. the raw parameters (overwritten into ``out``)."""
         g, keep = _gaussians(params, self.device)
         dl = _check_param(dl_dimage, "dl_dimage", self.device)
-        if dl.numel() != frame.height * frame.width * 3:
-            raise ValueError("dl_dimage must be [H, W, 3] of the rendered frame")
+        if dl.numel() != frame.n_pixels * 3:
+            raise ValueError("dl_dimage must hold 3 values per rendered pixel ([H, W, 3], or packed for a batch)")
         if out is None:
             out = {"d_" + k: torch.empty_like(keep[k]) for k in PARAM_KEYS}
         gr = _abi.Grads(*(out["d_" + k].data_ptr() for k in PARAM_KEYS))

@@ -68,3 +68,20 @@ def describe_mismatch(gpu, ref, bad, scale=None, limit=5):
     for gi, j in list(zip(*np.nonzero(bad)))[:limit]:
         out.append(f"[{gi},{j}] gpu={a[gi, j]:.6g} ref={b[gi, j]:.6g}" + ("" if s is None else f" scale={s[gi, j]:.4g}"))
     return "; ".join(out)
+
+
+def batch_arrays(frame):
+    """Host copies of a (batch) frame's buffers: records [n_views n, 12], keys, values, ranges [tiles, 2],
+    replay state [pixels, 8], and the per-view pixel / tile bases."""
+    v = frame.view()
+    n, P, m = v["n_gaussians"], v["n_pairs"], v["n_views"]
+    T = int(v["view_tile_base"][m])
+    npix = int(v["view_pixel_base"][m])
+    return dict(
+        records=device_array(v["records"], (m * n, 12), np.float32),
+        keys=device_array(v["keys"], (P,), np.uint64),
+        values=device_array(v["values"], (P,), np.uint32),
+        ranges=device_array(v["ranges"], (T, 2), np.uint32),
+        state=device_array(v["pixel_state"], (npix, 8), np.float32),
+        pixel_base=v["view_pixel_base"], tile_base=v["view_tile_base"], view=v,
+    )

@@ -1,0 +1,213 @@
+"""GPU: batched multi-view rendering (ngs_render_batch) against single-view renders and the oracle.
+
+* bit identity: every view of a batch equals the render of its camera alone -- image, overdraw, replay
+  state, splat records, and the per-tile lists (keys with the view's first global tile removed, values
+  with the view's first record removed) -- for the four models and the three tile shapes, on cameras of
+  uneven, ragged sizes, one of them looking away from the scene (a view with no splats);
+* gradients: the backward of a batch is the gradient of the sum over its views: against the sum of the
+  FP64 oracle's per-view gradients on the tiny scene (three views), and against the sum of the GPU's own
+  single-view gradients on a clustered scene;
+* edge cases: a batch of one view equals ngs_render; n_views outside 1..4096 is rejected.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+from paper_2603_02887_gb300 import _abi, synth  # noqa: E402
+from paper_2603_02887_gb300.render import PARAM_KEYS, Renderer  # noqa: E402
+from tests.gpu_util import batch_arrays, describe_mismatch, frame_arrays, grad_mismatch, upload  # noqa: E402
+
+MODELS = ["exp", "sub", "lin", "sup"]
+NT = os.cpu_count() or 4
+SMALL_SIZES = ((97, 61), (128, 128), (200, 113), (64, 40), (160, 90))
+
+
+@pytest.fixture(scope="module")
+def rnd():
+    r = Renderer("cuda:0")
+    yield r
+    r.close()
+
+
+@pytest.fixture(scope="module")
+def clustered():
+    scene = synth.clustered_scene(20000, seed=5, sh_degree=3)
+    cams = synth.orbit_cameras(5, radius=12.0, seed=7, resolutions=SMALL_SIZES)
+    away = synth.look_at(np.array([0.0, 0.0, -12.0]), np.array([0.0, 0.0, -30.0]), 72, 56)
+    return scene, cams[:3] + [away] + cams[3:]
+
+
+def _bits(a):
+    return np.ascontiguousarray(a).view(np.uint32)
+
+
+@pytest.mark.parametrize("tile", [(8, 8), (16, 16), (16, 32)])
+@pytest.mark.parametrize("model", MODELS)
+def test_batch_views_bit_identical_to_single(rnd, clustered, model, tile):
+    scene, cams = clustered
+    params = upload(scene)
+    n = len(scene["means"])
+    opts = dict(tile_w=tile[0], tile_h=tile[1])
+    images, overdraw, frame = rnd.render_batch(params, cams, model, options=opts)
+    imgs, ods = frame.split(images), frame.split(overdraw)
+    ba = batch_arrays(frame)
+    tile_of = (ba["keys"] >> np.uint64(32)).astype(np.int64)
+    single_frame = rnd.frame()
+    total_pairs = 0
+    for v, cam in enumerate(cams):
+        img1, od1, single_frame = rnd.render(params, cam, model, options=opts, frame=single_frame)
+        assert torch.equal(imgs[v], img1), f"view {v}: image differs"
+        assert torch.equal(ods[v], od1), f"view {v}: overdraw differs"
+        sa = frame_arrays(single_frame)
+        assert np.array_equal(_bits(ba["records"][v * n:(v + 1) * n]), _bits(sa["records"])), f"view {v}: records"
+        p0, p1 = ba["pixel_base"][v], ba["pixel_base"][v + 1]
+        assert np.array_equal(_bits(ba["state"][p0:p1]), _bits(sa["state"].reshape(-1, 8))), f"view {v}: state"
+        t0, t1 = int(ba["tile_base"][v]), int(ba["tile_base"][v + 1])
+        sel = (tile_of >= t0) & (tile_of < t1)
+        assert np.array_equal(ba["keys"][sel] - (np.uint64(t0) << np.uint64(32)), sa["keys"]), f"view {v}: keys"
+        assert np.array_equal(ba["values"][sel] - np.uint32(v * n), sa["values"]), f"view {v}: values"
+        r = ba["ranges"][t0:t1].astype(np.int64)
+        nonempty = r[:, 1] > r[:, 0]
+        sr = sa["ranges"].astype(np.int64)
+        assert np.array_equal(nonempty, sr[:, 1] > sr[:, 0]), f"view {v}: non-empty tiles"
+        start = int(np.nonzero(sel)[0][0]) if sel.any() else 0
+        assert np.array_equal(r[nonempty] - start, sr[nonempty]), f"view {v}: ranges"
+        total_pairs += sa["view"]["n_pairs"]
+        if v == 3:  # the camera looking away from the scene
+            assert sa["view"]["n_pairs"] == 0 and not torch.any(img1)
+    assert total_pairs == ba["view"]["n_pairs"]
+    rnd.recycle(single_frame)
+
+
+def _tiny_views():
+    c0 = synth.tiny_camera()
+    c1 = synth.look_at(np.array([0.3, -0.2, 0.0]), np.array([0.0, 0.0, 4.0]), 96, 80, hfov_deg=50.0)
+    c2 = synth.look_at(np.array([-0.4, 0.1, 0.2]), np.array([0.1, 0.0, 4.0]), 112, 72, hfov_deg=55.0)
+    return [c0, c1, c2]
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_batch_gradient_is_sum_over_views_oracle(rnd, model):
+    scene = synth.tiny_scene(0)
+    cams = _tiny_views()
+    params = upload(scene)
+    images, _, frame = rnd.render_batch(params, cams, model)
+    dls, ref = [], None
+    for v, cam in enumerate(cams):
+        H, W = cam["height"], cam["width"]
+        ref0 = oracle.render(scene, cam, model, nthreads=NT)
+        ok = ~ref0["fragile"]
+        assert ref0["fragile"].sum() <= max(2, 0.01 * ok.size)
+        err = np.abs(frame.split(images)[v].cpu().numpy() - ref0["image"])[ok]
+        assert err.max() <= 1e-4, (v, err.max())
+        g = synth.upstream_gradient(H, W, seed=20 + v).astype(np.float64) * ok[..., None]
+        r = oracle.render(scene, cam, model, nthreads=NT, dl_dimage=g)
+        dls.append(g.reshape(-1, 3))
+        if ref is None:
+            ref = {k: np.array(val, copy=True) for k, val in r.items() if k.startswith(("d_", "s_"))}
+            ref["fragile_gauss"] = r["fragile_gauss"].copy()
+        else:
+            for k in ref:
+                if k.startswith(("d_", "s_")):
+                    ref[k] = ref[k] + r[k]
+            ref["fragile_gauss"] |= r["fragile_gauss"]
+    dl = torch.from_numpy(np.concatenate(dls).astype(np.float32)).cuda()
+    grads = rnd.backward(frame, params, dl)
+    report = {}
+    for k in PARAM_KEYS:
+        a = grads["d_" + k].cpu().numpy()
+        bad = grad_mismatch(a, ref["d_" + k], exclude=ref["fragile_gauss"], scale=ref["s_" + k])
+        if bad.any():
+            report[k] = f"{int(bad.sum())} of {bad.size}: " + describe_mismatch(a, ref["d_" + k], bad, ref["s_" + k])
+    assert not report, report
+
+
+@pytest.mark.parametrize("model", ["exp", "sup"])
+def test_batch_gradient_is_sum_of_single_view_gradients(rnd, clustered, model):
+    scene, cams = clustered
+    params = upload(scene)
+    images, _, frame = rnd.render_batch(params, cams, model)
+    dl_views = [torch.from_numpy(synth.upstream_gradient(c["height"], c["width"], seed=40 + v)).cuda()
+                for v, c in enumerate(cams)]
+    grads = rnd.backward(frame, params, torch.cat([d.reshape(-1, 3) for d in dl_views]))
+    total = {k: torch.zeros_like(grads[k], dtype=torch.float64) for k in grads}
+    for v, cam in enumerate(cams):
+        _, _, f1 = rnd.render(params, cam, model)
+        g1 = rnd.backward(f1, params, dl_views[v])
+        for k in total:
+            total[k] += g1[k].double()
+        rnd.recycle(f1)
+    for k in total:
+        a, b = grads[k].double(), total[k]
+        tol = 1e-3 * torch.maximum(b.abs(), 1e-3 * b.abs().max()) + 1e-5 * b.abs().max()
+        assert torch.all((a - b).abs() <= tol), (k, float(((a - b).abs() - tol).max()))
+
+
+def test_batch_of_one_equals_render(rnd):
+    scene, cam = synth.clustered_scene(5000, seed=3, sh_degree=2), synth.outside_camera(211, 157)
+    params = upload(scene)
+    for model in MODELS:
+        img1, od1, f1 = rnd.render(params, cam, model)
+        img2, od2, f2 = rnd.render_batch(params, [cam], model)
+        assert torch.equal(img1.reshape(-1, 3), img2) and torch.equal(od1.reshape(-1), od2)
+        g = torch.from_numpy(synth.upstream_gradient(157, 211, seed=1)).cuda()
+        ga, gb = rnd.backward(f1, params, g), rnd.backward(f2, params, g)
+        for k in ga:  # the same kernels; only the order of the replay's atomic additions may differ
+            assert torch.allclose(ga[k], gb[k], rtol=1e-4, atol=1e-6 * float(ga[k].abs().max())), k
+        rnd.recycle(f1)
+        rnd.recycle(f2)
+
+
+def test_batch_rejects_bad_view_counts(rnd):
+    scene, cam = synth.tiny_scene(0), synth.tiny_camera()
+    params = upload(scene)
+    with pytest.raises(ValueError):
+        rnd.render_batch(params, [], "exp")
+    with pytest.raises(_abi.NGSError, match="n_views"):
+        rnd.render_batch(params, [synth.pinhole(cam["viewmat"], 4, 4, 10.0, 10.0)] * 4097, "exp")
+
+
+@pytest.mark.parametrize("model", ["exp", "sup"])
+@pytest.mark.parametrize("tile", [(8, 8), (16, 16), (16, 32)])
+def test_chunk_and_schedule_do_not_change_results(rnd, clustered, model, tile):
+    """Every staging chunk (tile pixels x 1/2, 1, 2) and both schedules (one CTA per tile; persistent CTAs
+    over the tiles by descending pair count) give bit-identical images, overdraw and replay state, and
+    gradients equal up to the order of the replay's atomic additions."""
+    scene, cams = clustered
+    params = upload(scene)
+    P = tile[0] * tile[1]
+    dl = None
+    ref = None
+    for chunk in (P // 2, P, 2 * P):
+        for schedule in ("tiles", "persistent"):
+            opts = dict(tile_w=tile[0], tile_h=tile[1], chunk=chunk, schedule=schedule)
+            img, od, frame = rnd.render_batch(params, cams, model, options=opts)
+            st = batch_arrays(frame)["state"]
+            if dl is None:
+                dl = torch.from_numpy(synth.upstream_gradient(1, img.shape[0], seed=9).reshape(-1, 3)).cuda()
+            g = rnd.backward(frame, params, dl)
+            if ref is None:
+                ref = (img.clone(), od.clone(), st, {k: v.clone() for k, v in g.items()})
+                continue
+            assert torch.equal(img, ref[0]) and torch.equal(od, ref[1]), (chunk, schedule)
+            assert np.array_equal(st.view(np.uint32), ref[2].view(np.uint32)), (chunk, schedule)
+            for k, v in g.items():
+                r = ref[3][k]
+                assert torch.allclose(v, r, rtol=1e-4, atol=1e-6 * float(r.abs().max())), (chunk, schedule, k)
+            rnd.recycle(frame)
+
+
+def test_invalid_chunk_and_schedule_rejected(rnd):
+    scene, cam = synth.tiny_scene(0), synth.tiny_camera()
+    params = upload(scene)
+    with pytest.raises(_abi.NGSError, match="chunk"):
+        rnd.render(params, cam, "exp", options=dict(chunk=100))
+    with pytest.raises(_abi.NGSError, match="schedule"):
+        rnd.render(params, cam, "exp", options=dict(schedule=7))
