@@ -209,6 +209,17 @@ NGS_API int ngs_render_backward_static(ngs_ctx* ctx, const ngs_frame* frame, con
  * the records, and synchronises the device to do so. */
 NGS_API int ngs_frame_view_get(const ngs_frame* frame, ngs_frame_view* out);
 
+/* CUDA graphs (off by default). When enabled, ngs_render and ngs_render_batch run each of their two phases
+ * (projection .. pair count; key emission .. composite) as a CUDA graph, captured on the context's own
+ * stream the first time a frame meets a configuration (Gaussian arrays, image sizes, model, options,
+ * output pointers) and replayed after that. Camera poses are copied in by the graph, so a new pose needs
+ * no new capture; phase 2 is captured for a pair capacity (the count met plus a quarter) that replays reuse
+ * while the count fits, its kernels reading the exact count from device memory. Results are bit-identical
+ * to the direct launches. Stage timing is not recorded for replayed phases. ngs_graph_captures returns how
+ * many phases the context has captured. */
+NGS_API int ngs_set_graphs(ngs_ctx* ctx, int enable);
+NGS_API int64_t ngs_graph_captures(const ngs_ctx* ctx);
+
 /* Stage timing. When enabled, every render/backward records CUDA events on its stream around each
  * stage and ngs_stage_times() adds up the elapsed time per stage (synchronising on the recorded
  * events). Stages: 0 project, 1 depth sort, 2 scan + key emit, 3 tile sort, 4 tile ranges,

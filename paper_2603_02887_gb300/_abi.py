@@ -73,6 +73,8 @@ SIGNATURES = {
     "ngs_render_backward_static": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.c_void_p,
                                              C.POINTER(Grads), C.c_void_p]),
     "ngs_frame_view_get": (C.c_int, [C.c_void_p, C.POINTER(FrameView)]),
+    "ngs_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
+    "ngs_graph_captures": (C.c_int64, [C.c_void_p]),
     "ngs_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "ngs_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
     "ngs_reset_stage_times": (None, [C.c_void_p]),

@@ -97,77 +97,6 @@ using namespace ngs;
     if (_rc != NGS_OK) return _rc; \
   } while (0)
 
-extern "C" {
-
-NGS_API void ngs_default_options(ngs_options* o) {
-  if (!o) return;
-  memset(o, 0, sizeof(*o));
-  o->alpha_min = 1.0f / 255.0f;
-  o->alpha_max = 0.99f;
-  o->t_eps = 1e-4f;
-  o->dilation = 0.3f;
-  o->near_plane = 0.2f;
-  o->tile_w = 16;
-  o->tile_h = 16;
-  o->max_splats = 0;
-}
-
-NGS_API int ngs_create(ngs_ctx** out) {
-  if (!out) return NGS_ERR_INVALID_ARG;
-  *out = nullptr;
-  ngs_ctx* ctx = new (std::nothrow) ngs_ctx();
-  if (!ctx) return NGS_ERR_OUT_OF_MEMORY;
-  cudaError_t e = cudaGetDevice(&ctx->device);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_total, 2 * sizeof(uint64_t));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    delete ctx;
-    return NGS_ERR_CUDA;
-  }
-  *out = ctx;
-  return NGS_OK;
-}
-
-NGS_API void ngs_destroy(ngs_ctx* ctx) {
-  if (!ctx) return;
-  cudaDeviceSynchronize();
-  free_buf(ctx->hist);
-  free_buf(ctx->scan_tmp);
-  free_buf(ctx->grad2d);
-  free_buf(ctx->total);
-  if (ctx->h_total) cudaFreeHost(ctx->h_total);
-  for (auto& p : ctx->pending) {
-    cudaEventDestroy(p.a);
-    cudaEventDestroy(p.b);
-  }
-  for (auto e : ctx->event_pool) cudaEventDestroy(e);
-  delete ctx;
-}
-
-NGS_API const char* ngs_last_error(const ngs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
-
-NGS_API int ngs_frame_create(ngs_ctx* ctx, ngs_frame** out) {
-  if (!ctx || !out) return NGS_ERR_INVALID_ARG;
-  ngs_frame* f = new (std::nothrow) ngs_frame();
-  if (!f) return fail(ctx, NGS_ERR_OUT_OF_MEMORY, "host allocation of a frame failed");
-  f->ctx = ctx;
-  *out = f;
-  return NGS_OK;
-}
-
-NGS_API void ngs_frame_destroy(ngs_frame* f) {
-  if (!f) return;
-  cudaDeviceSynchronize();
-  DevBuf* bufs[] = {&f->rec,     &f->tile_count, &f->gkeys[0], &f->gkeys[1], &f->gvals[0], &f->gvals[1],
-                    &f->offsets, &f->ptile[0],   &f->ptile[1], &f->pvals[0], &f->pvals[1], &f->ranges,
-                    &f->state,   &f->views,      &f->keys64,   &f->work,     &f->sched};
-  for (DevBuf* b : bufs) free_buf(*b);
-  if (f->h_views) cudaFreeHost(f->h_views);
-  if (f->views_uploaded) cudaEventDestroy(f->views_uploaded);
-  delete f;
-}
-
 static int check_camera(ngs_ctx* ctx, const ngs_camera* cam) {
   if (!cam) return fail(ctx, NGS_ERR_INVALID_ARG, "null camera");
   if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
@@ -224,9 +153,9 @@ static void camera_params(const ngs_camera* cam, CamParams& cp) {
   cp.H = cam->height;
 }
 
-// Upload the frame's view table through its pinned staging buffer. The staging is rewritten only after
-// the previous upload from it has completed.
-static int upload_views(ngs_ctx* ctx, ngs_frame* f, cudaStream_t s) {
+// Stage the view table in the frame's pinned buffer (the copy to the device is a launch of phase 1). The
+// staging is rewritten only after the previous copy from it has completed.
+static int stage_views(ngs_ctx* ctx, ngs_frame* f) {
   size_t bytes = sizeof(ViewParams) * f->view_host.size();
   if (f->views_uploaded) {
     cudaError_t e = cudaEventSynchronize(f->views_uploaded);
@@ -248,9 +177,161 @@ static int upload_views(ngs_ctx* ctx, ngs_frame* f, cudaStream_t s) {
   }
   NGS_TRY(ensure(ctx, f->views, bytes));
   memcpy(f->h_views, f->view_host.data(), bytes);
-  cudaError_t e = cudaMemcpyAsync(f->views.p, f->h_views, bytes, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaEventRecord(f->views_uploaded, s);
-  if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("view table upload: ") + cudaGetErrorString(e));
+  return NGS_OK;
+}
+
+// Everything a render derives from its arguments before the first launch.
+struct RenderPlan {
+  RenderParams rp;
+  const ngs_gaussians* g;
+  uint32_t n, R, ntiles;
+  uint64_t pix_total;
+  float* image;
+  int32_t* overdraw;
+};
+
+// Phase 1: view table upload, projection, depth sort, scan of the tile counts, and the copy of the pair
+// count (and the device error word) to pinned host memory. Launches only.
+static void phase1(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, cudaStream_t s) {
+  const RenderParams& rp = pl.rp;
+  const ViewParams* views = f->views.as<ViewParams>();
+  cudaMemcpyAsync(f->views.p, f->h_views, sizeof(ViewParams) * f->view_host.size(), cudaMemcpyHostToDevice, s);
+  cudaEvent_t ev;
+  // 1. projection of every (view, Gaussian): splat records, FP32 depth keys (all-ones for splats that take
+  //    no tile), tile counts
+  stage_begin(ctx, s, 0, &ev);
+  launch_project(*pl.g, views, f->view_host[0].cam, rp, f->rec.as<float4>(), f->gkeys[0].as<uint32_t>(),
+                 f->tile_count.as<uint32_t>(), f->gvals[0].as<uint32_t>(), s);
+  stage_end(ctx, s, 0, ev, pl.n ? 1 : 0);
+  // 2. stable sort of each view's splats by FP32 depth (ties keep Gaussian order)
+  stage_begin(ctx, s, 1, &ev);
+  int launches = 0;
+  {
+    uint32_t* k2[2] = {f->gkeys[0].as<uint32_t>(), f->gkeys[1].as<uint32_t>()};
+    uint32_t* v2[2] = {f->gvals[0].as<uint32_t>(), f->gvals[1].as<uint32_t>()};
+    f->g_final = radix_sort_u32(k2, v2, pl.n, rp.n_views, nullptr, 0, 32, ctx->hist.as<uint32_t>(), s, &launches);
+  }
+  stage_end(ctx, s, 1, ev, launches);
+  // 3. exclusive scan of the tile counts in (view, depth) order; the pair count goes to the host
+  stage_begin(ctx, s, 2, &ev);
+  launches = 0;
+  launch_scan_counts(f->tile_count.as<uint32_t>(), f->gvals[f->g_final].as<uint32_t>(), pl.R,
+                     f->offsets.as<uint32_t>(), ctx->scan_tmp.as<uint64_t>(), ctx->total.as<uint64_t>(), s,
+                     &launches);
+  cudaMemcpyAsync(ctx->h_total, ctx->total.p, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+  stage_end(ctx, s, 2, ev, launches);
+}
+
+// Phase 2: key emission, tile sort, tile ranges (+ work list), composite. `cap` items are covered by the
+// sort's grid; with np_dev (graph replays) the kernels read the actual pair count from the device.
+static void phase2(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, uint32_t cap, const uint32_t* np_dev,
+                   cudaStream_t s) {
+  const RenderParams& rp = pl.rp;
+  const ViewParams* views = f->views.as<ViewParams>();
+  cudaEvent_t ev;
+  stage_begin(ctx, s, 2, &ev);
+  launch_emit_pairs(f->rec.as<float4>(), f->gvals[f->g_final].as<uint32_t>(), f->offsets.as<uint32_t>(), views, rp,
+                    f->ptile[0].as<uint32_t>(), f->pvals[0].as<uint32_t>(), s);
+  stage_end(ctx, s, 2, ev, pl.R ? 1 : 0);
+  // 4. stable sort of the pairs by global tile: the depth order inside each tile is kept, so the result is
+  //    the order of the full 64-bit (tile << 32 | depth) keys
+  stage_begin(ctx, s, 3, &ev);
+  int launches = 0;
+  {
+    uint32_t* k2[2] = {f->ptile[0].as<uint32_t>(), f->ptile[1].as<uint32_t>()};
+    uint32_t* v2[2] = {f->pvals[0].as<uint32_t>(), f->pvals[1].as<uint32_t>()};
+    f->p_final = radix_sort_u32(k2, v2, cap, 1, np_dev, 0, tile_bits(pl.ntiles), ctx->hist.as<uint32_t>(), s,
+                                &launches);
+  }
+  stage_end(ctx, s, 3, ev, launches);
+  // 5. per-tile [start, end); for the persistent schedule, the tiles by descending pair count
+  stage_begin(ctx, s, 4, &ev);
+  launches = cap ? 1 : 0;
+  launch_tile_ranges(f->ptile[f->p_final].as<uint32_t>(), cap, np_dev, pl.ntiles, f->ranges.as<uint2>(), s);
+  const uint32_t* work = nullptr;
+  uint32_t* counter = nullptr;
+  if (rp.schedule == NGS_SCHEDULE_PERSISTENT) {
+    cudaMemsetAsync(f->sched.p, 0, sizeof(uint32_t) * kSchedWords, s);
+    launch_tile_order(f->ranges.as<uint2>(), pl.ntiles, f->sched.as<uint32_t>(), f->work.as<uint32_t>(), s,
+                      &launches);
+    work = f->work.as<uint32_t>();
+    counter = f->sched.as<uint32_t>();
+  }
+  stage_end(ctx, s, 4, ev, launches);
+  // 6. composite every tile of every view
+  stage_begin(ctx, s, 5, &ev);
+  launch_composite_forward(f->rec.as<float4>(), f->pvals[f->p_final].as<uint32_t>(), f->ranges.as<uint2>(), rp, views,
+                           pl.image, pl.overdraw, f->state.as<float4>(), work, counter, ctx->num_sms, s);
+  stage_end(ctx, s, 5, ev, 1);
+}
+
+// Serialised launch arguments of a phase: a captured graph is replayed only while they are unchanged.
+struct KeyBuf {
+  std::vector<uint8_t> b;
+  template <typename T>
+  void add(const T& v) {
+    const uint8_t* p = reinterpret_cast<const uint8_t*>(&v);
+    b.insert(b.end(), p, p + sizeof(T));
+  }
+};
+
+// Run one phase: directly, or (graphs enabled) by replaying the frame's graph for it, captured anew on
+// the context's capture stream when the key changed.
+template <typename Fn>
+static int run_phase(ngs_ctx* ctx, ngs_frame* f, int which, const KeyBuf& key, cudaStream_t s, Fn&& launch) {
+  if (!ctx->graphs) {
+    launch(s);
+    return check_launch(ctx, which == 0 ? "render phase 1" : "render phase 2");
+  }
+  GraphSlot& g = f->graph[which];
+  if (!g.exec || g.key != key.b) {
+    if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(ctx, NGS_ERR_CUDA, "creating the capture stream failed");
+    const bool timing = ctx->timing;
+    int64_t before[NGS_NUM_STAGES];
+    for (int i = 0; i < NGS_NUM_STAGES; ++i) before[i] = ctx->stage_launches[i];
+    const int64_t total_before = ctx->launches;
+    ctx->timing = false;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      launch(ctx->cap_stream);
+      e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    }
+    ctx->timing = timing;
+    for (int i = 0; i < NGS_NUM_STAGES; ++i) {  // counted per replay below, not at capture
+      g.stage_launches[i] = (int)(ctx->stage_launches[i] - before[i]);
+      ctx->stage_launches[i] = before[i];
+    }
+    ctx->launches = total_before;
+    if (e == cudaSuccess && g.exec) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(g.exec, graph, &info) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+      }
+    }
+    if (e == cudaSuccess && !g.exec) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      g.exec = nullptr;
+      g.key.clear();
+      return fail(ctx, NGS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    g.key = key.b;
+    g.p_final = f->p_final;
+    g.g_final = f->g_final;
+    ++ctx->graph_captures;
+  }
+  f->p_final = g.p_final;
+  f->g_final = g.g_final;
+  cudaError_t e = cudaGraphLaunch(g.exec, s);
+  if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  for (int i = 0; i < NGS_NUM_STAGES; ++i) {
+    ctx->stage_launches[i] += g.stage_launches[i];
+    ctx->launches += g.stage_launches[i];
+  }
   return NGS_OK;
 }
 
@@ -290,7 +371,8 @@ static int render_views(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, cons
   const uint64_t records64 = (uint64_t)g->n * (uint64_t)n_views;
   if (records64 >= (1ull << 32)) return fail(ctx, NGS_ERR_INVALID_ARG, "n * n_views must be below 2^32");
 
-  RenderParams rp;
+  RenderPlan pl;
+  RenderParams& rp = pl.rp;
   memset(&rp, 0, sizeof rp);
   rp.alpha_min = o->alpha_min;
   rp.alpha_max = o->alpha_max;
@@ -315,8 +397,18 @@ static int render_views(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, cons
   rp.n_views = (uint32_t)n_views;
   rp.n_records = (uint32_t)records64;
   rp.n_tiles = (uint32_t)tiles_total;
-  const uint32_t n = (uint32_t)g->n, R = rp.n_records, ntiles = rp.n_tiles;
+  // a captured projection takes every camera from the view table, so that a replay serves any pose
+  rp.cam_from_table = (n_views > 1 || ctx->graphs) ? 1 : 0;
+  pl.g = g;
+  pl.n = (uint32_t)g->n;
+  pl.R = rp.n_records;
+  pl.ntiles = rp.n_tiles;
+  pl.pix_total = pix_total;
+  pl.image = image;
+  pl.overdraw = overdraw;
+  const uint32_t R = pl.R;
 
+  // phase 1 buffers
   NGS_TRY(ensure(ctx, f->rec, sizeof(float4) * 3 * (size_t)std::max(R, 1u)));
   NGS_TRY(ensure(ctx, f->tile_count, sizeof(uint32_t) * (size_t)std::max(R, 1u)));
   for (int k = 0; k < 2; ++k) {
@@ -324,7 +416,7 @@ static int render_views(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, cons
     NGS_TRY(ensure(ctx, f->gvals[k], sizeof(uint32_t) * (size_t)std::max(R, 1u)));
   }
   NGS_TRY(ensure(ctx, f->offsets, sizeof(uint32_t) * ((size_t)R + 1)));
-  NGS_TRY(ensure(ctx, f->ranges, sizeof(uint2) * (size_t)ntiles));
+  NGS_TRY(ensure(ctx, f->ranges, sizeof(uint2) * (size_t)pl.ntiles));
   NGS_TRY(ensure(ctx, f->state, sizeof(float4) * 2 * (size_t)pix_total));
   NGS_TRY(ensure(ctx, ctx->scan_tmp, sizeof(uint64_t) * scan_tmp_words(R)));
   if (!ctx->total.p) {
@@ -332,36 +424,30 @@ static int render_views(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, cons
     cudaMemsetAsync(ctx->total.p, 0, 2 * sizeof(uint64_t), s);
   }
   rp.check = reinterpret_cast<uint32_t*>(ctx->total.as<uint64_t>() + 1);
-  NGS_TRY(ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(std::max(n, 1u), (uint32_t)n_views)));
-  NGS_TRY(upload_views(ctx, f, s));
-  const ViewParams* views = f->views.as<ViewParams>();
-
-  cudaEvent_t ev;
-  // 1. projection of every (view, Gaussian): splat records, FP32 depth keys (all-ones for splats that take
-  //    no tile), tile counts
-  stage_begin(ctx, s, 0, &ev);
-  launch_project(*g, views, f->view_host[0].cam, rp, f->rec.as<float4>(), f->gkeys[0].as<uint32_t>(),
-                 f->tile_count.as<uint32_t>(), f->gvals[0].as<uint32_t>(), s);
-  stage_end(ctx, s, 0, ev, n ? 1 : 0);
-  NGS_TRY(check_launch(ctx, "project"));
-  // 2. stable sort of each view's splats by FP32 depth (ties keep Gaussian order)
-  stage_begin(ctx, s, 1, &ev);
-  int launches = 0;
-  {
-    uint32_t* k2[2] = {f->gkeys[0].as<uint32_t>(), f->gkeys[1].as<uint32_t>()};
-    uint32_t* v2[2] = {f->gvals[0].as<uint32_t>(), f->gvals[1].as<uint32_t>()};
-    f->g_final = radix_sort_u32(k2, v2, n, (uint32_t)n_views, nullptr, 0, 32, ctx->hist.as<uint32_t>(), s, &launches);
+  NGS_TRY(ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(std::max(pl.n, 1u), (uint32_t)n_views)));
+  if (rp.schedule == NGS_SCHEDULE_PERSISTENT) {
+    NGS_TRY(ensure(ctx, f->work, sizeof(uint32_t) * (size_t)std::max(pl.ntiles, 1u)));
+    NGS_TRY(ensure(ctx, f->sched, sizeof(uint32_t) * kSchedWords));
   }
-  stage_end(ctx, s, 1, ev, launches);
-  NGS_TRY(check_launch(ctx, "depth sort"));
-  // 3. exclusive scan of the tile counts in (view, depth) order; the pair count comes back to the host
-  stage_begin(ctx, s, 2, &ev);
-  launches = 0;
-  const uint32_t* order = f->gvals[f->g_final].as<uint32_t>();
-  launch_scan_counts(f->tile_count.as<uint32_t>(), order, R, f->offsets.as<uint32_t>(), ctx->scan_tmp.as<uint64_t>(),
-                     ctx->total.as<uint64_t>(), s, &launches);
-  NGS_TRY(check_launch(ctx, "scan"));
-  cudaError_t e = cudaMemcpyAsync(ctx->h_total, ctx->total.p, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+  NGS_TRY(stage_views(ctx, f));
+
+  KeyBuf k1;
+  k1.add(*g);
+  k1.add(rp);
+  k1.add(f->view_host.size());
+  for (const ViewParams& vp : f->view_host) {  // everything but the pose, which the replay copies anew
+    k1.add(vp.cam.W);
+    k1.add(vp.cam.H);
+    k1.add(vp.tile_base);
+    k1.add(vp.pix_base);
+  }
+  for (const DevBuf* b : {&f->rec, &f->tile_count, &f->gkeys[0], &f->gkeys[1], &f->gvals[0], &f->gvals[1], &f->offsets,
+                          &f->views, &ctx->hist, &ctx->scan_tmp, &ctx->total})
+    k1.add(b->p);
+  k1.add(f->h_views);
+  k1.add(ctx->h_total);
+  NGS_TRY(run_phase(ctx, f, 0, k1, s, [&](cudaStream_t st) { phase1(ctx, f, pl, st); }));
+  cudaError_t e = cudaEventRecord(f->views_uploaded, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("reading the pair count: ") + cudaGetErrorString(e));
   if (ctx->h_total[1] != 0) {  // a bounds check fired in an earlier call on this context
@@ -369,60 +455,117 @@ static int render_views(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, cons
     return fail(ctx, NGS_ERR_DEVICE_CHECK, "a kernel bounds check fired in an earlier call on this context; its "
                                            "output was not valid");
   }
-  uint64_t P = *ctx->h_total;
+  const uint64_t P = *ctx->h_total;
   if (P >= (1ull << 31)) return fail(ctx, NGS_ERR_INVALID_ARG, "more than 2^31 (tile, Gaussian) pairs");
-  uint32_t np = (uint32_t)P;
-  for (int k = 0; k < 2; ++k) {
-    NGS_TRY(ensure(ctx, f->ptile[k], sizeof(uint32_t) * (size_t)std::max(np, 1u)));
-    NGS_TRY(ensure(ctx, f->pvals[k], sizeof(uint32_t) * (size_t)std::max(np, 1u)));
-  }
-  NGS_TRY(ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(std::max(np, 1u), 1)));
-  launch_emit_pairs(f->rec.as<float4>(), order, f->offsets.as<uint32_t>(), views, rp, f->ptile[0].as<uint32_t>(),
-                    f->pvals[0].as<uint32_t>(), s);
-  stage_end(ctx, s, 2, ev, launches + (R ? 1 : 0));
-  NGS_TRY(check_launch(ctx, "emit keys"));
-  // 4. stable sort of the pairs by global tile: the depth order inside each tile is kept, so the result is
-  //    the order of the full 64-bit (tile << 32 | depth) keys
-  stage_begin(ctx, s, 3, &ev);
-  launches = 0;
-  {
-    uint32_t* k2[2] = {f->ptile[0].as<uint32_t>(), f->ptile[1].as<uint32_t>()};
-    uint32_t* v2[2] = {f->pvals[0].as<uint32_t>(), f->pvals[1].as<uint32_t>()};
-    int tb = tile_bits(ntiles);
-    f->p_final = radix_sort_u32(k2, v2, np, 1, nullptr, 0, tb, ctx->hist.as<uint32_t>(), s, &launches);
-  }
-  stage_end(ctx, s, 3, ev, launches);
-  NGS_TRY(check_launch(ctx, "tile sort"));
-  // 5. per-tile [start, end); for the persistent schedule, the tiles by descending pair count
-  stage_begin(ctx, s, 4, &ev);
-  launches = np ? 1 : 0;
-  launch_tile_ranges(f->ptile[f->p_final].as<uint32_t>(), np, nullptr, ntiles, f->ranges.as<uint2>(), s);
-  const uint32_t* work = nullptr;
-  uint32_t* counter = nullptr;
-  if (rp.schedule == NGS_SCHEDULE_PERSISTENT) {
-    NGS_TRY(ensure(ctx, f->work, sizeof(uint32_t) * (size_t)ntiles));
-    NGS_TRY(ensure(ctx, f->sched, sizeof(uint32_t) * kSchedWords));
-    cudaMemsetAsync(f->sched.p, 0, sizeof(uint32_t) * kSchedWords, s);
-    launch_tile_order(f->ranges.as<uint2>(), ntiles, f->sched.as<uint32_t>(), f->work.as<uint32_t>(), s, &launches);
-    work = f->work.as<uint32_t>();
-    counter = f->sched.as<uint32_t>();
-  }
-  stage_end(ctx, s, 4, ev, launches);
-  NGS_TRY(check_launch(ctx, "tile ranges"));
-  // 6. composite every tile of every view
-  stage_begin(ctx, s, 5, &ev);
-  launch_composite_forward(f->rec.as<float4>(), f->pvals[f->p_final].as<uint32_t>(), f->ranges.as<uint2>(), rp, views,
-                           image, overdraw, f->state.as<float4>(), work, counter, ctx->num_sms, s);
-  stage_end(ctx, s, 5, ev, 1);
-  NGS_TRY(check_launch(ctx, "composite"));
+  const uint32_t np = (uint32_t)P;
 
-  f->n = n;
+  // phase 2: exact sizes, or, for graph replays, a capacity that a replay reuses while the count fits
+  uint32_t cap = np;
+  const uint32_t* np_dev = nullptr;
+  if (ctx->graphs) {
+    if (np > f->pair_cap) f->pair_cap = (uint32_t)std::min<uint64_t>((uint64_t)np + np / 4 + 1024, (1ull << 31) - 1);
+    cap = f->pair_cap;
+    np_dev = reinterpret_cast<const uint32_t*>(ctx->total.p);  // low word of the pair count (< 2^31)
+  }
+  for (int k = 0; k < 2; ++k) {
+    NGS_TRY(ensure(ctx, f->ptile[k], sizeof(uint32_t) * (size_t)std::max(cap, 1u)));
+    NGS_TRY(ensure(ctx, f->pvals[k], sizeof(uint32_t) * (size_t)std::max(cap, 1u)));
+  }
+  NGS_TRY(ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(std::max(cap, 1u), 1)));
+  KeyBuf k2;
+  k2.add(rp);
+  k2.add(cap);
+  k2.add(np_dev);
+  k2.add(f->g_final);
+  k2.add(image);
+  k2.add(overdraw);
+  k2.add(ctx->num_sms);
+  for (const DevBuf* b : {&f->rec, &f->gvals[0], &f->gvals[1], &f->offsets, &f->views, &f->ptile[0], &f->ptile[1],
+                          &f->pvals[0], &f->pvals[1], &ctx->hist, &f->ranges, &f->work, &f->sched, &f->state})
+    k2.add(b->p);
+  NGS_TRY(run_phase(ctx, f, 1, k2, s, [&](cudaStream_t st) { phase2(ctx, f, pl, cap, np_dev, st); }));
+
+  f->n = pl.n;
   f->pairs = np;
   f->n_views = n_views;
   f->n_pixels = (int64_t)pix_total;
   f->rp = rp;
   f->has_render = true;
   return NGS_OK;
+}
+
+extern "C" {
+
+NGS_API void ngs_default_options(ngs_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->alpha_min = 1.0f / 255.0f;
+  o->alpha_max = 0.99f;
+  o->t_eps = 1e-4f;
+  o->dilation = 0.3f;
+  o->near_plane = 0.2f;
+  o->tile_w = 16;
+  o->tile_h = 16;
+  o->max_splats = 0;
+}
+
+NGS_API int ngs_create(ngs_ctx** out) {
+  if (!out) return NGS_ERR_INVALID_ARG;
+  *out = nullptr;
+  ngs_ctx* ctx = new (std::nothrow) ngs_ctx();
+  if (!ctx) return NGS_ERR_OUT_OF_MEMORY;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_total, 2 * sizeof(uint64_t));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return NGS_ERR_CUDA;
+  }
+  *out = ctx;
+  return NGS_OK;
+}
+
+NGS_API void ngs_destroy(ngs_ctx* ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  free_buf(ctx->hist);
+  free_buf(ctx->scan_tmp);
+  free_buf(ctx->grad2d);
+  free_buf(ctx->total);
+  if (ctx->h_total) cudaFreeHost(ctx->h_total);
+  for (auto& p : ctx->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : ctx->event_pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+NGS_API const char* ngs_last_error(const ngs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+NGS_API int ngs_frame_create(ngs_ctx* ctx, ngs_frame** out) {
+  if (!ctx || !out) return NGS_ERR_INVALID_ARG;
+  ngs_frame* f = new (std::nothrow) ngs_frame();
+  if (!f) return fail(ctx, NGS_ERR_OUT_OF_MEMORY, "host allocation of a frame failed");
+  f->ctx = ctx;
+  *out = f;
+  return NGS_OK;
+}
+
+NGS_API void ngs_frame_destroy(ngs_frame* f) {
+  if (!f) return;
+  cudaDeviceSynchronize();
+  DevBuf* bufs[] = {&f->rec,     &f->tile_count, &f->gkeys[0], &f->gkeys[1], &f->gvals[0], &f->gvals[1],
+                    &f->offsets, &f->ptile[0],   &f->ptile[1], &f->pvals[0], &f->pvals[1], &f->ranges,
+                    &f->state,   &f->views,      &f->keys64,   &f->work,     &f->sched};
+  for (DevBuf* b : bufs) free_buf(*b);
+  if (f->h_views) cudaFreeHost(f->h_views);
+  if (f->views_uploaded) cudaEventDestroy(f->views_uploaded);
+  for (GraphSlot& g : f->graph)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  delete f;
 }
 
 NGS_API int ngs_render(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const ngs_camera* cam,
@@ -506,6 +649,14 @@ NGS_API int ngs_frame_view_get(const ngs_frame* fc, ngs_frame_view* out) {
   out->pixel_state = f->state.as<float>();
   return NGS_OK;
 }
+
+NGS_API int ngs_set_graphs(ngs_ctx* ctx, int enable) {
+  if (!ctx) return NGS_ERR_INVALID_ARG;
+  ctx->graphs = enable != 0;
+  return NGS_OK;
+}
+
+NGS_API int64_t ngs_graph_captures(const ngs_ctx* ctx) { return ctx ? ctx->graph_captures : 0; }
 
 NGS_API int ngs_set_timing(ngs_ctx* ctx, int enable) {
   if (!ctx) return NGS_ERR_INVALID_ARG;

@@ -44,6 +44,8 @@ struct RenderParams {
   int max_splats;
   int chunk;             // records staged per round of a tile's list walk (tile pixels x 1/2, 1 or 2)
   int schedule;          // NGS_SCHEDULE_*
+  int cam_from_table;    // the projection reads every camera from the view table (else a single view's
+                         // camera is a kernel parameter)
   int sh_degree;
   uint32_t n_gaussians;  // n: Gaussians per view
   uint32_t n_views;
@@ -166,7 +168,20 @@ struct ngs_ctx {
   double stage_ms[NGS_NUM_STAGES] = {0};
   int64_t stage_launches[NGS_NUM_STAGES] = {0};
   int64_t launches = 0;
+  bool graphs = false;                 // capture each render phase once per configuration and replay it
+  cudaStream_t cap_stream = nullptr;   // private stream for capturing
+  int64_t graph_captures = 0;
 };
+
+namespace ngs {
+// A captured render phase of a frame, replayed while its launch arguments (`key`) are unchanged.
+struct GraphSlot {
+  std::vector<uint8_t> key;
+  cudaGraphExec_t exec = nullptr;
+  int stage_launches[NGS_NUM_STAGES] = {0};
+  int g_final = 0, p_final = 0;
+};
+}  // namespace ngs
 
 struct ngs_frame {
   ngs_ctx* ctx = nullptr;
@@ -188,6 +203,8 @@ struct ngs_frame {
   ngs::DevBuf keys64;  // 64-bit keys, materialised only for ngs_frame_view_get
   ngs::DevBuf work;    // persistent schedule: tiles by descending pair count
   ngs::DevBuf sched;   // persistent schedule: kSchedWords counters (see launch_tile_order)
+  ngs::GraphSlot graph[2];  // phase 1 (projection .. pair count) and phase 2 (emission .. composite)
+  uint32_t pair_cap = 0;    // pair capacity of the captured phase 2
   int g_final = 0;  // which gvals[] holds the depth-sorted Gaussian order
   int p_final = 0;  // which ptile[]/pvals[] hold the sorted pairs
 };

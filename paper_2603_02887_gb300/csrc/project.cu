@@ -327,8 +327,8 @@ __device__ __forceinline__ uint32_t count_tiles(float4 r0, float4 r1, float4 r2,
 
 // Block b works on view b % n_views and Gaussians [256 (b / n_views), +256): the views of one block of
 // Gaussians run side by side, so their parameters are read from HBM once and from L2 afterwards.
-// A single view takes its camera from the kernel parameters (cam0), a batch from the view table; the
-// arithmetic below is the same code either way.
+// A single view takes its camera from the kernel parameters (cam0), a batch (or a captured graph, which
+// must serve any pose) from the view table; the arithmetic below is the same code either way.
 template <int DEG, bool VEC>
 __global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, const ViewParams* __restrict__ views,
                                                       CamParams cam0, RenderParams rp, float4* rec,
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, const Vie
   const uint32_t view = blockIdx.x % rp.n_views;
   int i = (blockIdx.x / rp.n_views) * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
-  const CamParams cam = rp.n_views == 1 ? cam0 : views[view].cam;
+  const CamParams cam = rp.cam_from_table ? views[view].cam : cam0;
   if (rp.n_views != 1) {
     rp.tiles_x = views[view].tiles_x;
     rp.tiles_y = views[view].tiles_y;

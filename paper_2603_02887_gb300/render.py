@@ -236,6 +236,13 @@ class Renderer:
         _abi.check(rc, self.ctx)
         return out
 
+    def set_graphs(self, enable: bool):
+        """Capture each render phase as a CUDA graph once per configuration and replay it."""
+        _abi.check(self.lib.ngs_set_graphs(self.ctx, int(bool(enable))), self.ctx)
+
+    def graph_captures(self) -> int:
+        return int(self.lib.ngs_graph_captures(self.ctx))
+
     def set_timing(self, enable: bool):
         _abi.check(self.lib.ngs_set_timing(self.ctx, int(bool(enable))), self.ctx)
 

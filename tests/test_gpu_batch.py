@@ -211,3 +211,53 @@ def test_invalid_chunk_and_schedule_rejected(rnd):
         rnd.render(params, cam, "exp", options=dict(chunk=100))
     with pytest.raises(_abi.NGSError, match="schedule"):
         rnd.render(params, cam, "exp", options=dict(schedule=7))
+
+
+def test_graph_replay_bit_identical_and_reused(clustered):
+    """With CUDA graphs on, renders equal the direct launches bit for bit; a new pose of the same sizes is a
+    replay (no capture); a pair count above the captured capacity makes a new phase-2 capture."""
+    scene, cams = clustered
+    params = upload(scene)
+    direct, graphed = Renderer("cuda:0"), Renderer("cuda:0")
+    graphed.set_graphs(True)
+    try:
+        fd, fg = direct.frame(), graphed.frame()
+        for model in ("exp", "sup"):
+            for schedule in ("tiles", "persistent"):
+                opts = dict(schedule=schedule)
+                a = direct.render_batch(params, cams, model, options=opts, frame=fd)
+                b = graphed.render_batch(params, cams, model, options=opts, frame=fg)
+                assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]), (model, schedule)
+        # same sizes, other poses: replays only
+        img = torch.empty_like(a[0])
+        od = torch.empty_like(a[1])
+        graphed.render_batch(params, cams, "sup", frame=fg, images=img, overdraw=od)
+        n0 = graphed.graph_captures()
+        rng = np.random.default_rng(99)
+        moved = []
+        for c in cams:  # keep each view's size, change its pose
+            d = rng.standard_normal(3)
+            moved.append(synth.look_at(12.0 * d / np.linalg.norm(d), np.zeros(3), c["width"], c["height"]))
+        for pose_set in (moved, cams):
+            gi, go, _ = graphed.render_batch(params, pose_set, "sup", frame=fg, images=img, overdraw=od)
+            di, do, _ = direct.render_batch(params, pose_set, "sup", frame=fd)
+            assert torch.equal(gi, di) and torch.equal(go, do)
+        assert graphed.graph_captures() == n0, "a new pose must not need a new capture"
+        # single view: a camera facing away (no pairs) then one facing the scene (many): the pair count
+        # outgrows the captured capacity, so phase 2 is captured anew
+        far = synth.look_at(np.array([0.0, 0.0, -12.0]), np.array([0.0, 0.0, -30.0]), 320, 240)
+        near = synth.outside_camera(320, 240)
+        f1 = graphed.frame()
+        graphed.render(params, far, "lin", frame=f1)
+        n1 = graphed.graph_captures()
+        gi, go, f1 = graphed.render(params, near, "lin", frame=f1)
+        assert graphed.graph_captures() > n1
+        di, do, _ = direct.render(params, near, "lin")
+        assert torch.equal(gi, di) and torch.equal(go, do)
+        g1 = graphed.backward(f1, params, torch.ones_like(gi))
+        d1 = direct.backward(direct.render(params, near, "lin")[2], params, torch.ones_like(di))
+        for k in g1:
+            assert torch.allclose(g1[k], d1[k], rtol=1e-4, atol=1e-6 * float(d1[k].abs().max())), k
+    finally:
+        direct.close()
+        graphed.close()
