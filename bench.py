@@ -44,9 +44,13 @@ def parse():
     p.add_argument("--gaussians", type=int, default=500_000)
     p.add_argument("--width", type=int, default=1920)
     p.add_argument("--height", type=int, default=1080)
-    p.add_argument("--tile", default="16x16")
-    p.add_argument("--chunk", type=int, default=0, help="records staged per round (0: tile pixels)")
-    p.add_argument("--schedule", default="tiles", choices=["tiles", "persistent"])
+    p.add_argument("--tile", default=None, help="fixed tile shape WxH (default: autotuned per model)")
+    p.add_argument("--chunk", type=int, default=None, help="records staged per round (default: autotuned)")
+    p.add_argument("--schedule", default=None, choices=["tiles", "persistent"], help="(default: autotuned)")
+    p.add_argument("--no-graphs", action="store_true", help="launch the render phases directly")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched multi-view measurement")
+    p.add_argument("--batched-gaussians", type=int, default=3_000_000)
+    p.add_argument("--batched-views", type=int, default=32)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-crop", type=int, default=0, help="oracle crop side (0: sized automatically)")
@@ -145,13 +149,11 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    tw, th = (int(v) for v in args.tile.split("x"))
-    opts = dict(tile_w=tw, tile_h=th, chunk=args.chunk, schedule=args.schedule)
-
     scene, cam = workload(args, rank)
     H, W = cam["height"], cam["width"]
     params = {k: torch.from_numpy(np.ascontiguousarray(scene[k])).to(dev) for k in PARAM_KEYS}
     r = Renderer(dev)
+    opts, tuning = launch_options(args, r, params, [cam])
     frames = {m: r.frame() for m in MODELS}
     images = {m: torch.empty((H, W, 3), device=dev) for m in MODELS}
     ods = {m: torch.empty((H, W), dtype=torch.int32, device=dev) for m in MODELS}
@@ -161,8 +163,8 @@ def run_ours(args):
                      for k, v in synth.perturbed(scene, seed=1).items()}
     dl = {}
     for m in MODELS:
-        tgt, _, f = r.render(target_params, cam, m, opts)
-        img, _, _ = r.render(params, cam, m, opts, frame=frames[m], image=images[m], overdraw=ods[m])
+        tgt, _, f = r.render(target_params, cam, m, opts[m])
+        img, _, _ = r.render(params, cam, m, opts[m], frame=frames[m], image=images[m], overdraw=ods[m])
         dl[m] = torch.sign(img - tgt).contiguous()
         r.recycle(f)
     del target_params
@@ -173,13 +175,14 @@ def run_ours(args):
             ev = per_model_events[m] if per_model_events is not None else None
             if ev:
                 ev[0].record()
-            r.render(params, cam, m, opts, frame=frames[m], image=images[m], overdraw=ods[m])
+            r.render(params, cam, m, opts[m], frame=frames[m], image=images[m], overdraw=ods[m])
             if ev:
                 ev[1].record()
             r.backward(frames[m], params, dl[m], out=grads[m])
             if ev:
                 ev[2].record()
 
+    r.set_graphs(not args.no_graphs)
     for _ in range(args.warmup):
         flush.zero_()
         step()
@@ -210,6 +213,20 @@ def run_ours(args):
     launches = r.launch_count() - launches0
     stage = r.stage_times()
     r.set_timing(False)
+    # replayed graph phases carry no stage events: the forward stages come from two more steps with direct
+    # launches (the backward stages, the dominant ones, are the timed region's own)
+    stage_direct = stage
+    if not args.no_graphs:
+        r.set_graphs(False)
+        r.set_timing(True)
+        r.reset_stage_times()
+        for _ in range(2):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        stage_direct = r.stage_times()
+        r.set_timing(False)
+        r.set_graphs(not args.no_graphs)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = max_over_ranks(sum(step_ms), device=dev)
     ms_per_step = total_ms / K
@@ -233,6 +250,9 @@ def run_ours(args):
 
     # roofline of the dominant stage
     stage_ms = {k: v[0] / K for k, v in stage.items()}
+    if stage_direct is not stage:
+        for k in ("project", "depth_sort", "scan_emit", "tile_sort", "tile_ranges", "composite_fwd"):
+            stage_ms[k] = stage_direct[k][0] / 2
     dominant = max(stage_ms, key=stage_ms.get)
     roof = roofline(dominant, stage_ms, frames, ods, args.gaussians, measured_peaks(), clk)
 
@@ -243,16 +263,24 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "gaussians": args.gaussians, "width": W, "height": H, "sh_degree": 3,
                    "models": {"exp": "exponential", "sub": "quadratic c=-0.5", "lin": "quadratic c=0",
                               "sup": "quadratic c=+0.5"},
-                   "tile": args.tile, "chunk": args.chunk, "schedule": args.schedule, "step": "per model: render + path-replay backward",
+                   "launch_options": {m: {k: opts[m][k] for k in ("tile_w", "tile_h", "chunk", "schedule")}
+                                      for m in MODELS},
+                   "launch_options_source": tuning, "cuda_graphs": not args.no_graphs,
+                   "step": "per model: render + path-replay backward",
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"views x{world}",
                    "pairs_per_view": int(frames["exp"].view()["n_pairs"])},
         "per_model": per_model,
         "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
+        "stage_ms_source": ("timed region" if args.no_graphs else
+                            "backward stages: timed region; forward stages: 2 further steps with direct launches"),
         "gpu_launches": int(launches), "gpu_launches_per_step": round(launches / K, 1),
         "roofline": roof, "clocks": clk,
     }
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, r, scene, cam, opts, dl, dev, world)
+    if not args.no_batched and world == 1:
+        del params, frames, grads
+        line["batched"] = run_batched(args, r, dev, line["per_model"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, scene, cam)
     if rank == 0:
@@ -267,7 +295,7 @@ FLOP_TEST = 11                              # per walked list entry: d = p - mu,
 FLOP_FWD = {"quad": 20, "exp": 12}          # per composited splat, forward
 FLOP_BWD = {"quad": 50, "exp": 45}          # per composited splat, replay + chain to the splat record
 BYTES = {  # per Gaussian (projection, depth sort, projection backward) or per (tile, Gaussian) pair
-    "project": 236 + 48 + 12, "depth_sort": 16, "scan_emit": 12, "tile_sort": 24, "tile_ranges": 8,
+    "project": 236 + 48 + 12, "depth_sort": 16, "scan_emit": 8, "tile_sort": 16, "tile_ranges": 4,
     "project_bwd": 236 + 48 + 236,
 }
 
@@ -326,6 +354,100 @@ def roofline(dominant, stage_ms, frames, ods, n_gauss, peaks, clk):
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
 
+def launch_options(args, r, params, cams, reps=2):
+    """Per-model launch options: the fixed ones given on the command line, else the library's autotuner
+    (render + backward timed under every tile shape x chunk x schedule on this very workload)."""
+    fixed = {}
+    if args.tile:
+        fixed["tile_w"], fixed["tile_h"] = (int(v) for v in args.tile.split("x"))
+    if args.chunk is not None:
+        fixed["chunk"] = args.chunk
+    if args.schedule:
+        fixed["schedule"] = args.schedule
+    from paper_2603_02887_gb300.render import default_options
+    if fixed:
+        return {m: default_options(**fixed) for m in MODELS}, "command line"
+    out = {}
+    for m in MODELS:
+        best, _ = r.autotune(params, cams, m, backward=True, reps=reps)
+        out[m] = best
+    return out, f"autotuned (render + backward, median of {reps} with L2 cleared before each, 18 candidates per model)"
+
+
+def run_batched(args, r, dev, single_view_models):
+    """The batched form: one ngs_render_batch call renders a 3M-Gaussian clustered scene (SH 3) from 32
+    cameras of uneven sizes (640x360 .. 1920x1080, poses on a sphere of radius 12 m), forward and forward +
+    backward, against rendering the same 32 views one at a time on the same GPU; all views are checked
+    bit-identical between the two forms."""
+    import torch
+
+    from paper_2603_02887_gb300 import synth
+    from paper_2603_02887_gb300.render import PARAM_KEYS
+
+    scene = synth.clustered_scene(args.batched_gaussians, seed=0, sh_degree=3)
+    cams = synth.orbit_cameras(args.batched_views, radius=12.0, seed=2)
+    params = {k: torch.from_numpy(np.ascontiguousarray(scene[k])).to(dev) for k in PARAM_KEYS}
+    del scene
+    npix = sum(c["width"] * c["height"] for c in cams)
+    opts, tuning = launch_options(args, r, params, cams, reps=3)
+    # the one-view-at-a-time form gets its own tuning, on the largest view
+    big = max(cams, key=lambda c: c["width"] * c["height"])
+    vopts, _ = launch_options(args, r, params, [big], reps=3)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {"gaussians": args.batched_gaussians, "views": len(cams), "mpix_per_batch": round(npix / 1e6, 3),
+           "resolutions": sorted({f"{c['width']}x{c['height']}" for c in cams}), "launch_options_source": tuning,
+           "cuda_graphs": not args.no_graphs, "l2": "flushed before every timed call (256 MB write)"}
+    fb = r.frame()
+    # the one-view-at-a-time form keeps a frame and output buffers per view, so it replays its graphs too
+    fviews = [r.frame() for _ in cams]
+    vimg = [torch.empty((c["height"], c["width"], 3), device=dev) for c in cams]
+    vod = [torch.empty((c["height"], c["width"]), dtype=torch.int32, device=dev) for c in cams]
+    reps = 3
+    for m in MODELS:
+        img, od, fb = r.render_batch(params, cams, m, opts[m], frame=fb)
+        dl = torch.sign(img - 0.5).contiguous()
+        g = r.backward(fb, params, dl)
+        torch.cuda.synchronize()
+        tf, tfb, ts = [], [], []
+        for _ in range(reps):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            r.render_batch(params, cams, m, opts[m], frame=fb, images=img, overdraw=od)
+            e[1].record()
+            r.backward(fb, params, dl, out=g)
+            e[2].record()
+            torch.cuda.synchronize()
+            tf.append(e[0].elapsed_time(e[1]))
+            tfb.append(e[0].elapsed_time(e[2]))
+        for _ in range(3):
+            flush.zero_()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            for v, c in enumerate(cams):
+                r.render(params, c, m, vopts[m], frame=fviews[v], image=vimg[v], overdraw=vod[v])
+            s1.record()
+            torch.cuda.synchronize()
+            ts.append(s0.elapsed_time(s1))
+        same = all(torch.equal(a, b) for a, b in zip(vimg, fb.split(img)))
+        fwd, fwdbwd, single = min(tf), min(tfb), min(ts)
+        out[m] = {"fwd_mpix_s": round(npix / fwd / 1e3, 1), "fwd_bwd_mpix_s": round(npix / fwdbwd / 1e3, 1),
+                  "fwd_ms": round(fwd, 3), "fwd_bwd_ms": round(fwdbwd, 3),
+                  "one_view_at_a_time_fwd_ms": round(single, 3),
+                  "one_view_at_a_time_fwd_mpix_s": round(npix / single / 1e3, 1),
+                  "batched_speedup_fwd": round(single / fwd, 3), "bit_identical_to_single_views": bool(same),
+                  "pairs": int(fb.view()["n_pairs"]), "overdraw_mean": round(float(od.double().mean()), 3),
+                  "launch_options": {k: opts[m][k] for k in ("tile_w", "tile_h", "chunk", "schedule")},
+                  "one_view_at_a_time_launch_options": {k: vopts[m][k] for k in ("tile_w", "tile_h", "chunk",
+                                                                                  "schedule")}}
+    for m in MODELS[1:]:
+        out[m]["overdraw_reduction_vs_exp"] = round(out["exp"]["overdraw_mean"] / max(out[m]["overdraw_mean"], 1e-9), 3)
+    r.recycle(fb)
+    for f in fviews:
+        f.release()
+    return out
+
+
 def run_e2e(args, r, scene, cam, opts, dl, dev, world):
     """Same metric through the public API with host buffers: each step copies the parameters and the
     upstream gradients from pinned host memory, renders + backpropagates every model, and reads the
@@ -351,7 +473,7 @@ def run_e2e(args, r, scene, cam, opts, dl, dev, world):
             dev_p[k].copy_(host[k], non_blocking=True)
         for m in MODELS:
             dev_dl[m].copy_(host_dl[m], non_blocking=True)
-            img, od, f = r.render(dev_p, cam, m, opts, frame=frames[m])
+            img, od, f = r.render(dev_p, cam, m, opts[m], frame=frames[m])
             g = r.backward(f, dev_p, dev_dl[m])
             out_img[m].copy_(img, non_blocking=True)
             out_od[m].copy_(od, non_blocking=True)

@@ -220,6 +220,27 @@ NGS_API int ngs_frame_view_get(const ngs_frame* frame, ngs_frame_view* out);
 NGS_API int ngs_set_graphs(ngs_ctx* ctx, int enable);
 NGS_API int64_t ngs_graph_captures(const ngs_ctx* ctx);
 
+/* Autotuner. Times the render (and, when dl_dimage and grads are both given, the backward too) of this
+ * batch under every supported launch configuration -- tile shape 8x8, 16x16, 16x32; chunk half, once and
+ * twice the tile's pixel count; schedule tiles or persistent -- and writes the fastest into *best, every
+ * other field copied from *base. Each candidate gets one untimed render (+ backward) and then `reps`
+ * (1..100) timed ones, CUDA events on `stream` around each; a candidate's time is the median. When
+ * flush_bytes > 0, a context-owned scratch of that size is cleared before each timed call (outside the
+ * events), so that no candidate finds its inputs in L2 left over from the previous call. The results
+ * of a render never depend on these choices, only its speed. `table` (may be NULL) receives one entry per
+ * candidate, up to table_cap. Returns the number of candidates timed, or a negative status.
+ * Synchronises the stream; the frame holds the last candidate's render afterwards. Arguments otherwise as
+ * ngs_render_batch and ngs_render_backward. */
+typedef struct {
+  int32_t tile_w, tile_h, chunk, schedule;
+  float ms; /* median time of one render (+ backward), milliseconds */
+} ngs_tune_entry;
+NGS_API int ngs_autotune(ngs_ctx* ctx, ngs_frame* frame, const ngs_gaussians* g, const ngs_camera* cams,
+                         int32_t n_views, const ngs_model* model, const ngs_options* base, float* images,
+                         int32_t* overdraw, const float* dl_dimage, const ngs_grads* grads, int32_t reps,
+                         int64_t flush_bytes, ngs_options* best, ngs_tune_entry* table, int32_t table_cap,
+                         void* stream);
+
 /* Stage timing. When enabled, every render/backward records CUDA events on its stream around each
  * stage and ngs_stage_times() adds up the elapsed time per stage (synchronising on the recorded
  * events). Stages: 0 project, 1 depth sort, 2 scan + key emit, 3 tile sort, 4 tile ranges,

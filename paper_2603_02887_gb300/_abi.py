@@ -43,6 +43,11 @@ class Options(C.Structure):
                 ("tile_h", C.c_int32), ("max_splats", C.c_int32), ("chunk", C.c_int32), ("schedule", C.c_int32)]
 
 
+class TuneEntry(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("chunk", C.c_int32), ("schedule", C.c_int32),
+                ("ms", C.c_float)]
+
+
 class Grads(C.Structure):
     _fields_ = [("d_means", C.c_void_p), ("d_log_scales", C.c_void_p), ("d_quats", C.c_void_p),
                 ("d_opacity_logits", C.c_void_p), ("d_sh", C.c_void_p)]
@@ -73,6 +78,10 @@ SIGNATURES = {
     "ngs_render_backward_static": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.c_void_p,
                                              C.POINTER(Grads), C.c_void_p]),
     "ngs_frame_view_get": (C.c_int, [C.c_void_p, C.POINTER(FrameView)]),
+    "ngs_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.POINTER(Camera), C.c_int32,
+                               C.POINTER(Model), C.POINTER(Options), C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.POINTER(Grads), C.c_int32, C.c_int64, C.POINTER(Options), C.POINTER(TuneEntry),
+                               C.c_int32, C.c_void_p]),
     "ngs_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
     "ngs_graph_captures": (C.c_int64, [C.c_void_p]),
     "ngs_set_timing": (C.c_int, [C.c_void_p, C.c_int]),

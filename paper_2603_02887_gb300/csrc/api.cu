@@ -336,9 +336,9 @@ static int run_phase(ngs_ctx* ctx, ngs_frame* f, int which, const KeyBuf& key, c
 }
 
 // The render pipeline for n_views cameras of one set of Gaussians (n_views = 1 for ngs_render).
-static int render_views(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const ngs_camera* cams, int n_views,
-                        const ngs_model* model, const ngs_options* o, float* image, int32_t* overdraw,
-                        cudaStream_t s) {
+int ngs::render_views(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const ngs_camera* cams, int n_views,
+                      const ngs_model* model, const ngs_options* o, float* image, int32_t* overdraw,
+                      cudaStream_t s) {
   if (!f || f->ctx != ctx) return fail(ctx, NGS_ERR_INVALID_ARG, "frame missing or from another context");
   NGS_TRY(check_inputs(ctx, g, model, o));
   if (!cams) return fail(ctx, NGS_ERR_INVALID_ARG, "null camera");
@@ -534,6 +534,7 @@ NGS_API void ngs_destroy(ngs_ctx* ctx) {
   free_buf(ctx->scan_tmp);
   free_buf(ctx->grad2d);
   free_buf(ctx->total);
+  free_buf(ctx->flush);
   if (ctx->h_total) cudaFreeHost(ctx->h_total);
   for (auto& p : ctx->pending) {
     cudaEventDestroy(p.a);
@@ -583,6 +584,13 @@ NGS_API int ngs_render_batch(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g,
 
 NGS_API int ngs_render_backward(ngs_ctx* ctx, const ngs_frame* f, const ngs_gaussians* g, const float* dl_dimage,
                                 const ngs_grads* out, void* stream) {
+  return ngs::backward_frame(ctx, f, g, dl_dimage, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+int ngs::backward_frame(ngs_ctx* ctx, const ngs_frame* f, const ngs_gaussians* g, const float* dl_dimage,
+                        const ngs_grads* out, cudaStream_t s) {
   if (!ctx) return NGS_ERR_INVALID_ARG;
   if (!f || f->ctx != ctx || !f->has_render) return fail(ctx, NGS_ERR_INVALID_ARG, "frame holds no render");
   if (!g || !dl_dimage || !out) return fail(ctx, NGS_ERR_INVALID_ARG, "null argument");
@@ -590,7 +598,6 @@ NGS_API int ngs_render_backward(ngs_ctx* ctx, const ngs_frame* f, const ngs_gaus
     return fail(ctx, NGS_ERR_INVALID_ARG, "Gaussians do not match the rendered frame");
   if (g->n > 0 && (!out->d_means || !out->d_log_scales || !out->d_quats || !out->d_opacity_logits || !out->d_sh))
     return fail(ctx, NGS_ERR_INVALID_ARG, "null gradient array");
-  cudaStream_t s = (cudaStream_t)stream;
   const uint32_t R = f->rp.n_records;
   NGS_TRY(ensure(ctx, ctx->grad2d, sizeof(float4) * 3 * (size_t)std::max(R, 1u)));
   cudaMemsetAsync(ctx->grad2d.p, 0, sizeof(float4) * 3 * (size_t)R, s);
@@ -615,6 +622,8 @@ NGS_API int ngs_render_backward(ngs_ctx* ctx, const ngs_frame* f, const ngs_gaus
   NGS_TRY(check_launch(ctx, "projection backward"));
   return NGS_OK;
 }
+
+extern "C" {
 
 NGS_API int ngs_frame_view_get(const ngs_frame* fc, ngs_frame_view* out) {
   if (!fc || !out) return NGS_ERR_INVALID_ARG;

@@ -160,6 +160,7 @@ struct ngs_ctx {
   ngs::DevBuf scan_tmp;  // block sums of scans
   ngs::DevBuf grad2d;    // per-Gaussian splat-record gradients (backward)
   ngs::DevBuf total;     // device-side pair count (uint64) and error word (uint64)
+  ngs::DevBuf flush;     // autotuner: scratch cleared between timed calls to evict L2
   uint64_t* h_total = nullptr;  // pinned mirror of `total` (2 words)
   bool timing = false;
   struct Pending { cudaEvent_t a, b; int stage; };
@@ -210,6 +211,12 @@ struct ngs_frame {
 };
 
 namespace ngs {
+
+// the render and backward pipelines (api.cu), also used by the autotuner
+int render_views(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const ngs_camera* cams, int n_views,
+                 const ngs_model* model, const ngs_options* o, float* image, int32_t* overdraw, cudaStream_t s);
+int backward_frame(ngs_ctx* ctx, const ngs_frame* f, const ngs_gaussians* g, const float* dl_dimage,
+                   const ngs_grads* out, cudaStream_t s);
 
 // error / allocation helpers (api.cu)
 int fail(ngs_ctx* ctx, int code, const std::string& msg);

@@ -222,6 +222,41 @@ class Renderer:
         del keep
         return images, overdraw, frame
 
+    def autotune(self, params: dict, cameras: list, model="sup", options=None, backward: bool = True, reps: int = 3,
+                 frame: Frame | None = None, flush_bytes: int = 256 << 20):
+        """Time every tile shape x chunk x schedule on this batch (render, and backward with a unit upstream
+        gradient when ``backward``; L2 cleared before each timed call when ``flush_bytes``) and return
+        (fastest options dict, [(tile_w, tile_h, chunk, schedule, ms)])."""
+        g, keep = _gaussians(params, self.device)
+        cams = (_abi.Camera * len(cameras))(*(_camera(c) for c in cameras))
+        kind, param = model_spec(model)
+        m = _abi.Model(kind, param)
+        o = _options(options)
+        npix = sum(c.height * c.width for c in cams)
+        images = torch.empty((npix, 3), dtype=torch.float32, device=self.device)
+        overdraw = torch.empty((npix,), dtype=torch.int32, device=self.device)
+        dl = grads = None
+        if backward:
+            dl = torch.ones_like(images)
+            gout = {"d_" + k: torch.empty_like(keep[k]) for k in PARAM_KEYS}
+            grads = _abi.Grads(*(gout["d_" + k].data_ptr() for k in PARAM_KEYS))
+        frame = frame or self.frame()
+        best = _abi.Options()
+        table = (_abi.TuneEntry * 32)()
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        rc = self.lib.ngs_autotune(self.ctx, frame.handle, C.byref(g), cams, len(cameras), C.byref(m), C.byref(o),
+                                   images.data_ptr(), overdraw.data_ptr(), dl.data_ptr() if backward else None,
+                                   C.byref(grads) if backward else None, int(reps), int(flush_bytes), C.byref(best),
+                                   table, 32, stream)
+        if rc < 0:
+            _abi.check(rc, self.ctx)
+        self.recycle(frame)
+        d = default_options(**(options or {}))
+        d.update(tile_w=best.tile_w, tile_h=best.tile_h, chunk=best.chunk, schedule=best.schedule)
+        rows = [(t.tile_w, t.tile_h, t.chunk, t.schedule, t.ms) for t in table[:rc]]
+        del keep
+        return d, rows
+
     def backward(self, frame: Frame, params: dict, dl_dimage: torch.Tensor, out: dict | None = None) -> dict:
         """Path-replay gradients of the frame's render w.r.t. the raw parameters (overwritten into ``out``)."""
         g, keep = _gaussians(params, self.device)

@@ -261,3 +261,17 @@ def test_graph_replay_bit_identical_and_reused(clustered):
     finally:
         direct.close()
         graphed.close()
+
+
+def test_autotune_returns_a_valid_fastest_configuration(rnd, clustered):
+    scene, cams = clustered
+    params = upload(scene)
+    best, table = rnd.autotune(params, cams, "sup", backward=True, reps=2)
+    assert len(table) == 18  # 3 tile shapes x 3 chunks x 2 schedules
+    assert {(t[0], t[1]) for t in table} == {(8, 8), (16, 16), (16, 32)}
+    assert all(t[4] > 0 for t in table)
+    fastest = min(table, key=lambda t: t[4])
+    assert (best["tile_w"], best["tile_h"], best["chunk"], best["schedule"]) == fastest[:4]
+    a = rnd.render_batch(params, cams, "sup")
+    b = rnd.render_batch(params, cams, "sup", options=best)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
