@@ -51,6 +51,12 @@ def parse():
     p.add_argument("--no-batched", action="store_true", help="skip the batched multi-view measurement")
     p.add_argument("--batched-gaussians", type=int, default=3_000_000)
     p.add_argument("--batched-views", type=int, default=32)
+    p.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    p.add_argument("--serving-requests", type=int, default=2000)
+    p.add_argument("--serving-rate", type=float, default=200.0)
+    p.add_argument("--serving-high-rate", type=float, default=1500.0,
+                   help="second arrival rate, between the capacities of the two forms")
+    p.add_argument("--serving-workers", type=int, default=4)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-crop", type=int, default=0, help="oracle crop side (0: sized automatically)")
@@ -278,9 +284,12 @@ def run_ours(args):
     }
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, r, scene, cam, opts, dl, dev, world)
-    if not args.no_batched and world == 1:
+    if world == 1 and not (args.no_batched and args.no_serving):
         del params, frames, grads
+    if not args.no_batched and world == 1:
         line["batched"] = run_batched(args, r, dev, line["per_model"])
+    if not args.no_serving and world == 1:
+        line["serving"] = run_serving(args, r, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, scene, cam)
     if rank == 0:
@@ -445,6 +454,61 @@ def run_batched(args, r, dev, single_view_models):
     r.recycle(fb)
     for f in fviews:
         f.release()
+    return out
+
+
+def run_serving(args, r, dev):
+    """The served form: four resident clustered scenes (0.5M, 1M, 2M, 3M Gaussians, SH 3); requests
+    arrive as a seeded Poisson process (default 2000 at 200 req/s), each with a random scene, model (the
+    four equally likely), pose on the sphere of radius 12 m and resolution (640x360 .. 1920x1080). The
+    library's server batches them as they arrive (same scene and model), on several workers, admitting by
+    sort-buffer memory. Against: the same arrivals served by one render call at a time. Also a
+    saturation run (all requests at t = 0) for the throughput ceiling of both forms."""
+    import torch
+
+    from paper_2603_02887_gb300 import synth
+    from paper_2603_02887_gb300.render import PARAM_KEYS, default_options
+    from paper_2603_02887_gb300.serve import Server, poisson_arrivals, run_one_at_a_time, run_poisson
+
+    sizes = (500_000, 1_000_000, 2_000_000, 3_000_000)
+    scenes = []
+    for i, n in enumerate(sizes):
+        sc = synth.clustered_scene(n, seed=10 + i, sh_degree=3)
+        scenes.append({k: torch.from_numpy(np.ascontiguousarray(sc[k])).to(dev) for k in PARAM_KEYS})
+        del sc
+    n_req = args.serving_requests
+    rng = np.random.default_rng(3)
+    cams = synth.orbit_cameras(n_req, radius=12.0, seed=3)
+    reqs = [(int(rng.integers(0, len(sizes))), cams[i], MODELS[int(rng.integers(0, len(MODELS)))])
+            for i in range(n_req)]
+    loads = {"poisson": poisson_arrivals(n_req, args.serving_rate, seed=3),
+             "poisson_high": poisson_arrivals(n_req, args.serving_high_rate, seed=3),
+             "saturation": np.zeros(n_req)}
+    opts = default_options(schedule="persistent")
+    out = {"scenes": list(sizes), "requests": n_req, "rate_req_s": args.serving_rate,
+           "high_rate_req_s": args.serving_high_rate, "arrivals": "Poisson, seed 3 (saturation: all at t = 0)",
+           "workers": args.serving_workers, "max_batch_views": 16, "mem_budget_bytes": 8 << 30,
+           "latency": "arrival to images on the device, stream synchronised",
+           "options": {k: opts[k] for k in ("tile_w", "tile_h", "chunk", "schedule")}}
+    warm = reqs[:64]
+    srv = Server(workers=args.serving_workers, max_batch_views=16, mem_budget=8 << 30, options=opts, device=dev)
+    for p in scenes:
+        srv.add_scene(p)
+    run_poisson(srv, warm, np.zeros(len(warm)))
+    out["server"] = {}
+    for name, arr in loads.items():
+        res = run_poisson(srv, reqs, arr)
+        res.pop("results")
+        out["server"][name] = res
+    st = srv.stats()
+    srv.close()
+    out["server"]["stats"] = {k: st[k] for k in ("batches", "max_batch_views", "over_budget_admissions",
+                                                 "peak_reserved_bytes")}
+    r.set_graphs(True)  # the one-at-a-time form replays its graphs (one frame per scene and size)
+    run_one_at_a_time(r, scenes, warm, np.zeros(len(warm)), options=opts)
+    out["one_at_a_time"] = {name: run_one_at_a_time(r, scenes, reqs, arr, options=opts) for name, arr in loads.items()}
+    out["saturation_speedup_vs_one_at_a_time"] = round(out["server"]["saturation"]["frames_per_s"] /
+                                                       out["one_at_a_time"]["saturation"]["frames_per_s"], 3)
     return out
 
 

@@ -254,6 +254,76 @@ NGS_API void ngs_reset_stage_times(ngs_ctx* ctx);
 /* Total number of kernel launches this context has issued (all stages). */
 NGS_API int64_t ngs_launch_count(const ngs_ctx* ctx);
 
+/* ---- render server ---------------------------------------------------------------------------------
+ * A request loop over scenes kept resident on the device. The paper has no counterpart: this is the
+ * serving form of the render call above.
+ *  - Workers: `workers` host threads, each with its own CUDA stream, context and frame, so batches of
+ *    different workers overlap on the device.
+ *  - Continuous batching: a free worker takes the oldest pending request together with every pending
+ *    request for the same scene and model (in arrival order, at most max_batch_views) and renders them as
+ *    one ngs_render_batch-style pass; requests that arrive while the GPU is busy join the next batch.
+ *    Each image equals ngs_render of that request alone, bit for bit.
+ *  - Admission by memory: a batch reserves its depth-sort buffer bytes (16 per splat record) before it
+ *    starts and its tile-sort bytes (16 per pair) once the exact pair count is known; it waits while the
+ *    reservations of the batches in flight would exceed mem_budget. The oldest batch in flight may always
+ *    proceed (counted in over_budget_admissions when that exceeds the budget), so one always progresses.
+ * Threading: submit, poll and get_stats may be called from any host thread. Requests reference caller-owned
+ * device memory (scene arrays, output images) that must stay valid until the request completes. */
+typedef struct ngs_server ngs_server;
+
+typedef struct {
+  int32_t workers;         /* 1..64 (default 4)                                                        */
+  int32_t max_batch_views; /* 1..4096 (default 16)                                                     */
+  int64_t mem_budget;      /* bytes of sort buffers all batches in flight may reserve (default 8 GiB)   */
+  int32_t graphs;          /* 1: workers capture/replay CUDA graphs of the render phases; 0 (default):  */
+                           /* direct launches (batch shapes vary, so replays rarely match a capture)   */
+  int32_t reserved;        /* 0                                                                         */
+  ngs_options options;     /* render options of every request (default: ngs_default_options)           */
+} ngs_server_config;
+
+typedef struct {
+  int32_t scene;        /* id returned by ngs_server_add_scene                                          */
+  ngs_model model;
+  ngs_camera camera;
+  float* image;         /* device [height][width][3], written when the request completes                */
+  int32_t* overdraw;    /* device [height][width] or NULL                                               */
+  int64_t tag;          /* the caller's identifier, returned in the completion                          */
+} ngs_request;
+
+typedef struct {
+  int64_t tag;
+  int32_t status;       /* NGS_OK or the error of its batch                                             */
+  int32_t batch_views;  /* number of requests in its batch                                              */
+  double submit_s;      /* server clock (seconds since creation): submission, batch start, completion   */
+  double start_s;       /* (images on the device and the stream synchronised)                           */
+  double done_s;
+  int64_t pairs;        /* (tile, splat) pairs of its batch                                             */
+} ngs_completion;
+
+typedef struct {
+  int64_t submitted, completed, batches, max_batch_views;
+  int64_t over_budget_admissions;
+  int64_t peak_reserved_bytes, reserved_bytes, pending;
+  double now_s;
+} ngs_server_stats;
+
+NGS_API void ngs_default_server_config(ngs_server_config* cfg);
+/* Starts the workers on the current device. Errors: NGS_ERR_INVALID_ARG for values out of range. */
+NGS_API int ngs_server_create(const ngs_server_config* cfg, ngs_server** out);
+/* Register a resident scene (the arrays are referenced, not copied); *id receives its id. */
+NGS_API int ngs_server_add_scene(ngs_server* server, const ngs_gaussians* g, int32_t* id);
+/* Queue a request; returns at once. A camera or model outside its documented range is refused here with
+ * NGS_ERR_INVALID_ARG (it never joins a batch); errors met while rendering are reported in the
+ * completions of the batch's requests. */
+NGS_API int ngs_server_submit(ngs_server* server, const ngs_request* request);
+/* Move up to `cap` completions to `out`, waiting up to wait_ms for the first; returns how many. */
+NGS_API int ngs_server_poll(ngs_server* server, ngs_completion* out, int32_t cap, int32_t wait_ms);
+NGS_API int ngs_server_get_stats(ngs_server* server, ngs_server_stats* out);
+/* The first error a batch met ("" if none). */
+NGS_API const char* ngs_server_last_error(ngs_server* server);
+/* Render every queued request, then stop the workers and free the server. */
+NGS_API void ngs_server_destroy(ngs_server* server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -61,6 +61,28 @@ class FrameView(C.Structure):
                 ("view_pixel_base", C.c_void_p), ("view_tile_base", C.c_void_p)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("workers", C.c_int32), ("max_batch_views", C.c_int32), ("mem_budget", C.c_int64),
+                ("graphs", C.c_int32), ("reserved", C.c_int32), ("options", Options)]
+
+
+class Request(C.Structure):
+    _fields_ = [("scene", C.c_int32), ("model", Model), ("camera", Camera), ("image", C.c_void_p),
+                ("overdraw", C.c_void_p), ("tag", C.c_int64)]
+
+
+class Completion(C.Structure):
+    _fields_ = [("tag", C.c_int64), ("status", C.c_int32), ("batch_views", C.c_int32), ("submit_s", C.c_double),
+                ("start_s", C.c_double), ("done_s", C.c_double), ("pairs", C.c_int64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("batches", C.c_int64),
+                ("max_batch_views", C.c_int64), ("over_budget_admissions", C.c_int64),
+                ("peak_reserved_bytes", C.c_int64), ("reserved_bytes", C.c_int64), ("pending", C.c_int64),
+                ("now_s", C.c_double)]
+
+
 #: every function declared in include/ngs.h, with its ctypes signature
 SIGNATURES = {
     "ngs_default_options": (None, [C.POINTER(Options)]),
@@ -88,6 +110,14 @@ SIGNATURES = {
     "ngs_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
     "ngs_reset_stage_times": (None, [C.c_void_p]),
     "ngs_launch_count": (C.c_int64, [C.c_void_p]),
+    "ngs_default_server_config": (None, [C.POINTER(ServerConfig)]),
+    "ngs_server_create": (C.c_int, [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]),
+    "ngs_server_add_scene": (C.c_int, [C.c_void_p, C.POINTER(Gaussians), C.POINTER(C.c_int32)]),
+    "ngs_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Request)]),
+    "ngs_server_poll": (C.c_int, [C.c_void_p, C.POINTER(Completion), C.c_int32, C.c_int32]),
+    "ngs_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "ngs_server_last_error": (C.c_char_p, [C.c_void_p]),
+    "ngs_server_destroy": (None, [C.c_void_p]),
 }
 
 _lib = None

@@ -12,7 +12,7 @@
 
 namespace ngs {
 
-int fail(ngs_ctx* ctx, int code, const std::string& msg) {
+int fail(ngs_ctx* ctx, int code, const std::string& msg) {  // ctx may be null
   if (ctx) ctx->err = msg;
   return code;
 }
@@ -97,7 +97,7 @@ using namespace ngs;
     if (_rc != NGS_OK) return _rc; \
   } while (0)
 
-static int check_camera(ngs_ctx* ctx, const ngs_camera* cam) {
+int ngs::check_camera(ngs_ctx* ctx, const ngs_camera* cam) {
   if (!cam) return fail(ctx, NGS_ERR_INVALID_ARG, "null camera");
   if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
     return fail(ctx, NGS_ERR_INVALID_ARG, "image size out of range 1..16384");
@@ -108,18 +108,24 @@ static int check_camera(ngs_ctx* ctx, const ngs_camera* cam) {
   return NGS_OK;
 }
 
-static int check_inputs(ngs_ctx* ctx, const ngs_gaussians* g, const ngs_model* model, const ngs_options* o) {
-  if (!g || !model || !o) return fail(ctx, NGS_ERR_INVALID_ARG, "null argument");
-  if (g->n < 0 || g->n >= (1ll << 31)) return fail(ctx, NGS_ERR_INVALID_ARG, "n out of range [0, 2^31)");
-  if (g->sh_degree < 0 || g->sh_degree > 3) return fail(ctx, NGS_ERR_INVALID_ARG, "sh_degree must be 0..3");
-  if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
-    return fail(ctx, NGS_ERR_INVALID_ARG, "null Gaussian parameter array");
+int ngs::check_model(ngs_ctx* ctx, const ngs_model* model) {
+  if (!model) return fail(ctx, NGS_ERR_INVALID_ARG, "null model");
   if (model->kind == NGS_MODEL_QUAD) {
     if (!(model->param >= -0.5f) || !isfinite(model->param))
       return fail(ctx, NGS_ERR_INVALID_ARG, "quadratic model needs c >= -0.5");
   } else if (model->kind != NGS_MODEL_EXP) {
     return fail(ctx, NGS_ERR_INVALID_ARG, "unknown transmittance model");
   }
+  return NGS_OK;
+}
+
+static int check_inputs(ngs_ctx* ctx, const ngs_gaussians* g, const ngs_model* model, const ngs_options* o) {
+  if (!g || !model || !o) return fail(ctx, NGS_ERR_INVALID_ARG, "null argument");
+  if (g->n < 0 || g->n >= (1ll << 31)) return fail(ctx, NGS_ERR_INVALID_ARG, "n out of range [0, 2^31)");
+  if (g->sh_degree < 0 || g->sh_degree > 3) return fail(ctx, NGS_ERR_INVALID_ARG, "sh_degree must be 0..3");
+  if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+    return fail(ctx, NGS_ERR_INVALID_ARG, "null Gaussian parameter array");
+  NGS_TRY(check_model(ctx, model));
   bool tile_ok = (o->tile_w == 8 && o->tile_h == 8) || (o->tile_w == 16 && o->tile_h == 16) ||
                  (o->tile_w == 16 && o->tile_h == 32);
   if (!tile_ok) return fail(ctx, NGS_ERR_INVALID_ARG, "tile shape must be 8x8, 16x16 or 16x32");
@@ -339,12 +345,31 @@ static int run_phase(ngs_ctx* ctx, ngs_frame* f, int which, const KeyBuf& key, c
 int ngs::render_views(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const ngs_camera* cams, int n_views,
                       const ngs_model* model, const ngs_options* o, float* image, int32_t* overdraw,
                       cudaStream_t s) {
-  if (!f || f->ctx != ctx) return fail(ctx, NGS_ERR_INVALID_ARG, "frame missing or from another context");
-  NGS_TRY(check_inputs(ctx, g, model, o));
   if (!cams) return fail(ctx, NGS_ERR_INVALID_ARG, "null camera");
   if (n_views < 1 || n_views > kMaxViews) return fail(ctx, NGS_ERR_INVALID_ARG, "n_views out of range 1..4096");
-  for (int v = 0; v < n_views; ++v) NGS_TRY(check_camera(ctx, &cams[v]));
   if (!image) return fail(ctx, NGS_ERR_INVALID_ARG, "null image");
+  std::vector<float*> images(n_views);
+  std::vector<int32_t*> ods(n_views);
+  uint64_t base = 0;
+  for (int v = 0; v < n_views; ++v) {  // the packed layout: view v after views 0..v-1
+    images[v] = image + 3 * base;
+    ods[v] = overdraw ? overdraw + base : nullptr;
+    base += (uint64_t)std::max(cams[v].width, 0) * (uint64_t)std::max(cams[v].height, 0);
+  }
+  return render_views_out(ctx, f, g, cams, n_views, model, o, images.data(), ods.data(), s);
+}
+
+int ngs::render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const ngs_camera* cams, int n_views,
+                          const ngs_model* model, const ngs_options* o, float* const* images,
+                          int32_t* const* overdraws, cudaStream_t s, AdmitFn admit, void* admit_user) {
+  if (!f || f->ctx != ctx) return fail(ctx, NGS_ERR_INVALID_ARG, "frame missing or from another context");
+  NGS_TRY(check_inputs(ctx, g, model, o));
+  if (!cams || !images) return fail(ctx, NGS_ERR_INVALID_ARG, "null camera or image array");
+  if (n_views < 1 || n_views > kMaxViews) return fail(ctx, NGS_ERR_INVALID_ARG, "n_views out of range 1..4096");
+  for (int v = 0; v < n_views; ++v) {
+    NGS_TRY(check_camera(ctx, &cams[v]));
+    if (!images[v]) return fail(ctx, NGS_ERR_INVALID_ARG, "null image");
+  }
   f->has_render = false;
 
   // views, packed: tiles and pixels of view v follow those of views 0..v-1
@@ -360,6 +385,8 @@ int ngs::render_views(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const 
     vp.tiles_y = (cams[v].height + o->tile_h - 1) / o->tile_h;
     vp.tile_base = (uint32_t)tiles_total;
     vp.pix_base = pix_total;
+    vp.image = images[v];
+    vp.overdraw = overdraws ? overdraws[v] : nullptr;
     f->tile_base[v] = (uint32_t)tiles_total;
     f->pix_base[v] = (int64_t)pix_total;
     tiles_total += (uint64_t)vp.tiles_x * vp.tiles_y;
@@ -404,8 +431,8 @@ int ngs::render_views(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const 
   pl.R = rp.n_records;
   pl.ntiles = rp.n_tiles;
   pl.pix_total = pix_total;
-  pl.image = image;
-  pl.overdraw = overdraw;
+  pl.image = images[0];
+  pl.overdraw = overdraws ? overdraws[0] : nullptr;
   const uint32_t R = pl.R;
 
   // phase 1 buffers
@@ -430,6 +457,7 @@ int ngs::render_views(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const 
     NGS_TRY(ensure(ctx, f->sched, sizeof(uint32_t) * kSchedWords));
   }
   NGS_TRY(stage_views(ctx, f));
+  if (admit) NGS_TRY(admit(admit_user, 0, sizeof(uint32_t) * 4 * (size_t)R));
 
   KeyBuf k1;
   k1.add(*g);
@@ -458,6 +486,7 @@ int ngs::render_views(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const 
   const uint64_t P = *ctx->h_total;
   if (P >= (1ull << 31)) return fail(ctx, NGS_ERR_INVALID_ARG, "more than 2^31 (tile, Gaussian) pairs");
   const uint32_t np = (uint32_t)P;
+  if (admit) NGS_TRY(admit(admit_user, 1, sizeof(uint32_t) * 4 * (size_t)np));
 
   // phase 2: exact sizes, or, for graph replays, a capacity that a replay reuses while the count fits
   uint32_t cap = np;
@@ -477,8 +506,8 @@ int ngs::render_views(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const 
   k2.add(cap);
   k2.add(np_dev);
   k2.add(f->g_final);
-  k2.add(image);
-  k2.add(overdraw);
+  k2.add(n_views == 1 ? pl.image : nullptr);  // a batch reads its outputs from the view table
+  k2.add(n_views == 1 ? pl.overdraw : nullptr);
   k2.add(ctx->num_sms);
   for (const DevBuf* b : {&f->rec, &f->gvals[0], &f->gvals[1], &f->offsets, &f->views, &f->ptile[0], &f->ptile[1],
                           &f->pvals[0], &f->pvals[1], &ctx->hist, &f->ranges, &f->work, &f->sched, &f->state})

@@ -113,7 +113,7 @@ __device__ __forceinline__ void forward_tile(const float4* __restrict__ rec, con
                                              uint32_t tile, StageBuf<CH>& sb) {
   using G = TileGeom<TW, TH, 1>;
   constexpr int B = G::kThreads;
-  const TileView tv = tile_view(rp, views, (uint32_t)tile);
+  const TileView tv = tile_view(rp, views, (uint32_t)tile, image, overdraw);
   const int W = tv.W, H = tv.H;
   const int tx = tv.local % tv.tiles_x, ty = tv.local / tv.tiles_x;
   int tid = threadIdx.x;
@@ -193,13 +193,14 @@ __device__ __forceinline__ void forward_tile(const float4* __restrict__ rec, con
     }
   }
   if (!inside) return;  // (the caller's next barrier is reached by every thread)
-  size_t pix = tv.pix_base + (size_t)y * W + x;
+  const size_t lpix = (size_t)y * W + x;  // pixel within the view
+  const size_t pix = tv.pix_base + lpix;  // packed pixel of the replay state
   float Tend = KIND == NGS_MODEL_QUAD ? (saturated ? 0.f : 1.f - S) : T;
   float L0 = C0 + rp.bg[0] * Tend, L1 = C1 + rp.bg[1] * Tend, L2 = C2 + rp.bg[2] * Tend;
-  image[3 * pix] = L0;
-  image[3 * pix + 1] = L1;
-  image[3 * pix + 2] = L2;
-  if (overdraw) overdraw[pix] = od;
+  tv.image[3 * lpix] = L0;
+  tv.image[3 * lpix + 1] = L1;
+  tv.image[3 * lpix + 2] = L2;
+  if (tv.overdraw) tv.overdraw[lpix] = od;
   uint32_t nbits = stop | (saturated ? 0x80000000u : 0u);
   if (KIND == NGS_MODEL_QUAD) {
     state[2 * pix] = make_float4(__uint_as_float(nbits), Ek0, Ek1, Ek2);

@@ -23,13 +23,16 @@ struct CamParams {
 
 // One view of a batch (a device array of these per frame). Views are packed one after the other: view v's
 // splat records are records [v n, (v + 1) n), its tiles have the global indices [tile_base, tile_base +
-// tiles_x tiles_y) and its pixels the packed-image indices [pix_base, pix_base + W H).
+// tiles_x tiles_y) and its pixels the packed indices [pix_base, pix_base + W H) of the replay state. Its
+// image and overdraw map are written to `image` / `overdraw` (row-major [H][W][3] / [H][W]).
 struct ViewParams {
   CamParams cam;
   int tiles_x, tiles_y;
   uint32_t tile_base;
   uint32_t pad;
   uint64_t pix_base;
+  float* image;
+  int32_t* overdraw;  // may be null
 };
 
 struct RenderParams {
@@ -60,13 +63,15 @@ constexpr uint32_t kCheckIndex = 1u;  // a sorted pair named a splat record inde
 // dependent load before the tile's work starts); a batch looks it up in the view table.
 struct TileView {
   int W, H, tiles_x, local;  // image size, tiles per row, tile index within the view
-  size_t pix_base;           // first packed pixel of the view
+  size_t pix_base;           // first packed pixel of the view (replay state)
+  float* image;              // the view's outputs
+  int32_t* overdraw;
 };
 
 __device__ __forceinline__ int view_of_tile(const ViewParams* __restrict__ views, int n_views, uint32_t t);
 
 __device__ __forceinline__ TileView tile_view(const RenderParams& rp, const ViewParams* __restrict__ views,
-                                              uint32_t t) {
+                                              uint32_t t, float* image0 = nullptr, int32_t* overdraw0 = nullptr) {
   TileView tv;
   if (rp.n_views == 1) {
     tv.W = rp.width;
@@ -74,6 +79,8 @@ __device__ __forceinline__ TileView tile_view(const RenderParams& rp, const View
     tv.tiles_x = rp.tiles_x;
     tv.local = (int)t;
     tv.pix_base = 0;
+    tv.image = image0;
+    tv.overdraw = overdraw0;
   } else {
     const int v = view_of_tile(views, (int)rp.n_views, t);
     tv.W = __ldg(&views[v].cam.W);
@@ -81,6 +88,8 @@ __device__ __forceinline__ TileView tile_view(const RenderParams& rp, const View
     tv.tiles_x = __ldg(&views[v].tiles_x);
     tv.local = (int)(t - __ldg(&views[v].tile_base));
     tv.pix_base = (size_t)__ldg(reinterpret_cast<const unsigned long long*>(&views[v].pix_base));
+    tv.image = reinterpret_cast<float*>(__ldg(reinterpret_cast<const unsigned long long*>(&views[v].image)));
+    tv.overdraw = reinterpret_cast<int32_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&views[v].overdraw)));
   }
   return tv;
 }
@@ -212,11 +221,24 @@ struct ngs_frame {
 
 namespace ngs {
 
-// the render and backward pipelines (api.cu), also used by the autotuner
+// the render and backward pipelines (api.cu), also used by the autotuner and the server
 int render_views(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const ngs_camera* cams, int n_views,
                  const ngs_model* model, const ngs_options* o, float* image, int32_t* overdraw, cudaStream_t s);
+// Admission of a render's sort buffers: called with stage 0 and the depth-sort bytes before phase 1, and
+// with stage 1 and the pair-sort bytes once the exact pair count is known; anything but NGS_OK stops the
+// render with that status.
+typedef int (*AdmitFn)(void* user, int stage, size_t bytes);
+// The same pipeline writing view v's image / overdraw map to images[v] / overdraws[v] ([H][W][3] / [H][W];
+// overdraws may be null, or hold nulls).
+int render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const ngs_camera* cams, int n_views,
+                     const ngs_model* model, const ngs_options* o, float* const* images, int32_t* const* overdraws,
+                     cudaStream_t s, AdmitFn admit = nullptr, void* admit_user = nullptr);
 int backward_frame(ngs_ctx* ctx, const ngs_frame* f, const ngs_gaussians* g, const float* dl_dimage,
                    const ngs_grads* out, cudaStream_t s);
+
+// argument checks (api.cu); ctx may be null (no message is kept then)
+int check_camera(ngs_ctx* ctx, const ngs_camera* cam);
+int check_model(ngs_ctx* ctx, const ngs_model* model);
 
 // error / allocation helpers (api.cu)
 int fail(ngs_ctx* ctx, int code, const std::string& msg);
