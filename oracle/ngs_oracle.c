@@ -121,6 +121,7 @@ typedef struct {
   double T_end;     /* Tbar after the composited entries */
   double margin;    /* smallest relative distance of a stop decision to its threshold */
   int clamp_fired;  /* the [.]_+ clamp of a quadratic slope term was active */
+  int k_lin, k_exp; /* Vicini: entry where its linear list saturated / its exponential list stopped (-1: none) */
 } comp_result;
 
 static void margin_update(double* margin, double value, double threshold) {
@@ -187,6 +188,7 @@ static void composite(int kind, double param, double t_eps, int max_splats, cons
   } else { /* ORC_VICINI: lerp of the saturated linear list and the exponential list */
     double gam = param, Sl = 0.0, Te = 1.0;
     int sat_l = 0, stop_e = 0, m = 0;
+    r->k_lin = r->k_exp = -1;
     for (int i = 0; i < n; ++i) {
       if (max_splats > 0 && m == max_splats) break;
       double pe = 0.0, pl = 0.0;
@@ -194,14 +196,14 @@ static void composite(int kind, double param, double t_eps, int max_splats, cons
         double testT = Te * (1.0 - alpha[i]);
         if (t_eps > 0) {
           margin_update(&r->margin, testT, t_eps);
-          if (testT < t_eps) stop_e = 1;
+          if (testT < t_eps) { stop_e = 1; r->k_exp = i; }
         }
         if (!stop_e) { pe = alpha[i] * Te; Te = testT; }
       }
       if (sat_l && stop_e) break;
       if (!sat_l) {
         margin_update(&r->margin, Sl + alpha[i], 1.0);
-        if (Sl + alpha[i] >= 1.0) { pl = 1.0 - Sl; Sl = 1.0; sat_l = 1; }
+        if (Sl + alpha[i] >= 1.0) { pl = 1.0 - Sl; Sl = 1.0; sat_l = 1; r->k_lin = i; }
         else { pl = alpha[i]; Sl += alpha[i]; }
       }
       pbar[i] = (1.0 - gam) * pl + gam * pe;
@@ -533,6 +535,7 @@ static void* render_rows(void* argp) {
         uint64_t h = 1469598103934665603ULL;
         for (int i = 0; i < r.m; ++i) h = fnv(h, (uint64_t)J->gid[L[i].g] * 4 + (uint64_t)(L[i].clamped == 1));
         h = fnv(h, (uint64_t)r.m * 2 + (uint64_t)r.saturated);
+        if (kind == ORC_VICINI) h = fnv(h, ((uint64_t)(r.k_lin + 1) << 32) | (uint64_t)(r.k_exp + 1));
         J->fwd->signature[pix] = h;
       }
       if (grec) {

@@ -193,7 +193,7 @@ def test_exponential_pixels_are_textbook_alpha_blending(orc):
         assert img["overdraw"][y, x] == len(keep)
 
 
-@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("model", MODELS + [(2, 0.5), (3, 0.5)])
 def test_render_gradient_matches_finite_differences(orc, model):
     """Gradients of L = sum(g * image) w.r.t. raw parameters (mean, log-scale, quaternion, opacity logit,
     SH) against central differences of the FP64 render, on a reduced tiny scene. A sample is redrawn if
