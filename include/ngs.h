@@ -47,6 +47,11 @@ extern "C" {
 #define NGS_MODEL_EXP 0  /* T = exp(-tau): pbar_i = alpha_i prod_{j<i}(1 - alpha_j) (standard 3DGS)      */
 #define NGS_MODEL_QUAD 1 /* T = [1 - tau - c/2 tau^2]_+: pbar_i = alpha_i (1 + c taubar_i); param = c,    */
                          /* c >= -1/2. c = -1/2 sub-linear, c = 0 linear, c = +1/2 super-linear (Sec. 5)  */
+#define NGS_MODEL_BLEND 2  /* T = [lerp(1 - tau, exp(-tau), g)]_+: pbar_i = alpha_i (1 - g + g P_i),        */
+                           /* P_i = prod_{j<i}(1 - alpha_j); param = g in [0, 1]                          */
+#define NGS_MODEL_VICINI 3 /* T = lerp([1 - tau]_+, exp(-tau), g): pbar_i = lerp(pbar_i^lin, pbar_i^exp, g), */
+                           /* each list with its own stop (linear: saturation; exponential: t_eps);       */
+                           /* the ray stops when both have; param = g in [0, 1]                           */
 
 typedef struct ngs_ctx ngs_ctx;
 typedef struct ngs_frame ngs_frame;
@@ -76,8 +81,8 @@ typedef struct {
 } ngs_camera;
 
 typedef struct {
-  int32_t kind; /* NGS_MODEL_EXP or NGS_MODEL_QUAD                                                    */
-  float param;  /* c for NGS_MODEL_QUAD (>= -0.5); ignored for NGS_MODEL_EXP                          */
+  int32_t kind; /* NGS_MODEL_EXP, _QUAD, _BLEND or _VICINI (Table 1)                                   */
+  float param;  /* c for NGS_MODEL_QUAD (>= -0.5), g for _BLEND / _VICINI (0..1); ignored for _EXP      */
 } ngs_model;
 
 /* Rendering options. ngs_default_options() fills the values below, which are the conventions of the

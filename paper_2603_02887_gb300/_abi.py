@@ -16,6 +16,8 @@ NGS_ERR_CUDA = -3
 NGS_ERR_DEVICE_CHECK = -5
 NGS_MODEL_EXP = 0
 NGS_MODEL_QUAD = 1
+NGS_MODEL_BLEND = 2
+NGS_MODEL_VICINI = 3
 NGS_SCHEDULE_TILES = 0
 NGS_SCHEDULE_PERSISTENT = 1
 NGS_NUM_STAGES = 8

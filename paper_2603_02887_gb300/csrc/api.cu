@@ -113,6 +113,9 @@ int ngs::check_model(ngs_ctx* ctx, const ngs_model* model) {
   if (model->kind == NGS_MODEL_QUAD) {
     if (!(model->param >= -0.5f) || !isfinite(model->param))
       return fail(ctx, NGS_ERR_INVALID_ARG, "quadratic model needs c >= -0.5");
+  } else if (model->kind == NGS_MODEL_BLEND || model->kind == NGS_MODEL_VICINI) {
+    if (!(model->param >= 0.f && model->param <= 1.f))
+      return fail(ctx, NGS_ERR_INVALID_ARG, "blended / Vicini model needs gamma in [0, 1]");
   } else if (model->kind != NGS_MODEL_EXP) {
     return fail(ctx, NGS_ERR_INVALID_ARG, "unknown transmittance model");
   }
@@ -408,7 +411,8 @@ int ngs::render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, co
   rp.near_plane = o->near_plane;
   rp.log2_alpha_min = log2f(o->alpha_min);
   for (int c = 0; c < 3; ++c) rp.bg[c] = o->background[c];
-  rp.c = model->kind == NGS_MODEL_QUAD ? model->param : 0.f;
+  rp.c = model->kind == NGS_MODEL_EXP ? 0.f : model->param;
+  rp.c1 = 1.0f - rp.c;
   rp.kind = model->kind;
   rp.tile_w = o->tile_w;
   rp.tile_h = o->tile_h;

@@ -10,7 +10,10 @@
 //   alpha_i = min(alpha_max, aleph_i K_i(p)), skipped when alpha_i < alpha_min;
 //   quadratic:   pt = [alpha_i (1 + c taubar_i)]_+; if S + pt >= 1 the splat is k: pbar_k = 1 - S, the
 //                ray has saturated and stops; else pbar_i = pt, S += pt, taubar += alpha_i;
-//   exponential: stop before the splat that would take T below t_eps; pbar_i = alpha_i T, T *= 1 - alpha_i.
+//   exponential: stop before the splat that would take T below t_eps; pbar_i = alpha_i T, T *= 1 - alpha_i;
+//   blended:     as quadratic with pt = alpha_i (1 - g + g P_i), P_i = prod_{j<i}(1 - alpha_j);
+//   Vicini:      pbar_i = (1 - g) pbar_i^lin + g pbar_i^exp, the linear list saturating and the exponential
+//                list stopping on their own; the ray stops once both have.
 // A warp whose 32 pixels have all stopped leaves the chunk loop (ballot), and the CTA leaves the tile once
 // every pixel has stopped (__syncthreads_count), which is where the faster-than-exponential models win.
 //
@@ -19,6 +22,9 @@
 //                Theta_{-1} = A - E_k taubar_k (A = sum_{i<k} E_i alpha_i saved by the forward pass);
 //                dL0/dE_i = pbar_i; dL0/dalpha_k = 0;
 //   exponential: dL0/dalpha_i = T_i E_i - R_i / (1 - alpha_i), R_i = L0 - sum_{j<=i} E_j pbar_j;
+//   blended:     dL0/dalpha_i = DeltaE_i (1 - g + g P_i) - g (B - B_i) / (1 - alpha_i), B_i the prefix sums
+//                of DeltaE_l alpha_l P_l and B their total (saved by the forward pass);
+//   Vicini:      (1 - g) x the linear adjoint + g x the exponential adjoint, each over its own list;
 // then w = dL/d(log2 alpha) and its moments w, w dx, w dy, w dx^2, w dx dy, w dy^2 (which determine the
 // gradient of the splat record, see the projection backward) and dL/dE, reduced over the warp's pixels with
 // shuffles and added to the per-Gaussian buffer with one atomic-add instruction per warp and splat.
@@ -113,7 +119,7 @@ __device__ __forceinline__ void forward_tile(const float4* __restrict__ rec, con
                                              uint32_t tile, StageBuf<CH>& sb) {
   using G = TileGeom<TW, TH, 1>;
   constexpr int B = G::kThreads;
-  const TileView tv = tile_view(rp, views, (uint32_t)tile, image, overdraw);
+  const TileView tv = tile_view(rp, views, (uint32_t)tile);
   const int W = tv.W, H = tv.H;
   const int tx = tv.local % tv.tiles_x, ty = tv.local / tv.tiles_x;
   int tid = threadIdx.x;
@@ -125,12 +131,15 @@ __device__ __forceinline__ void forward_tile(const float4* __restrict__ rec, con
   bool done = !inside;
   int od = 0;
   uint32_t stop = range.y - range.x;  // entries walked (n of the replay state)
-  bool saturated = false;
-  float C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  // quadratic state
+  bool saturated = false;  // quadratic / blended: the ray saturated; Vicini: its linear list did
+  float C0 = 0.f, C1 = 0.f, C2 = 0.f;  // Vicini: the linear list's sum
+  // quadratic (A = sum E alpha, tau) and blended (A = sum E alpha P, X = sum alpha P, P) state
   float S = 0.f, tau = 0.f, A0 = 0.f, A1 = 0.f, A2 = 0.f, Ek0 = rp.bg[0], Ek1 = rp.bg[1], Ek2 = rp.bg[2];
-  // exponential state
+  float P = 1.f, X = 0.f;
+  // exponential state (Vicini: its exponential list, with its own colour sum)
   float T = 1.f;
+  bool stop_e = false;
+  float Ce0 = 0.f, Ce1 = 0.f, Ce2 = 0.f;
   const float amax = rp.alpha_max, l2min = rp.log2_alpha_min, c = rp.c;
   for (uint32_t base = range.x; base < range.y; base += CH) {
     if (__syncthreads_count(done) == B) break;
@@ -145,11 +154,11 @@ __device__ __forceinline__ void forward_tile(const float4* __restrict__ rec, con
         if (e < l2min) continue;
         float alpha = fminf(amax, fast_exp2(e));
         float E0 = r1.z, E1 = r1.w, E2 = sb.e2[j];
-        if (KIND == NGS_MODEL_QUAD) {
-          float pt = quad_slope(alpha, c, tau);
+        if constexpr (KIND == NGS_MODEL_QUAD || KIND == NGS_MODEL_BLEND) {
+          const float pt = KIND == NGS_MODEL_QUAD ? quad_slope(alpha, c, tau) : blend_slope(alpha, c, rp.c1, P);
           float Sn = __fadd_rn(S, pt);
           ++od;
-          if (Sn >= 1.0f) {
+          if (Sn >= 1.0f) {  // the saturating splat k: pbar_k = 1 - S (Eq. nexp_p)
             float pk = 1.0f - S;
             C0 = fmaf(E0, pk, C0);
             C1 = fmaf(E1, pk, C1);
@@ -165,11 +174,61 @@ __device__ __forceinline__ void forward_tile(const float4* __restrict__ rec, con
           C0 = fmaf(E0, pt, C0);
           C1 = fmaf(E1, pt, C1);
           C2 = fmaf(E2, pt, C2);
-          A0 = fmaf(E0, alpha, A0);
-          A1 = fmaf(E1, alpha, A1);
-          A2 = fmaf(E2, alpha, A2);
+          const float w = KIND == NGS_MODEL_QUAD ? alpha : __fmul_rn(alpha, P);
+          A0 = fmaf(E0, w, A0);
+          A1 = fmaf(E1, w, A1);
+          A2 = fmaf(E2, w, A2);
           S = Sn;
-          tau = __fadd_rn(tau, alpha);
+          if (KIND == NGS_MODEL_QUAD) {
+            tau = __fadd_rn(tau, alpha);
+          } else {
+            X = __fadd_rn(X, w);
+            P = __fmul_rn(P, __fsub_rn(1.0f, alpha));
+          }
+        } else if constexpr (KIND == NGS_MODEL_VICINI) {
+          // the exponential list (own t_eps stop) and the linear list (own saturation), lerped by gamma
+          float pe = 0.f;
+          if (!stop_e) {
+            const float testT = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+            if (testT < rp.t_eps) {
+              stop_e = true;
+            } else {
+              pe = alpha * T;
+              T = testT;
+            }
+          }
+          if (saturated && stop_e) {  // both lists have stopped before this splat
+            done = true;
+            stop = base + j - range.x;
+            break;
+          }
+          float pl = 0.f;
+          if (!saturated) {
+            const float Sn = __fadd_rn(S, alpha);
+            if (Sn >= 1.0f) {
+              pl = 1.0f - S;
+              S = 1.0f;
+              saturated = true;
+              Ek0 = E0;
+              Ek1 = E1;
+              Ek2 = E2;
+            } else {
+              pl = alpha;
+              S = Sn;
+            }
+          }
+          C0 = fmaf(E0, pl, C0);
+          C1 = fmaf(E1, pl, C1);
+          C2 = fmaf(E2, pl, C2);
+          Ce0 = fmaf(E0, pe, Ce0);
+          Ce1 = fmaf(E1, pe, Ce1);
+          Ce2 = fmaf(E2, pe, Ce2);
+          ++od;
+          if (saturated && stop_e) {
+            done = true;
+            stop = base + j + 1 - range.x;
+            break;
+          }
         } else {
           float testT = __fmul_rn(T, __fsub_rn(1.0f, alpha));
           if (testT < rp.t_eps) {
@@ -193,18 +252,36 @@ __device__ __forceinline__ void forward_tile(const float4* __restrict__ rec, con
     }
   }
   if (!inside) return;  // (the caller's next barrier is reached by every thread)
-  const size_t lpix = (size_t)y * W + x;  // pixel within the view
-  const size_t pix = tv.pix_base + lpix;  // packed pixel of the replay state
-  float Tend = KIND == NGS_MODEL_QUAD ? (saturated ? 0.f : 1.f - S) : T;
-  float L0 = C0 + rp.bg[0] * Tend, L1 = C1 + rp.bg[1] * Tend, L2 = C2 + rp.bg[2] * Tend;
-  tv.image[3 * lpix] = L0;
-  tv.image[3 * lpix + 1] = L1;
-  tv.image[3 * lpix + 2] = L2;
-  if (tv.overdraw) tv.overdraw[lpix] = od;
+  const size_t lpix = (size_t)y * W + x;                         // pixel within the view
+  const size_t pix = view_pix_base(rp, views, tv.view) + lpix;  // packed pixel of the replay state
+  float* const out_image = view_image(rp, views, tv.view, image);
+  int32_t* const out_overdraw = view_overdraw(rp, views, tv.view, overdraw);
+  float L0, L1, L2, Tend;
+  if constexpr (KIND == NGS_MODEL_VICINI) {
+    Tend = fmaf(rp.c1, 1.0f - S, c * T);  // lerp(1 - S, T_exp, gamma)
+    L0 = fmaf(rp.c1, C0, fmaf(c, Ce0, rp.bg[0] * Tend));
+    L1 = fmaf(rp.c1, C1, fmaf(c, Ce1, rp.bg[1] * Tend));
+    L2 = fmaf(rp.c1, C2, fmaf(c, Ce2, rp.bg[2] * Tend));
+  } else {
+    Tend = KIND == NGS_MODEL_EXP ? T : (saturated ? 0.f : 1.f - S);
+    L0 = C0 + rp.bg[0] * Tend;
+    L1 = C1 + rp.bg[1] * Tend;
+    L2 = C2 + rp.bg[2] * Tend;
+  }
+  out_image[3 * lpix] = L0;
+  out_image[3 * lpix + 1] = L1;
+  out_image[3 * lpix + 2] = L2;
+  if (out_overdraw) out_overdraw[lpix] = od;
   uint32_t nbits = stop | (saturated ? 0x80000000u : 0u);
-  if (KIND == NGS_MODEL_QUAD) {
+  if constexpr (KIND == NGS_MODEL_QUAD) {
     state[2 * pix] = make_float4(__uint_as_float(nbits), Ek0, Ek1, Ek2);
     state[2 * pix + 1] = make_float4(A0, A1, A2, tau);
+  } else if constexpr (KIND == NGS_MODEL_BLEND) {
+    state[2 * pix] = make_float4(__uint_as_float(nbits), Ek0, Ek1, Ek2);
+    state[2 * pix + 1] = make_float4(A0, A1, A2, X);
+  } else if constexpr (KIND == NGS_MODEL_VICINI) {
+    state[2 * pix] = make_float4(__uint_as_float(nbits), Ek0, Ek1, Ek2);
+    state[2 * pix + 1] = make_float4(fmaf(rp.bg[0], T, Ce0), fmaf(rp.bg[1], T, Ce1), fmaf(rp.bg[2], T, Ce2), 0.f);
   } else {
     state[2 * pix] = make_float4(__uint_as_float(nbits), L0, L1, L2);
     state[2 * pix + 1] = make_float4(Tend, 0.f, 0.f, 0.f);
@@ -240,8 +317,10 @@ struct BwdPixel {
   float px, py;
   uint32_t last;        // replay entries [range.x, last)
   float g0, g1, g2;
-  float gEk, gTh, gL0;  // quadratic: g.E_k, g.Theta; exponential: g.L0
+  float gEk, gTh, gL0;  // quadratic: g.E_k, g.Theta; exponential: g.L0; Vicini: both lists' (gEk, gL0)
   float S, tau, T, gacc;
+  float P, gB, gBi;     // blended: prod (1 - alpha), g.B and its running prefix
+  bool sat, stop_e;     // Vicini: the linear list saturated / the exponential list stopped
 };
 
 // Sum nine per-lane values over the warp and add the totals to dst[0..8] with one atomic instruction.
@@ -292,7 +371,52 @@ __device__ __forceinline__ bool bwd_step(BwdPixel& p, float4 r0, float4 r1, cons
   float E0 = r1.z, E1 = r1.w, E2 = e2;
   float gE = fmaf(p.g2, E2, fmaf(p.g1, E1, p.g0 * E0));  // g.E_i
   float dLda, wE;
-  if (KIND == NGS_MODEL_QUAD) {
+  if constexpr (KIND == NGS_MODEL_BLEND) {
+    // L0 = sum_{i<k} DeltaE_i alpha_i (1 - g + g P_i) + E_k; with B = sum_{l<k} DeltaE_l alpha_l P_l and its
+    // prefix B_i = sum_{l<=i}: dL0/dalpha_i = DeltaE_i (1 - g + g P_i) - g (B - B_i) / (1 - alpha_i)
+    const float pt = blend_slope(alpha, rp.c, rp.c1, p.P);
+    const float Sn = __fadd_rn(p.S, pt);
+    if (Sn >= 1.0f) {
+      wE = 1.0f - p.S;
+      dLda = 0.f;
+    } else {
+      const float gd = gE - p.gEk;
+      p.gBi = fmaf(gd, __fmul_rn(alpha, p.P), p.gBi);
+      dLda = fmaf(gd, __fmaf_rn(rp.c, p.P, rp.c1), -rp.c * (p.gB - p.gBi) * __frcp_rn(1.0f - alpha));
+      wE = pt;
+      p.S = Sn;
+      p.P = __fmul_rn(p.P, __fsub_rn(1.0f, alpha));
+    }
+  } else if constexpr (KIND == NGS_MODEL_VICINI) {
+    // (1 - g) x the linear list's adjoint + g x the exponential list's, each up to its own stop
+    float pe = 0.f, dexp = 0.f;
+    if (!p.stop_e) {
+      const float testT = __fmul_rn(p.T, __fsub_rn(1.0f, alpha));
+      if (testT < rp.t_eps) {
+        p.stop_e = true;
+      } else {
+        pe = alpha * p.T;
+        p.gacc = fmaf(gE, pe, p.gacc);
+        dexp = fmaf(p.T, gE, -__frcp_rn(1.0f - alpha) * (p.gL0 - p.gacc));
+        p.T = testT;
+      }
+    }
+    float pl = 0.f, dlin = 0.f;
+    if (!p.sat) {
+      const float Sn = __fadd_rn(p.S, alpha);
+      if (Sn >= 1.0f) {
+        pl = 1.0f - p.S;
+        p.S = 1.0f;
+        p.sat = true;
+      } else {
+        pl = alpha;
+        p.S = Sn;
+        dlin = gE - p.gEk;
+      }
+    }
+    dLda = fmaf(rp.c1, dlin, rp.c * dexp);
+    wE = fmaf(rp.c1, pl, rp.c * pe);
+  } else if constexpr (KIND == NGS_MODEL_QUAD) {
     float pt = quad_slope(alpha, rp.c, p.tau);
     float Sn = __fadd_rn(p.S, pt);
     if (Sn >= 1.0f) {  // the saturating splat k: pbar_k = 1 - S, no dependence on alpha_k
@@ -344,7 +468,7 @@ __device__ __forceinline__ void backward_tile(const float4* __restrict__ rec, co
   static_assert(kBwdPix == 2, "the replay below is written for two pixels per thread");
   const TileView tv = tile_view(rp, views, (uint32_t)tile);
   const int W = tv.W, H = tv.H;
-  const size_t pix_base = tv.pix_base;
+  const size_t pix_base = view_pix_base(rp, views, tv.view);
   const int tx = tv.local % tv.tiles_x, ty = tv.local / tv.tiles_x;
   const int tid = threadIdx.x, lane = tid & 31;
   const uint2 range = ranges[tile];
@@ -363,6 +487,9 @@ __device__ __forceinline__ void backward_tile(const float4* __restrict__ rec, co
     q.gEk = q.gTh = q.gL0 = 0.f;
     q.S = q.tau = q.gacc = 0.f;
     q.T = 1.f;
+    q.P = 1.f;
+    q.gB = q.gBi = 0.f;
+    q.sat = q.stop_e = false;
     if (x < W && y < H) {
       size_t pix = pix_base + (size_t)y * W + x;
       float4 s0 = state[2 * pix], s1 = state[2 * pix + 1];
@@ -370,10 +497,17 @@ __device__ __forceinline__ void backward_tile(const float4* __restrict__ rec, co
       q.g0 = dl_dimage[3 * pix];
       q.g1 = dl_dimage[3 * pix + 1];
       q.g2 = dl_dimage[3 * pix + 2];
-      if (KIND == NGS_MODEL_QUAD) {
+      if constexpr (KIND == NGS_MODEL_QUAD) {
         q.gEk = q.g0 * s0.y + q.g1 * s0.z + q.g2 * s0.w;
         // Theta_{-1} = A - E_k taubar_k
         q.gTh = q.g0 * (s1.x - s0.y * s1.w) + q.g1 * (s1.y - s0.z * s1.w) + q.g2 * (s1.z - s0.w * s1.w);
+      } else if constexpr (KIND == NGS_MODEL_BLEND) {
+        q.gEk = q.g0 * s0.y + q.g1 * s0.z + q.g2 * s0.w;
+        // B = sum_{l<k} E_l alpha_l P_l - E_k sum_{l<k} alpha_l P_l
+        q.gB = q.g0 * s1.x + q.g1 * s1.y + q.g2 * s1.z - q.gEk * s1.w;
+      } else if constexpr (KIND == NGS_MODEL_VICINI) {
+        q.gEk = q.g0 * s0.y + q.g1 * s0.z + q.g2 * s0.w;  // E_k of the linear list
+        q.gL0 = q.g0 * s1.x + q.g1 * s1.y + q.g2 * s1.z;  // L0 of the exponential list
       } else {
         q.gL0 = q.g0 * s0.y + q.g1 * s0.z + q.g2 * s0.w;
       }
@@ -501,20 +635,38 @@ template <int TW, int TH>
 void forward_kind(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
                   const ViewParams* views, float* image, int32_t* overdraw, float4* state, const Launch& L,
                   cudaStream_t s) {
-  if (rp.kind == NGS_MODEL_QUAD)
-    forward_chunk<TW, TH, NGS_MODEL_QUAD>(rec, ids, ranges, rp, views, image, overdraw, state, L, s);
-  else
-    forward_chunk<TW, TH, NGS_MODEL_EXP>(rec, ids, ranges, rp, views, image, overdraw, state, L, s);
+  switch (rp.kind) {
+    case NGS_MODEL_QUAD:
+      forward_chunk<TW, TH, NGS_MODEL_QUAD>(rec, ids, ranges, rp, views, image, overdraw, state, L, s);
+      break;
+    case NGS_MODEL_BLEND:
+      forward_chunk<TW, TH, NGS_MODEL_BLEND>(rec, ids, ranges, rp, views, image, overdraw, state, L, s);
+      break;
+    case NGS_MODEL_VICINI:
+      forward_chunk<TW, TH, NGS_MODEL_VICINI>(rec, ids, ranges, rp, views, image, overdraw, state, L, s);
+      break;
+    default:
+      forward_chunk<TW, TH, NGS_MODEL_EXP>(rec, ids, ranges, rp, views, image, overdraw, state, L, s);
+  }
 }
 
 template <int TW, int TH>
 void backward_kind(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
                    const ViewParams* views, const float* dl, const float4* state, float4* grad2d, const Launch& L,
                    cudaStream_t s) {
-  if (rp.kind == NGS_MODEL_QUAD)
-    backward_chunk<TW, TH, NGS_MODEL_QUAD>(rec, ids, ranges, rp, views, dl, state, grad2d, L, s);
-  else
-    backward_chunk<TW, TH, NGS_MODEL_EXP>(rec, ids, ranges, rp, views, dl, state, grad2d, L, s);
+  switch (rp.kind) {
+    case NGS_MODEL_QUAD:
+      backward_chunk<TW, TH, NGS_MODEL_QUAD>(rec, ids, ranges, rp, views, dl, state, grad2d, L, s);
+      break;
+    case NGS_MODEL_BLEND:
+      backward_chunk<TW, TH, NGS_MODEL_BLEND>(rec, ids, ranges, rp, views, dl, state, grad2d, L, s);
+      break;
+    case NGS_MODEL_VICINI:
+      backward_chunk<TW, TH, NGS_MODEL_VICINI>(rec, ids, ranges, rp, views, dl, state, grad2d, L, s);
+      break;
+    default:
+      backward_chunk<TW, TH, NGS_MODEL_EXP>(rec, ids, ranges, rp, views, dl, state, grad2d, L, s);
+  }
 }
 
 int chunk_code(const RenderParams& rp) {

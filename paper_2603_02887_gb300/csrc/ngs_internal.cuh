@@ -39,7 +39,8 @@ struct RenderParams {
   float alpha_min, alpha_max, t_eps, dilation, near_plane;
   float log2_alpha_min;  // the alpha >= alpha_min test is made on log2(alpha)
   float bg[3];
-  float c;               // quadratic parameter (NGS_MODEL_QUAD)
+  float c;               // model parameter: c (quadratic) or gamma (blended, Vicini)
+  float c1;              // 1 - gamma
   int kind;
   int tile_w, tile_h;
   int tiles_x, tiles_y;  // of the view a kernel works on (kernels that see several views set them per view)
@@ -62,36 +63,47 @@ constexpr uint32_t kCheckIndex = 1u;  // a sorted pair named a splat record inde
 // Geometry of the view holding global tile t. A single view takes it from the kernel parameters (no
 // dependent load before the tile's work starts); a batch looks it up in the view table.
 struct TileView {
+  int view;                  // index of the view (0 for a single view)
   int W, H, tiles_x, local;  // image size, tiles per row, tile index within the view
-  size_t pix_base;           // first packed pixel of the view (replay state)
-  float* image;              // the view's outputs
-  int32_t* overdraw;
 };
 
 __device__ __forceinline__ int view_of_tile(const ViewParams* __restrict__ views, int n_views, uint32_t t);
 
 __device__ __forceinline__ TileView tile_view(const RenderParams& rp, const ViewParams* __restrict__ views,
-                                              uint32_t t, float* image0 = nullptr, int32_t* overdraw0 = nullptr) {
+                                              uint32_t t) {
   TileView tv;
   if (rp.n_views == 1) {
+    tv.view = 0;
     tv.W = rp.width;
     tv.H = rp.height;
     tv.tiles_x = rp.tiles_x;
     tv.local = (int)t;
-    tv.pix_base = 0;
-    tv.image = image0;
-    tv.overdraw = overdraw0;
   } else {
     const int v = view_of_tile(views, (int)rp.n_views, t);
+    tv.view = v;
     tv.W = __ldg(&views[v].cam.W);
     tv.H = __ldg(&views[v].cam.H);
     tv.tiles_x = __ldg(&views[v].tiles_x);
     tv.local = (int)(t - __ldg(&views[v].tile_base));
-    tv.pix_base = (size_t)__ldg(reinterpret_cast<const unsigned long long*>(&views[v].pix_base));
-    tv.image = reinterpret_cast<float*>(__ldg(reinterpret_cast<const unsigned long long*>(&views[v].image)));
-    tv.overdraw = reinterpret_cast<int32_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&views[v].overdraw)));
   }
   return tv;
+}
+
+// First packed pixel (replay state) and output arrays of view v; a single view takes its outputs from the
+// kernel parameters. Looked up where they are used, so that they are not held in registers meanwhile.
+__device__ __forceinline__ size_t view_pix_base(const RenderParams& rp, const ViewParams* __restrict__ views, int v) {
+  return rp.n_views == 1 ? 0 : (size_t)__ldg(reinterpret_cast<const unsigned long long*>(&views[v].pix_base));
+}
+__device__ __forceinline__ float* view_image(const RenderParams& rp, const ViewParams* __restrict__ views, int v,
+                                             float* image0) {
+  return rp.n_views == 1 ? image0
+                         : reinterpret_cast<float*>(__ldg(reinterpret_cast<const unsigned long long*>(&views[v].image)));
+}
+__device__ __forceinline__ int32_t* view_overdraw(const RenderParams& rp, const ViewParams* __restrict__ views, int v,
+                                                  int32_t* overdraw0) {
+  return rp.n_views == 1
+             ? overdraw0
+             : reinterpret_cast<int32_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&views[v].overdraw)));
 }
 
 // The view whose global tiles contain tile t (views[0].tile_base = 0; tile bases ascend).
@@ -125,7 +137,9 @@ constexpr float kConicScale = -0.5f * 1.4426950408889634f;
 // Per-pixel replay state, 2 float4 per pixel (App. C: E_k is computed in the forward pass and handed
 // to the adjoint pass).
 //   quadratic:   s0 = (n | sat << 31, E_k), s1 = (A = sum_{i<k} E_i alpha_i, taubar_k)
+//   blended:     s0 = (n | sat << 31, E_k), s1 = (sum_{i<k} E_i alpha_i P_i, sum_{i<k} alpha_i P_i)
 //   exponential: s0 = (n, C = L0 including background), s1 = (T_end, 0, 0, 0)
+//   Vicini:      s0 = (n | linear sat << 31, E_k of the linear list), s1 = (L0 of the exponential list, 0)
 // n = number of list entries of the pixel's tile that the forward pass walked through.
 
 // ---- helpers shared bit-for-bit by the forward and the replay kernels ---------------------------
@@ -148,6 +162,11 @@ __device__ __forceinline__ float splat_log2_alpha(float px, float py, float4 r0,
 // Quadratic slope term alpha (1 + c taubar), clamped at 0 (Table 1 with the [.]_+ of T).
 __device__ __forceinline__ float quad_slope(float alpha, float c, float tau) {
   return fmaxf(__fmul_rn(alpha, __fmaf_rn(c, tau, 1.0f)), 0.0f);
+}
+
+// Blended slope term alpha (1 - gamma + gamma P), P = prod_{j<i}(1 - alpha_j) (Table 1).
+__device__ __forceinline__ float blend_slope(float alpha, float gamma, float one_minus_gamma, float P) {
+  return __fmul_rn(alpha, __fmaf_rn(gamma, P, one_minus_gamma));
 }
 
 // ---- host-side objects ---------------------------------------------------------------------------

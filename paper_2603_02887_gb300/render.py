@@ -18,15 +18,21 @@ from . import _abi
 #: c = -0.5 (sub-linear), 0 (linear), +0.5 (super-linear) as in the paper's experiments (Sec. 5)
 MODELS = {"exp": (_abi.NGS_MODEL_EXP, 0.0), "sub": (_abi.NGS_MODEL_QUAD, -0.5), "lin": (_abi.NGS_MODEL_QUAD, 0.0),
           "sup": (_abi.NGS_MODEL_QUAD, 0.5)}
+#: the other rows of Table 1 on the same kernels, with the parameter of the paper's figures (gamma = 0.5)
+EXTRA_MODELS = {"blend": (_abi.NGS_MODEL_BLEND, 0.5), "vicini": (_abi.NGS_MODEL_VICINI, 0.5)}
+KINDS = {"exp": _abi.NGS_MODEL_EXP, "quad": _abi.NGS_MODEL_QUAD, "blend": _abi.NGS_MODEL_BLEND,
+         "vicini": _abi.NGS_MODEL_VICINI}
 PARAM_KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 
 
 def model_spec(model):
+    """A model name ("exp", "sub", "lin", "sup", "blend", "vicini") or a (kind, parameter) pair, kind a
+    name of KINDS or its number; returns (kind number, parameter)."""
     if isinstance(model, str):
-        return MODELS[model]
+        return MODELS[model] if model in MODELS else EXTRA_MODELS[model]
     kind, param = model
     if isinstance(kind, str):
-        kind = {"exp": _abi.NGS_MODEL_EXP, "quad": _abi.NGS_MODEL_QUAD}[kind]
+        kind = KINDS[kind]
     return int(kind), float(param)
 
 

@@ -1,0 +1,75 @@
+"""GPU parity of the other rows of Table 1 on the same kernels: the blended transmittance and Vicini et
+al.'s lerp of the linear and exponential lists (gamma = 0.5 as in the paper's figures, and other gamma),
+and the quadratic model with c outside the three experiment values (c = 1 as in Fig. 2, and c = -0.3).
+Same bars as the four main models: images <= 1e-4 and overdraw exact on non-fragile pixels, gradients
+within the relative criterion with the oracle's error scale, tile shapes and batches bit-identical."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2603_02887_gb300 import _abi, synth  # noqa: E402
+from paper_2603_02887_gb300.render import Renderer  # noqa: E402
+from tests.gpu_util import upload  # noqa: E402
+from tests.test_gpu_parity import _backward_check, _forward_check  # noqa: E402
+
+BLEND, VICINI, QUAD = _abi.NGS_MODEL_BLEND, _abi.NGS_MODEL_VICINI, _abi.NGS_MODEL_QUAD
+VARIANTS = [(BLEND, 0.5), (VICINI, 0.5), (BLEND, 0.2), (VICINI, 0.8), (QUAD, 1.0), (QUAD, -0.3)]
+IDS = ["blend0.5", "vicini0.5", "blend0.2", "vicini0.8", "quad1", "quad-0.3"]
+
+
+@pytest.fixture(scope="module")
+def rnd():
+    r = Renderer("cuda:0")
+    yield r
+    r.close()
+
+
+@pytest.mark.parametrize("model", VARIANTS, ids=IDS)
+def test_forward_matches_oracle(rnd, model):
+    _forward_check(rnd, synth.tiny_scene(0), synth.tiny_camera(), model)
+    _forward_check(rnd, synth.clustered_scene(20000, seed=4, sh_degree=3), synth.outside_camera(203, 141, 12.0),
+                   model)
+
+
+@pytest.mark.parametrize("model", VARIANTS, ids=IDS)
+def test_backward_matches_oracle(rnd, model):
+    _backward_check(rnd, synth.tiny_scene(0), synth.tiny_camera(), model)
+    _backward_check(rnd, synth.clustered_scene(6000, seed=6, sh_degree=3), synth.outside_camera(160, 120, 12.0),
+                    model)
+
+
+@pytest.mark.parametrize("model", VARIANTS[:2], ids=IDS[:2])
+def test_backward_with_background_and_cap(rnd, model):
+    """A non-black background enters through E_k = L_b (unsaturated rays) and the end transmittance; a
+    max_splats cap cuts lists before either stop."""
+    opts = dict(background=(0.2, 0.5, 0.8), max_splats=6)
+    scene, cam = synth.clustered_scene(6000, seed=8, sh_degree=1), synth.outside_camera(120, 96, 12.0)
+    _forward_check(rnd, scene, cam, model, options=opts)
+
+
+def test_named_variants_and_bit_identities(rnd):
+    scene, cam = synth.clustered_scene(20000, seed=5, sh_degree=2), synth.outside_camera(250, 170, 13.0)
+    params = upload(scene)
+    cams = [cam, synth.outside_camera(97, 61, 11.0), synth.outside_camera(160, 90, 14.0)]
+    for name, spec in (("blend", (BLEND, 0.5)), ("vicini", (VICINI, 0.5))):
+        a = rnd.render(params, cam, name)[0]
+        b = rnd.render(params, cam, spec)[0]
+        assert torch.equal(a, b)
+        outs = [rnd.render(params, cam, name, dict(tile_w=t[0], tile_h=t[1]))[:2] for t in ((8, 8), (16, 16), (16, 32))]
+        for img, od in outs[1:]:
+            assert torch.equal(img, outs[0][0]) and torch.equal(od, outs[0][1]), name
+        imgs, ods, frame = rnd.render_batch(params, cams, name, dict(schedule="persistent"))
+        for v, c in enumerate(cams):
+            i1, o1, _ = rnd.render(params, c, name)
+            assert torch.equal(frame.split(imgs)[v], i1) and torch.equal(frame.split(ods)[v], o1), (name, v)
+
+
+def test_gamma_out_of_range_rejected(rnd):
+    params = upload(synth.tiny_scene(0))
+    for bad in ((BLEND, 1.5), (VICINI, -0.1)):
+        with pytest.raises(_abi.NGSError, match="gamma"):
+            rnd.render(params, synth.tiny_camera(), bad)
