@@ -2,7 +2,7 @@
 //
 // The sort works on `nseg` equal segments of seg_len items at once, each sorted on its own (the depth sort
 // of a batch sorts every view's Gaussians in one launch per kernel). Each pass runs three kernels:
-//   upsweep   per block of 2048 items of a segment: digit histogram -> hist[segment][digit][block]
+//   upsweep   per block of 1024 items of a segment: digit histogram -> hist[segment][digit][block]
 //   scan      one block per (segment, digit): exclusive scan of that row in place, total -> totals
 //   downsweep per block: stable rank of every item within the block (warp multi-split with
 //             __match_any_sync, warps in order), reorder in shared memory so that items of one digit
@@ -51,7 +51,7 @@ __device__ __forceinline__ T block_exclusive_sum(T v, T* s_warp, T* total) {
 }
 
 constexpr int kThreads = 256;
-constexpr int kItems = 8;
+constexpr int kItems = 4;  // (a sweep of 4, 6, 8, 12, 16 on GB300: 4 is fastest at 0.5-3.3 M items)
 constexpr int kTile = kThreads * kItems;  // items per block
 constexpr int kWarps = kThreads / 32;
 constexpr int kDigits = 256;
