@@ -38,7 +38,7 @@ WORKLOAD = "single view, 500k clustered Gaussians (SH 3, FP32), 1920x1080, 4 tra
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--gaussians", type=int, default=500_000)
@@ -80,9 +80,10 @@ def workload(args, rank):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms while the timed region runs."""
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms; only the samples taken inside the timed
+    region (between mark_start and mark_end, by their timestamps) are summarised."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -90,11 +91,18 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -103,7 +111,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
     def stop(self):
         if self.proc is None:
@@ -113,22 +121,28 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], None, set()
+        sm, smax, reasons, power = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        t0 = self.t0 if self.t0 is not None else -1e30
+        t1 = (self.t1 if self.t1 is not None else 1e30) + 0.15  # a sample is printed shortly after it is taken
+        for stamp, line in self.lines:
+            if not (t0 <= stamp <= t1):
+                continue
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax = float(parts[2])
+                sm.append(float(parts[2]))
+                smax = float(parts[3])
+                power.append(float(parts[4]))
             except ValueError:
                 continue
-            for name, val in zip(names, parts[5:9]):
+            for name, val in zip(names, parts[6:10]):
                 if val.lower().startswith("active"):
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w_median": statistics.median(power) if power else None,
+                "window": "samples printed during the timed region"}
 
 
 def measured_peaks():
@@ -204,15 +218,18 @@ def run_ours(args):
     launches0 = r.launch_count()
     clocks = ClockSampler(local)
     clocks.start()
+    time.sleep(0.3)  # nvidia-smi's first samples
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    clocks.mark_start()
     for i in range(K):
         flush.zero_()
         starts[i].record()
         step(model_ev[i])
         ends[i].record()
     torch.cuda.synchronize()
+    clocks.mark_end()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
@@ -504,7 +521,7 @@ def run_serving(args, r, dev):
     srv.close()
     out["server"]["stats"] = {k: st[k] for k in ("batches", "max_batch_views", "over_budget_admissions",
                                                  "peak_reserved_bytes")}
-    r.set_graphs(True)  # the one-at-a-time form replays its graphs (one frame per scene and size)
+    r.set_graphs(False)  # direct launches, as the server's workers (the model varies from call to call)
     run_one_at_a_time(r, scenes, warm, np.zeros(len(warm)), options=opts)
     out["one_at_a_time"] = {name: run_one_at_a_time(r, scenes, reqs, arr, options=opts) for name, arr in loads.items()}
     out["saturation_speedup_vs_one_at_a_time"] = round(out["server"]["saturation"]["frames_per_s"] /

@@ -2,7 +2,7 @@
 //
 // The sort works on `nseg` equal segments of seg_len items at once, each sorted on its own (the depth sort
 // of a batch sorts every view's Gaussians in one launch per kernel). Each pass runs three kernels:
-//   upsweep   per block of 1024 items of a segment: digit histogram -> hist[segment][digit][block]
+//   upsweep   per block of 1024 (or 4096) items of a segment: digit histogram -> hist[segment][digit][block]
 //   scan      one block per (segment, digit): exclusive scan of that row in place, total -> totals
 //   downsweep per block: stable rank of every item within the block (warp multi-split with
 //             __match_any_sync, warps in order), reorder in shared memory so that items of one digit
@@ -51,8 +51,16 @@ __device__ __forceinline__ T block_exclusive_sum(T v, T* s_warp, T* total) {
 }
 
 constexpr int kThreads = 256;
-constexpr int kItems = 4;  // (a sweep of 4, 6, 8, 12, 16 on GB300: 4 is fastest at 0.5-3.3 M items)
-constexpr int kTile = kThreads * kItems;  // items per block
+// Items per thread: 4 (1024 per CTA) up to kSmallSort items per segment, where the passes are latency-bound
+// and more CTAs hide more latency (a sweep of 4..16 on GB300 at 0.5-3.3 M items); 16 above it, where the
+// per-digit scans over the CTAs' counts would otherwise grow long.
+constexpr int kSmallSort = 1 << 23;
+template <int ITEMS>
+struct SortTile {
+  static constexpr int kItems = ITEMS;
+  static constexpr int kTile = kThreads * ITEMS;
+};
+__host__ __device__ constexpr int tile_items(uint32_t seg_len) { return seg_len <= (uint32_t)kSmallSort ? 1024 : 4096; }
 constexpr int kWarps = kThreads / 32;
 constexpr int kDigits = 256;
 
@@ -65,7 +73,7 @@ __device__ __forceinline__ uint32_t segment_count(uint32_t seg_len, const uint32
   return n_dev ? min(*n_dev, seg_len) : seg_len;
 }
 
-template <typename K>
+template <typename K, int ITEMS>
 __global__ void __launch_bounds__(kThreads) upsweep_kernel(const K* __restrict__ keys, uint32_t seg_len,
                                                            const uint32_t* __restrict__ n_dev, int shift,
                                                            uint32_t* __restrict__ hist, uint32_t nblocks) {
@@ -77,10 +85,11 @@ __global__ void __launch_bounds__(kThreads) upsweep_kernel(const K* __restrict__
   hist += (size_t)seg * kDigits * nblocks;
   for (int i = tid; i < kWarps * kDigits; i += kThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
+  constexpr int kTile = SortTile<ITEMS>::kTile;
   uint32_t base = blk * (uint32_t)kTile;
   const int lane = tid & 31;
 #pragma unroll
-  for (int j = 0; j < kItems; ++j) {
+  for (int j = 0; j < ITEMS; ++j) {
     uint32_t idx = base + j * kThreads + tid;
     uint32_t d = idx < n ? digit_of(keys[idx], shift) : (uint32_t)kDigits;
     // one shared-memory atomic per distinct digit of the warp (neighbouring keys often share digits)
@@ -112,13 +121,14 @@ __global__ void __launch_bounds__(1024) scan_digit_kernel(uint32_t* hist, uint32
   if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
-template <typename K>
+template <typename K, int ITEMS>
 __global__ void __launch_bounds__(kThreads) downsweep_kernel(const K* __restrict__ keys_in,
                                                              const uint32_t* __restrict__ vals_in,
                                                              K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                                                              uint32_t seg_len, const uint32_t* __restrict__ n_dev,
                                                              int shift, const uint32_t* __restrict__ hist,
                                                              const uint32_t* __restrict__ totals, uint32_t nblocks) {
+  constexpr int kTile = SortTile<ITEMS>::kTile, kItems = ITEMS;
   const uint32_t seg = blockIdx.x / nblocks, blk = blockIdx.x - seg * nblocks;
   const uint32_t n = segment_count(seg_len, n_dev);
   if (blk * (uint32_t)kTile >= n) return;  // the whole block is past the segment's items
@@ -201,9 +211,10 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(const K* __restrict
   }
 }
 
-template <typename K>
+template <typename K, int ITEMS>
 int radix_sort(K* keys[2], uint32_t* vals[2], uint32_t seg_len, uint32_t nseg, const uint32_t* n_dev, int begin_bit,
                int end_bit, uint32_t* hist, cudaStream_t s, int* launches) {
+  constexpr int kTile = SortTile<ITEMS>::kTile;
   int cur = 0;
   if (seg_len <= 1 || nseg == 0 || begin_bit >= end_bit) return cur;
   uint32_t nblocks = (seg_len + kTile - 1) / kTile;
@@ -212,10 +223,10 @@ int radix_sort(K* keys[2], uint32_t* vals[2], uint32_t seg_len, uint32_t nseg, c
   // at most 24 KB of dynamic shared memory (for 64-bit keys), within the default limit without an opt-in
   size_t smem = (sizeof(K) + sizeof(uint32_t)) * kTile;
   for (int shift = begin_bit; shift < end_bit; shift += 8) {
-    upsweep_kernel<K><<<grid, kThreads, 0, s>>>(keys[cur], seg_len, n_dev, shift, hist, nblocks);
+    upsweep_kernel<K, ITEMS><<<grid, kThreads, 0, s>>>(keys[cur], seg_len, n_dev, shift, hist, nblocks);
     scan_digit_kernel<<<kDigits * nseg, 1024, 0, s>>>(hist, nblocks, totals);
-    downsweep_kernel<K><<<grid, kThreads, smem, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], seg_len,
-                                                     n_dev, shift, hist, totals, nblocks);
+    downsweep_kernel<K, ITEMS><<<grid, kThreads, smem, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1],
+                                                            seg_len, n_dev, shift, hist, totals, nblocks);
     cur ^= 1;
     *launches += 3;
   }
@@ -352,13 +363,16 @@ void launch_tile_order(const uint2* ranges, uint32_t ntiles, uint32_t* sched, ui
 }
 
 size_t radix_hist_words(uint32_t seg_len, uint32_t nseg) {
-  uint32_t nblocks = (seg_len + kTile - 1) / kTile;
+  const uint32_t tile = (uint32_t)tile_items(seg_len);
+  uint32_t nblocks = (seg_len + tile - 1) / tile;
   return (size_t)kDigits * (nblocks + 1) * nseg;
 }
 
 int radix_sort_u32(uint32_t* keys[2], uint32_t* vals[2], uint32_t seg_len, uint32_t nseg, const uint32_t* n_dev,
                    int begin_bit, int end_bit, uint32_t* hist, cudaStream_t s, int* launches) {
-  return radix_sort<uint32_t>(keys, vals, seg_len, nseg, n_dev, begin_bit, end_bit, hist, s, launches);
+  if (tile_items(seg_len) == SortTile<4>::kTile)
+    return radix_sort<uint32_t, 4>(keys, vals, seg_len, nseg, n_dev, begin_bit, end_bit, hist, s, launches);
+  return radix_sort<uint32_t, 16>(keys, vals, seg_len, nseg, n_dev, begin_bit, end_bit, hist, s, launches);
 }
 
 
