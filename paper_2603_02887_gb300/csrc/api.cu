@@ -242,21 +242,24 @@ static void phase2(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, uint32_t ca
   launch_emit_pairs(f->rec.as<float4>(), f->gvals[f->g_final].as<uint32_t>(), f->offsets.as<uint32_t>(), views, rp,
                     f->ptile[0].as<uint32_t>(), f->pvals[0].as<uint32_t>(), s);
   stage_end(ctx, s, 2, ev, pl.R ? 1 : 0);
-  // 4. stable sort of the pairs by global tile: the depth order inside each tile is kept, so the result is
-  //    the order of the full 64-bit (tile << 32 | depth) keys
+  // 4. stable sort of the pairs by view-local tile: the (view, depth) order inside each local tile is kept,
+  //    so every (view, tile) list is contiguous and in the order of the 64-bit (tile << 32 | depth) keys
   stage_begin(ctx, s, 3, &ev);
   int launches = 0;
   {
     uint32_t* k2[2] = {f->ptile[0].as<uint32_t>(), f->ptile[1].as<uint32_t>()};
     uint32_t* v2[2] = {f->pvals[0].as<uint32_t>(), f->pvals[1].as<uint32_t>()};
-    f->p_final = radix_sort_u32(k2, v2, cap, 1, np_dev, 0, tile_bits(pl.ntiles), ctx->hist.as<uint32_t>(), s,
+    int max_tiles = 0;  // the pairs carry view-local tiles
+    for (const ViewParams& vp : f->view_host) max_tiles = std::max(max_tiles, vp.tiles_x * vp.tiles_y);
+    f->p_final = radix_sort_u32(k2, v2, cap, 1, np_dev, 0, tile_bits((uint32_t)max_tiles), ctx->hist.as<uint32_t>(), s,
                                 &launches);
   }
   stage_end(ctx, s, 3, ev, launches);
   // 5. per-tile [start, end); for the persistent schedule, the tiles by descending pair count
   stage_begin(ctx, s, 4, &ev);
   launches = cap ? 1 : 0;
-  launch_tile_ranges(f->ptile[f->p_final].as<uint32_t>(), cap, np_dev, pl.ntiles, f->ranges.as<uint2>(), s);
+  launch_tile_ranges(f->ptile[f->p_final].as<uint32_t>(), f->pvals[f->p_final].as<uint32_t>(), views, pl.n, rp.n_views,
+                     cap, np_dev, pl.ntiles, f->ranges.as<uint2>(), s);
   const uint32_t* work = nullptr;
   uint32_t* counter = nullptr;
   if (rp.schedule == NGS_SCHEDULE_PERSISTENT) {
@@ -513,6 +516,10 @@ int ngs::render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, co
   k2.add(n_views == 1 ? pl.image : nullptr);  // a batch reads its outputs from the view table
   k2.add(n_views == 1 ? pl.overdraw : nullptr);
   k2.add(ctx->num_sms);
+  for (const ViewParams& vp : f->view_host) {  // the tile sort's bit count follows the largest view
+    k2.add(vp.tiles_x);
+    k2.add(vp.tiles_y);
+  }
   for (const DevBuf* b : {&f->rec, &f->gvals[0], &f->gvals[1], &f->offsets, &f->views, &f->ptile[0], &f->ptile[1],
                           &f->pvals[0], &f->pvals[1], &ctx->hist, &f->ranges, &f->work, &f->sched, &f->state})
     k2.add(b->p);
@@ -669,7 +676,8 @@ NGS_API int ngs_frame_view_get(const ngs_frame* fc, ngs_frame_view* out) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) {
     launch_compose_keys(f->ptile[f->p_final].as<uint32_t>(), f->pvals[f->p_final].as<uint32_t>(), f->rec.as<float4>(),
-                        np, f->keys64.as<uint64_t>(), nullptr);
+                        f->views.as<ViewParams>(), (uint32_t)f->n, (uint32_t)f->n_views, np, f->keys64.as<uint64_t>(),
+                        nullptr);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);

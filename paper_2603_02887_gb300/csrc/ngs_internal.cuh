@@ -288,17 +288,19 @@ size_t radix_hist_words(uint32_t seg_len, uint32_t nseg);
 void launch_scan_counts(const uint32_t* tile_count, const uint32_t* order, uint32_t n, uint32_t* offsets,
                         uint64_t* block_sums, uint64_t* total, cudaStream_t s, int* launches);
 size_t scan_tmp_words(uint32_t n);
-// One (global tile, record index) pair per covered tile, in the order of `order` (n_records entries): the
-// records are in (view, depth) order, so sorting the pairs stably by tile alone gives the order of the
-// 64-bit keys (tile << 32 | depth bits).
+// One (view-local tile, record index) pair per covered tile, in the order of `order` (n_records entries):
+// the records are in (view, depth) order, so sorting the pairs stably by the local tile alone orders them by
+// (local tile, view, depth): every (view, tile) list is contiguous and in the order of the 64-bit keys
+// (global tile << 32 | depth bits).
 void launch_emit_pairs(const float4* rec, const uint32_t* order, const uint32_t* offsets, const ViewParams* views,
                        const RenderParams& rp, uint32_t* tiles, uint32_t* vals, cudaStream_t s);
-// keys[i] = tiles[i] << 32 | bits(depth of record vals[i]) (diagnostics).
-void launch_compose_keys(const uint32_t* tiles, const uint32_t* vals, const float4* rec, uint32_t npairs,
-                         uint64_t* keys, cudaStream_t s);
+// keys[i] = global tile of pair i << 32 | bits(depth of record vals[i]) (diagnostics).
+void launch_compose_keys(const uint32_t* tiles, const uint32_t* vals, const float4* rec, const ViewParams* views,
+                         uint32_t n_per_view, uint32_t n_views, uint32_t npairs, uint64_t* keys, cudaStream_t s);
 // [start, end) of every global tile's pairs (zero-length ranges stay (0, 0)); npairs_cap items are
 // covered by the grid, of which the first *npairs_dev are valid if npairs_dev is not null.
-void launch_tile_ranges(const uint32_t* tiles, uint32_t npairs_cap, const uint32_t* npairs_dev, uint32_t ntiles,
+void launch_tile_ranges(const uint32_t* tiles, const uint32_t* vals, const ViewParams* views, uint32_t n_per_view,
+                        uint32_t n_views, uint32_t npairs_cap, const uint32_t* npairs_dev, uint32_t ntiles,
                         uint2* ranges, cudaStream_t s);
 // Persistent schedule: work[] lists all tiles by descending pair count (buckets of floor(log2(pairs)),
 // any order within a bucket). `sched` holds kSchedWords zeroed words: [0] forward and [1] backward work

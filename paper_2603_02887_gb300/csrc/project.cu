@@ -385,7 +385,6 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const float4* rec, cons
   const uint32_t view = id / rp.n_gaussians;
   rp.tiles_x = views[view].tiles_x;
   rp.tiles_y = views[view].tiles_y;
-  const uint32_t tile_base = views[view].tile_base;
   float4 r0 = rec[3 * (int64_t)id], r1 = rec[3 * (int64_t)id + 1], r2 = rec[3 * (int64_t)id + 2];
   int x0, x1, y0, y1;
   if (!tile_rect(r0.x, r0.y, r2.z, r2.w, rp, x0, x1, y0, y1)) return;
@@ -393,7 +392,7 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const float4* rec, cons
   for (int ty = y0; ty <= y1 && off < end; ++ty) {
     int t0, t1;
     if (!row_span(b, rp, ty, x0, x1, t0, t1)) continue;
-    uint32_t tile = tile_base + (uint32_t)(ty * rp.tiles_x + t0);
+    uint32_t tile = (uint32_t)(ty * rp.tiles_x + t0);  // within the view
     for (int tx = t0; tx <= t1 && off < end; ++tx, ++tile, ++off) {
       tiles[off] = tile;
       vals[off] = id;

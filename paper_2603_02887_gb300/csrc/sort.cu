@@ -292,22 +292,34 @@ __global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const uint32_t
   }
 }
 
-__global__ void tile_ranges_kernel(const uint32_t* __restrict__ tiles, uint32_t npairs_cap,
-                                   const uint32_t* __restrict__ npairs_dev, uint2* __restrict__ ranges) {
+// Global tile of pair i: the view's first tile plus the view-local tile it was sorted by.
+__device__ __forceinline__ uint32_t global_tile(const uint32_t* __restrict__ tiles, const uint32_t* __restrict__ vals,
+                                                const ViewParams* __restrict__ views, uint32_t n_per_view,
+                                                uint32_t n_views, uint32_t i) {
+  return n_views == 1 ? tiles[i] : __ldg(&views[vals[i] / n_per_view].tile_base) + tiles[i];
+}
+
+__global__ void tile_ranges_kernel(const uint32_t* __restrict__ tiles, const uint32_t* __restrict__ vals,
+                                   const ViewParams* __restrict__ views, uint32_t n_per_view, uint32_t n_views,
+                                   uint32_t npairs_cap, const uint32_t* __restrict__ npairs_dev,
+                                   uint2* __restrict__ ranges) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t npairs = npairs_dev ? min(*npairs_dev, npairs_cap) : npairs_cap;
   if (i >= npairs) return;
-  uint32_t t = tiles[i];
-  if (i == 0 || tiles[i - 1] != t) ranges[t].x = i;
-  if (i == npairs - 1 || tiles[i + 1] != t) ranges[t].y = i + 1;
+  const uint32_t t = global_tile(tiles, vals, views, n_per_view, n_views, i);
+  if (i == 0 || global_tile(tiles, vals, views, n_per_view, n_views, i - 1) != t) ranges[t].x = i;
+  if (i == npairs - 1 || global_tile(tiles, vals, views, n_per_view, n_views, i + 1) != t) ranges[t].y = i + 1;
 }
 
 __global__ void compose_keys_kernel(const uint32_t* __restrict__ tiles, const uint32_t* __restrict__ vals,
-                                    const float4* __restrict__ rec, uint32_t npairs, uint64_t* __restrict__ keys) {
+                                    const float4* __restrict__ rec, const ViewParams* __restrict__ views,
+                                    uint32_t n_per_view, uint32_t n_views, uint32_t npairs,
+                                    uint64_t* __restrict__ keys) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npairs) return;
   const float z = rec[3 * (size_t)vals[i] + 2].y;
-  keys[i] = ((uint64_t)tiles[i] << 32) | (uint64_t)__float_as_uint(z);
+  const uint32_t t = global_tile(tiles, vals, views, n_per_view, n_views, i);
+  keys[i] = ((uint64_t)t << 32) | (uint64_t)__float_as_uint(z);
 }
 
 // ---- tile work order for the persistent composite: descending pair count ---------------------------
@@ -393,17 +405,20 @@ void launch_scan_counts(const uint32_t* tile_count, const uint32_t* order, uint3
   *launches += 3;
 }
 
-void launch_tile_ranges(const uint32_t* tiles, uint32_t npairs_cap, const uint32_t* npairs_dev, uint32_t ntiles,
+void launch_tile_ranges(const uint32_t* tiles, const uint32_t* vals, const ViewParams* views, uint32_t n_per_view,
+                        uint32_t n_views, uint32_t npairs_cap, const uint32_t* npairs_dev, uint32_t ntiles,
                         uint2* ranges, cudaStream_t s) {
   cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, s);
   if (npairs_cap == 0) return;
-  tile_ranges_kernel<<<(npairs_cap + 255) / 256, 256, 0, s>>>(tiles, npairs_cap, npairs_dev, ranges);
+  tile_ranges_kernel<<<(npairs_cap + 255) / 256, 256, 0, s>>>(tiles, vals, views, n_per_view, n_views, npairs_cap,
+                                                              npairs_dev, ranges);
 }
 
-void launch_compose_keys(const uint32_t* tiles, const uint32_t* vals, const float4* rec, uint32_t npairs,
-                         uint64_t* keys, cudaStream_t s) {
+void launch_compose_keys(const uint32_t* tiles, const uint32_t* vals, const float4* rec, const ViewParams* views,
+                         uint32_t n_per_view, uint32_t n_views, uint32_t npairs, uint64_t* keys, cudaStream_t s) {
   if (npairs == 0) return;
-  compose_keys_kernel<<<(npairs + 255) / 256, 256, 0, s>>>(tiles, vals, rec, npairs, keys);
+  compose_keys_kernel<<<(npairs + 255) / 256, 256, 0, s>>>(tiles, vals, rec, views, n_per_view, n_views, npairs,
+                                                           keys);
 }
 
 }  // namespace ngs

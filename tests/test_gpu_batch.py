@@ -74,11 +74,11 @@ def test_batch_views_bit_identical_to_single(rnd, clustered, model, tile):
         assert np.array_equal(ba["keys"][sel] - (np.uint64(t0) << np.uint64(32)), sa["keys"]), f"view {v}: keys"
         assert np.array_equal(ba["values"][sel] - np.uint32(v * n), sa["values"]), f"view {v}: values"
         r = ba["ranges"][t0:t1].astype(np.int64)
-        nonempty = r[:, 1] > r[:, 0]
         sr = sa["ranges"].astype(np.int64)
-        assert np.array_equal(nonempty, sr[:, 1] > sr[:, 0]), f"view {v}: non-empty tiles"
-        start = int(np.nonzero(sel)[0][0]) if sel.any() else 0
-        assert np.array_equal(r[nonempty] - start, sr[nonempty]), f"view {v}: ranges"
+        assert np.array_equal(r[:, 1] - r[:, 0], sr[:, 1] - sr[:, 0]), f"view {v}: list lengths"
+        for t in np.nonzero(r[:, 1] > r[:, 0])[0]:  # every (view, tile) list, entry by entry
+            assert np.array_equal(ba["values"][r[t, 0]:r[t, 1]] - np.uint32(v * n),
+                                  sa["values"][sr[t, 0]:sr[t, 1]]), f"view {v} tile {t}: list"
         total_pairs += sa["view"]["n_pairs"]
         if v == 3:  # the camera looking away from the scene
             assert sa["view"]["n_pairs"] == 0 and not torch.any(img1)
