@@ -259,6 +259,55 @@ NGS_API void ngs_reset_stage_times(ngs_ctx* ctx);
 /* Total number of kernel launches this context has issued (all stages). */
 NGS_API int64_t ngs_launch_count(const ngs_ctx* ctx);
 
+/* ---- training step (Sec. 5.1 "Loss", "Optimization", "Densification") -------------------------------- */
+
+/* Image loss L = (1 - lambda) L1 + lambda (1 - SSIM) of `image` against `target` (both device
+ * [height][width][3] FP32): L1 the mean absolute difference, SSIM the mean over pixels and channels of the
+ * structural similarity of Wang et al. with the 11 x 11 Gaussian window (sigma 1.5), C1 = 0.01^2,
+ * C2 = 0.03^2 and zero padding, as in 3D Gaussian splatting. dl_dimage (device, may be NULL) receives
+ * dL/dimage. loss_out (host double[3], may be NULL) receives (L, L1, SSIM); it synchronises the stream. */
+NGS_API int ngs_loss_l1_ssim(ngs_ctx* ctx, const float* image, const float* target, int32_t width, int32_t height,
+                             float lambda, float* dl_dimage, double* loss_out, void* stream);
+
+/* Adam over the five parameter arrays of n Gaussians (ngs_grads layout: means, log_scales, quats,
+ * opacity_logits, sh) in one launch, with per-array learning rates lr[5]: m = b1 m + (1 - b1) g,
+ * v = b2 v + (1 - b2) g^2, theta -= lr m^ / (sqrt(v^) + eps) with the bias corrections of step `step`
+ * (1-based). bounded != 0 clips each update to [-lr, lr] (the paper's "bounded Adam" as read here). */
+typedef struct {
+  float lr[5];
+  float beta1, beta2, eps;
+  int32_t step;
+  int32_t bounded;
+} ngs_adam;
+NGS_API int ngs_adam_step(ngs_ctx* ctx, int64_t n, int32_t sh_degree, const ngs_grads* params,
+                          const ngs_grads* grads, const ngs_grads* m, const ngs_grads* v, const ngs_adam* cfg,
+                          void* stream);
+
+/* accum[i] += |d_means[i]| and count[i] += 1 for every Gaussian with a nonzero positional gradient. */
+NGS_API int ngs_accumulate_grad_norm(ngs_ctx* ctx, int64_t n, const float* d_means, float* accum, float* count,
+                                     void* stream);
+
+/* Split / prune (Sec. 5.1 "Densification"). Gaussian i is pruned (prune != 0) when its opacity is below
+ * min_opacity or its largest scale below min_scale; else split (split != 0) when accum[i] / count[i] >
+ * grad_threshold; else kept. Splits are granted in index order while the count stays within max_gaussians.
+ * A split writes two children at mu +- (sigma_a / 2) r_a along the longest axis a, with sigma_a scaled by
+ * sqrt(3)/2 (the pair keeps the parent's variance along r_a) and everything else the parent's; kept
+ * Gaussians keep their Adam moments, children start from zero. Writes the surviving and new Gaussians, in
+ * index order, to out_* (capacity >= min(2 n, max(n, max_gaussians))) and their number to *n_out
+ * (host); synchronises the stream. n < 2^30. */
+typedef struct {
+  float grad_threshold;
+  float min_opacity;
+  float min_scale;
+  int32_t split;
+  int32_t prune;
+  int64_t max_gaussians;
+} ngs_densify_cfg;
+NGS_API int ngs_densify(ngs_ctx* ctx, int64_t n, int32_t sh_degree, const ngs_grads* params, const ngs_grads* m,
+                        const ngs_grads* v, const float* accum, const float* count, const ngs_densify_cfg* cfg,
+                        int64_t capacity, const ngs_grads* out_params, const ngs_grads* out_m,
+                        const ngs_grads* out_v, int64_t* n_out, void* stream);
+
 /* ---- render server ---------------------------------------------------------------------------------
  * A request loop over scenes kept resident on the device. The paper has no counterpart: this is the
  * serving form of the render call above.

@@ -55,6 +55,16 @@ class Grads(C.Structure):
                 ("d_opacity_logits", C.c_void_p), ("d_sh", C.c_void_p)]
 
 
+class Adam(C.Structure):
+    _fields_ = [("lr", C.c_float * 5), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("step", C.c_int32), ("bounded", C.c_int32)]
+
+
+class DensifyCfg(C.Structure):
+    _fields_ = [("grad_threshold", C.c_float), ("min_opacity", C.c_float), ("min_scale", C.c_float),
+                ("split", C.c_int32), ("prune", C.c_int32), ("max_gaussians", C.c_int64)]
+
+
 class FrameView(C.Structure):
     _fields_ = [("n_gaussians", C.c_int64), ("n_pairs", C.c_int64), ("tiles_x", C.c_int32), ("tiles_y", C.c_int32),
                 ("width", C.c_int32), ("height", C.c_int32), ("log2_alpha_min", C.c_float), ("n_views", C.c_int32),
@@ -112,6 +122,14 @@ SIGNATURES = {
     "ngs_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
     "ngs_reset_stage_times": (None, [C.c_void_p]),
     "ngs_launch_count": (C.c_int64, [C.c_void_p]),
+    "ngs_loss_l1_ssim": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_float, C.c_void_p,
+                                   C.POINTER(C.c_double), C.c_void_p]),
+    "ngs_adam_step": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.POINTER(Grads), C.POINTER(Grads), C.POINTER(Grads),
+                                C.POINTER(Grads), C.POINTER(Adam), C.c_void_p]),
+    "ngs_accumulate_grad_norm": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ngs_densify": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.POINTER(Grads), C.POINTER(Grads), C.POINTER(Grads),
+                              C.c_void_p, C.c_void_p, C.POINTER(DensifyCfg), C.c_int64, C.POINTER(Grads),
+                              C.POINTER(Grads), C.POINTER(Grads), C.POINTER(C.c_int64), C.c_void_p]),
     "ngs_default_server_config": (None, [C.POINTER(ServerConfig)]),
     "ngs_server_create": (C.c_int, [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]),
     "ngs_server_add_scene": (C.c_int, [C.c_void_p, C.POINTER(Gaussians), C.POINTER(C.c_int32)]),

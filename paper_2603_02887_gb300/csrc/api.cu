@@ -575,6 +575,9 @@ NGS_API void ngs_destroy(ngs_ctx* ctx) {
   free_buf(ctx->grad2d);
   free_buf(ctx->total);
   free_buf(ctx->flush);
+  free_buf(ctx->loss_tmp);
+  free_buf(ctx->densify_tmp);
+  free_buf(ctx->densify_totals);
   if (ctx->h_total) cudaFreeHost(ctx->h_total);
   for (auto& p : ctx->pending) {
     cudaEventDestroy(p.a);

@@ -189,6 +189,8 @@ struct ngs_ctx {
   ngs::DevBuf grad2d;    // per-Gaussian splat-record gradients (backward)
   ngs::DevBuf total;     // device-side pair count (uint64) and error word (uint64)
   ngs::DevBuf flush;     // autotuner: scratch cleared between timed calls to evict L2
+  ngs::DevBuf loss_tmp;  // image loss: moment and partial-derivative planes
+  ngs::DevBuf densify_tmp, densify_totals;  // split / prune decisions, scans and totals
   uint64_t* h_total = nullptr;  // pinned mirror of `total` (2 words)
   bool timing = false;
   struct Pending { cudaEvent_t a, b; int stage; };

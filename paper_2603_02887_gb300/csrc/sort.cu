@@ -57,7 +57,6 @@ constexpr int kThreads = 256;
 constexpr int kSmallSort = 1 << 23;
 template <int ITEMS>
 struct SortTile {
-  static constexpr int kItems = ITEMS;
   static constexpr int kTile = kThreads * ITEMS;
 };
 __host__ __device__ constexpr int tile_items(uint32_t seg_len) { return seg_len <= (uint32_t)kSmallSort ? 1024 : 4096; }
