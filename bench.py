@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--batched-gaussians", type=int, default=3_000_000)
     p.add_argument("--batched-views", type=int, default=32)
     p.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    p.add_argument("--no-training", action="store_true", help="skip the training-step measurement")
+    p.add_argument("--training-steps", type=int, default=300)
     p.add_argument("--serving-requests", type=int, default=2000)
     p.add_argument("--serving-rate", type=float, default=200.0)
     p.add_argument("--serving-high-rate", type=float, default=1500.0,
@@ -301,12 +303,14 @@ def run_ours(args):
     }
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, r, scene, cam, opts, dl, dev, world)
-    if world == 1 and not (args.no_batched and args.no_serving):
+    if world == 1 and not (args.no_batched and args.no_serving and args.no_training):
         del params, frames, grads
     if not args.no_batched and world == 1:
         line["batched"] = run_batched(args, r, dev, line["per_model"])
     if not args.no_serving and world == 1:
         line["serving"] = run_serving(args, r, dev)
+    if not args.no_training and world == 1:
+        line["training"] = run_training(args, r, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, scene, cam)
     if rank == 0:
@@ -526,6 +530,54 @@ def run_serving(args, r, dev):
     out["one_at_a_time"] = {name: run_one_at_a_time(r, scenes, reqs, arr, options=opts) for name, arr in loads.items()}
     out["saturation_speedup_vs_one_at_a_time"] = round(out["server"]["saturation"]["frames_per_s"] /
                                                        out["one_at_a_time"]["saturation"]["frames_per_s"], 3)
+    return out
+
+
+def run_training(args, r, dev):
+    """The training step (Sec. 5.1's recipe) on synthetic targets: a 50k-Gaussian clustered scene (SH 1, as
+    the paper's reconstructions) rendered from 8 cameras at 640x360 is the target; the learner starts from
+    it perturbed (opacity logits -1, SH + N(0, 0.1), means + N(0, 0.01)) and runs render -> L1 + D-SSIM ->
+    path-replay backward -> Adam -> split / prune, coarse to fine. Per model: steps per second (wall clock,
+    device synchronised at the end) and PSNR before / after."""
+    import torch
+
+    from paper_2603_02887_gb300 import synth
+    from paper_2603_02887_gb300.render import PARAM_KEYS
+    from paper_2603_02887_gb300.train import Trainer, psnr, render_targets
+
+    sc = synth.clustered_scene(50_000, seed=30, sh_degree=1)
+    gt = {k: torch.from_numpy(np.ascontiguousarray(sc[k])).to(dev) for k in PARAM_KEYS}
+    cams = synth.orbit_cameras(8, radius=12.0, seed=31, resolutions=((640, 360),))
+    steps = args.training_steps
+    out = {"gaussians": 50_000, "views": 8, "resolution": "640x360 (1/4, 1/2 then full)", "steps": steps,
+           "loss": "0.8 L1 + 0.2 (1 - SSIM)", "densify": "split every 100 steps, prune every 200"}
+    gen = torch.Generator(device=dev).manual_seed(32)
+    noise = {"means": 0.01 * torch.randn(gt["means"].shape, device=dev, generator=gen),
+             "sh": 0.1 * torch.randn(gt["sh"].shape, device=dev, generator=gen)}
+    r.set_graphs(False)
+    for m in MODELS:
+        targets = render_targets(r, gt, cams, m)
+        init = {k: v.clone() for k, v in gt.items()}
+        init["means"] += noise["means"]
+        init["sh"] += noise["sh"]
+        init["opacity_logits"] -= 1.0
+        tr = Trainer(init, cams, targets, model=m, iters=steps, grad_threshold=5e-4, renderer=r)
+        before = psnr(r, tr.params, cams, targets, m)
+        tr.step()  # warm-up (buffers)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps - 1):
+            tr.step()
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        after = psnr(r, tr.params, cams, targets, m)
+        out[m] = {"steps_per_s": round((steps - 1) / secs, 1), "ms_per_step": round(1e3 * secs / (steps - 1), 3),
+                  "psnr_before": round(before, 2), "psnr_after": round(after, 2),
+                  "gaussians_after": int(tr.params["means"].shape[0])}
+        for f in tr.frames.values():
+            r.recycle(f)
+    for m in MODELS[1:]:
+        out[m]["steps_per_s_vs_exp"] = round(out[m]["steps_per_s"] / out["exp"]["steps_per_s"], 3)
     return out
 
 
