@@ -552,8 +552,10 @@ __device__ __forceinline__ void add_view_gradient(const ngs_gaussians& g, const 
 // One thread per Gaussian; MULTI: loop over the views of a batch (records v n + i), else the one view
 // `cam0`, passed by value so that its entries are constant-bank operands rather than registers.
 // Culled splats (no tile) contribute nothing; a Gaussian culled in every view gets zeros.
+// One view: at most ~96 registers (5 CTAs per SM) -- the occupancy that hides this kernel's memory latency
+// best (a sweep of 3..8 CTAs per SM on GB300: 0.35 / 0.32 / 0.31 / 0.33 / 0.34 / 0.41 ms per 4 calls).
 template <int DEG, bool VEC, bool MULTI>
-__global__ void __launch_bounds__(128) project_backward_kernel(ngs_gaussians g, const ViewParams* __restrict__ views,
+__global__ void __launch_bounds__(128, MULTI ? 1 : 5) project_backward_kernel(ngs_gaussians g, const ViewParams* __restrict__ views,
                                                                CamParams cam0, RenderParams rp,
                                                                const uint32_t* tile_count, const float4* grad2d,
                                                                ngs_grads out) {
