@@ -162,9 +162,10 @@ __device__ __forceinline__ void store_sh(float* dst, const float (&c)[3 * K]) {
   }
 }
 
+// sh_src: Gaussian i's 3K SH coefficients (in global memory, or staged in shared memory by the caller).
 template <int DEG, bool VEC = false>
 __device__ __forceinline__ void forward_map(const ngs_gaussians& g, const CamParams& cam, const RenderParams& rp,
-                                            int i, ProjState<DEG>& st) {
+                                            int i, ProjState<DEG>& st, const float* sh_src) {
   constexpr int K = ProjState<DEG>::K;
   const float* m = g.means + 3 * (int64_t)i;
   float px = m[0], py = m[1], pz = m[2];
@@ -222,7 +223,7 @@ __device__ __forceinline__ void forward_map(const ngs_gaussians& g, const CamPar
   st.dir[2] = d2 * idn;
   sh_basis(DEG, st.dir[0], st.dir[1], st.dir[2], st.Y);
   float sh[3 * K];
-  load_sh<K, VEC>(g.sh + (int64_t)i * K * 3, sh);
+  load_sh<K, VEC>(sh_src, sh);
   float e0 = 0.5f, e1 = 0.5f, e2 = 0.5f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, const Vie
   uint32_t count = 0;
   if (z > rp.near_plane) {
     ProjState<DEG> st;
-    forward_map<DEG, VEC>(g, cam, rp, i, st);
+    forward_map<DEG, VEC>(g, cam, rp, i, st, g.sh + (int64_t)i * ProjState<DEG>::K * 3);
     if (st.det > 0.f && st.aleph >= rp.alpha_min && isfinite(st.A) && isfinite(st.C)) {
       float u = cam.fx * st.x * st.iz + cam.cx;
       float v = cam.fy * st.y * st.iz + cam.cy;
@@ -413,7 +414,8 @@ struct ParamGrad {
 template <int DEG, bool VEC, bool DIRECT>
 __device__ __forceinline__ void add_view_gradient(const ngs_gaussians& g, const CamParams& cam,
                                                   const RenderParams& rp, int i, const float4* gr,
-                                                  ParamGrad<DEG>& acc, const ngs_grads& out) {
+                                                  ParamGrad<DEG>& acc, const ngs_grads& out, const float* sh_src,
+                                                  float* dsh_dst) {
   constexpr int K = ProjState<DEG>::K;
   float4 g0 = gr[0], g1 = gr[1], g2 = gr[2];
   // the replay accumulates w / ln 2 (w = dL/d(log2 alpha)): restore the factor on the six moments
@@ -421,7 +423,7 @@ __device__ __forceinline__ void add_view_gradient(const ngs_gaussians& g, const 
   g1.x *= kLn2;
   g1.y *= kLn2;
   ProjState<DEG> st;
-  forward_map<DEG, VEC>(g, cam, rp, i, st);
+  forward_map<DEG, VEC>(g, cam, rp, i, st, sh_src);
   // moments -> record gradient (the record's A', B', C' are these same products) -> natural quantities
   const float Ap = kConicScale * st.A, Bp = 2.f * kConicScale * st.B, Cp = kConicScale * st.C;
   float du = -(2.f * Ap * g0.x + Bp * g0.y);
@@ -511,7 +513,7 @@ __device__ __forceinline__ void add_view_gradient(const ngs_gaussians& g, const 
   }
   // emission: dE/dsh = Y (unclamped channels); direction term into the mean
   float sh[3 * K];
-  load_sh<K, VEC>(g.sh + (int64_t)i * K * 3, sh);
+  load_sh<K, VEC>(sh_src, sh);
   float d0 = st.e[0] < 0.f ? 0.f : dE[0];
   float d1 = st.e[1] < 0.f ? 0.f : dE[1];
   float d2 = st.e[2] < 0.f ? 0.f : dE[2];
@@ -526,7 +528,7 @@ __device__ __forceinline__ void add_view_gradient(const ngs_gaussians& g, const 
       gsh[3 * k + 1] = d1 * st.Y[k];
       gsh[3 * k + 2] = d2 * st.Y[k];
     }
-    store_sh<K, VEC>(out.d_sh + (int64_t)i * K * 3, gsh);
+    store_sh<K, VEC>(dsh_dst, gsh);
   } else {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -552,47 +554,82 @@ __device__ __forceinline__ void add_view_gradient(const ngs_gaussians& g, const 
 // One thread per Gaussian; MULTI: loop over the views of a batch (records v n + i), else the one view
 // `cam0`, passed by value so that its entries are constant-bank operands rather than registers.
 // Culled splats (no tile) contribute nothing; a Gaussian culled in every view gets zeros.
-// One view: at most ~96 registers (5 CTAs per SM) -- the occupancy that hides this kernel's memory latency
-// best (a sweep of 3..8 CTAs per SM on GB300: 0.35 / 0.32 / 0.31 / 0.33 / 0.34 / 0.41 ms per 4 calls).
+// One view: at most 128 registers (4 CTAs per SM). Without the SH staging below, 5 CTAs per SM hid the
+// memory latency best (a sweep of 3..8 on GB300: 0.35 / 0.32 / 0.31 / 0.33 / 0.34 / 0.41 ms per 4 calls);
+// with it, 4 CTAs per SM take 0.285 ms, while 5 spill and take 0.39.
 template <int DEG, bool VEC, bool MULTI>
-__global__ void __launch_bounds__(128, MULTI ? 1 : 5) project_backward_kernel(ngs_gaussians g, const ViewParams* __restrict__ views,
+__global__ void __launch_bounds__(128, MULTI ? 1 : 4) project_backward_kernel(ngs_gaussians g, const ViewParams* __restrict__ views,
                                                                CamParams cam0, RenderParams rp,
                                                                const uint32_t* tile_count, const float4* grad2d,
                                                                ngs_grads out) {
   constexpr int K = (DEG + 1) * (DEG + 1);
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.n) return;
-  ParamGrad<DEG> acc;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) acc.m[k] = acc.ls[k] = 0.f;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) acc.q[k] = 0.f;
-  acc.op = 0.f;
-#pragma unroll
-  for (int k = 0; k < 3 * K; ++k) acc.sh[k] = 0.f;
-  if constexpr (!MULTI) {
-    if (tile_count[i] != 0) {
-      add_view_gradient<DEG, VEC, true>(g, cam0, rp, i, grad2d + 3 * (int64_t)i, acc, out);
-      return;
+  // One view with 16-byte SH rows: each warp moves its 32 Gaussians' SH blocks (contiguous in memory)
+  // between global and shared memory with coalesced 16-byte accesses; each thread then reads its
+  // coefficients and writes its SH gradient there (row stride Q + 1 float4 against bank conflicts).
+  constexpr bool kStage = VEC && !MULTI;
+  constexpr int Q = VEC ? 3 * K / 4 : 1;  // float4 per Gaussian
+  __shared__ float4 s_sh[kStage ? 128 * (Q + 1) : 1];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + warp * 32;  // first Gaussian of the warp
+  const int64_t left = g.n - g0;
+  const int warp_n = left <= 0 ? 0 : (left >= 32 ? 32 : (int)left);
+  float4* my_sh = kStage ? &s_sh[threadIdx.x * (Q + 1)] : nullptr;
+  if constexpr (kStage) {
+    const float4* src = reinterpret_cast<const float4*>(g.sh) + g0 * Q;
+    for (int idx = lane; idx < warp_n * Q; idx += 32) {
+      const int j = idx / Q;
+      s_sh[(warp * 32 + j) * (Q + 1) + (idx - j * Q)] = src[idx];
     }
-  } else {
-    for (int v = 0; v < (int)rp.n_views; ++v) {
-      const int64_t r = (int64_t)v * g.n + i;
-      if (tile_count[r] == 0) continue;
-      const CamParams cam = views[v].cam;
-      add_view_gradient<DEG, VEC, false>(g, cam, rp, i, grad2d + 3 * r, acc, out);
+    __syncwarp();
+  }
+  if (i < g.n) {
+    ParamGrad<DEG> acc;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc.m[k] = acc.ls[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc.q[k] = 0.f;
+    acc.op = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3 * K; ++k) acc.sh[k] = 0.f;
+    bool written = false;
+    if constexpr (!MULTI) {
+      if (tile_count[i] != 0) {
+        const float* sh_src = kStage ? reinterpret_cast<const float*>(my_sh) : g.sh + (int64_t)i * K * 3;
+        float* dsh_dst = kStage ? reinterpret_cast<float*>(my_sh) : out.d_sh + (int64_t)i * K * 3;
+        add_view_gradient<DEG, VEC, true>(g, cam0, rp, i, grad2d + 3 * (int64_t)i, acc, out, sh_src, dsh_dst);
+        written = true;
+      }
+    } else {
+      for (int v = 0; v < (int)rp.n_views; ++v) {
+        const int64_t r = (int64_t)v * g.n + i;
+        if (tile_count[r] == 0) continue;
+        const CamParams cam = views[v].cam;
+        add_view_gradient<DEG, VEC, false>(g, cam, rp, i, grad2d + 3 * r, acc, out, g.sh + (int64_t)i * K * 3,
+                                           nullptr);
+      }
+    }
+    if (!written) {  // the sums over views (or zeros: culled in every view)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        out.d_means[3 * (int64_t)i + k] = acc.m[k];
+        out.d_log_scales[3 * (int64_t)i + k] = acc.ls[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) out.d_quats[4 * (int64_t)i + k] = acc.q[k];
+      out.d_opacity_logits[i] = acc.op;
+      if constexpr (kStage) store_sh<K, VEC>(reinterpret_cast<float*>(my_sh), acc.sh);
+      else store_sh<K, VEC>(out.d_sh + (int64_t)i * K * 3, acc.sh);
     }
   }
-  // the sums over views (or zeros: culled in every view)
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    out.d_means[3 * (int64_t)i + k] = acc.m[k];
-    out.d_log_scales[3 * (int64_t)i + k] = acc.ls[k];
+  if constexpr (kStage) {
+    __syncwarp();
+    float4* dst = reinterpret_cast<float4*>(out.d_sh) + g0 * Q;
+    for (int idx = lane; idx < warp_n * Q; idx += 32) {
+      const int j = idx / Q;
+      dst[idx] = s_sh[(warp * 32 + j) * (Q + 1) + (idx - j * Q)];
+    }
   }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) out.d_quats[4 * (int64_t)i + k] = acc.q[k];
-  out.d_opacity_logits[i] = acc.op;
-  store_sh<K, VEC>(out.d_sh + (int64_t)i * K * 3, acc.sh);
 }
 
 }  // namespace
