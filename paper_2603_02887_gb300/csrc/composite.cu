@@ -360,14 +360,15 @@ __device__ __forceinline__ void warp_reduce9_add(const float (&v)[9], float* dst
     atomicAdd(dst + 8, e);
 }
 
-// One list entry for one pixel of the replay: adds the pixel's contributions to v (the 9 per-splat sums)
-// and returns whether the splat was composited at this pixel.
+// One list entry for one pixel of the replay: adds the pixel's contributions to the per-splat sums that
+// do not involve dx (v[1], v[4..8]; the caller forms the dx moments once for the column) and returns
+// whether the splat was composited at this pixel.
 template <int KIND>
-__device__ __forceinline__ bool bwd_step(BwdPixel& p, float4 r0, float4 r1, const float& e2, uint32_t pos,
-                                         const RenderParams& rp, float (&v)[9]) {
+__device__ __forceinline__ bool bwd_step(BwdPixel& p, float dx, float adx, float4 r0, float4 r1, const float& e2,
+                                         uint32_t pos, const RenderParams& rp, float (&v)[9]) {
   if (pos >= p.last) return false;
-  float dx, dy;
-  float e = splat_log2_alpha(p.px, p.py, r0, r1, dx, dy);
+  float dy;
+  float e = splat_log2_alpha_col(dx, adx, p.py, r0, r1, dy);
   if (e < rp.log2_alpha_min) return false;
   float raw = fast_exp2(e);
   float alpha = fminf(rp.alpha_max, raw);
@@ -385,7 +386,7 @@ __device__ __forceinline__ bool bwd_step(BwdPixel& p, float4 r0, float4 r1, cons
     } else {
       const float gd = gE - p.gEk;
       p.gBi = fmaf(gd, __fmul_rn(alpha, p.P), p.gBi);
-      dLda = fmaf(gd, __fmaf_rn(rp.c, p.P, rp.c1), -rp.c * (p.gB - p.gBi) * __frcp_rn(1.0f - alpha));
+      dLda = fmaf(gd, __fmaf_rn(rp.c, p.P, rp.c1), -rp.c * (p.gB - p.gBi) * fast_rcp(1.0f - alpha));
       wE = pt;
       p.S = Sn;
       p.P = __fmul_rn(p.P, __fsub_rn(1.0f, alpha));
@@ -400,7 +401,7 @@ __device__ __forceinline__ bool bwd_step(BwdPixel& p, float4 r0, float4 r1, cons
       } else {
         pe = alpha * p.T;
         p.gacc = fmaf(gE, pe, p.gacc);
-        dexp = fmaf(p.T, gE, -__frcp_rn(1.0f - alpha) * (p.gL0 - p.gacc));
+        dexp = fmaf(p.T, gE, -fast_rcp(1.0f - alpha) * (p.gL0 - p.gacc));
         p.T = testT;
       }
     }
@@ -438,7 +439,7 @@ __device__ __forceinline__ bool bwd_step(BwdPixel& p, float4 r0, float4 r1, cons
     // g.dL0/dalpha_i = T_i g.E_i - (g.L0 - g.sum_{j<=i} E_j pbar_j) / (1 - alpha_i)
     wE = alpha * p.T;
     p.gacc = fmaf(gE, wE, p.gacc);
-    dLda = fmaf(p.T, gE, -__frcp_rn(1.0f - alpha) * (p.gL0 - p.gacc));
+    dLda = fmaf(p.T, gE, -fast_rcp(1.0f - alpha) * (p.gL0 - p.gacc));
     p.T = __fmul_rn(p.T, __fsub_rn(1.0f, alpha));
   }
   // alpha = 2^e with e = L + dx (A' dx + B' dy) + C' dy^2, unless clamped at alpha_max. With
@@ -446,11 +447,8 @@ __device__ __forceinline__ bool bwd_step(BwdPixel& p, float4 r0, float4 r1, cons
   // de/dv = -(B' dx + 2C' dy): the per-splat sums of w, w dx, w dy, w dx^2, w dx dy, w dy^2 carry
   // everything; the projection backward applies the per-splat A', B', C' (and ln 2) once.
   float wgt = raw >= rp.alpha_max ? 0.f : dLda * alpha;  // dL/de / ln 2
-  float wdx = wgt * dx, wdy = wgt * dy;
-  v[0] += wdx;
+  float wdy = wgt * dy;
   v[1] += wdy;
-  v[2] = fmaf(wdx, dx, v[2]);
-  v[3] = fmaf(wdx, dy, v[3]);
   v[4] = fmaf(wdy, dy, v[4]);
   v[5] += wgt;
   v[6] = fmaf(p.g0, wE, v[6]);
@@ -529,9 +527,15 @@ __device__ __forceinline__ void backward_tile(const float4* __restrict__ rec, co
       for (int j = 0; j < cnt; ++j) {
         const uint32_t pos = base + j;
         const float4 r0 = sb.r0[j], r1 = sb.r1[j];
+        // both pixels of the thread lie in one column: dx and A' dx are shared, and the dx moments
+        // follow from the others (sum w dx = dx sum w, sum w dx^2 = dx^2 sum w, sum w dx dy = dx sum w dy)
+        const float dx = __fsub_rn(p[0].px, r0.x), adx = __fmul_rn(r0.z, dx);
         float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        bool on = bwd_step<KIND>(p[0], r0, r1, sb.e2[j], pos, rp, v);
-        on |= bwd_step<KIND>(p[1], r0, r1, sb.e2[j], pos, rp, v);
+        bool on = bwd_step<KIND>(p[0], dx, adx, r0, r1, sb.e2[j], pos, rp, v);
+        on |= bwd_step<KIND>(p[1], dx, adx, r0, r1, sb.e2[j], pos, rp, v);
+        v[0] = dx * v[5];
+        v[2] = dx * v[0];
+        v[3] = dx * v[1];
         const uint32_t mask = __ballot_sync(kFull, on);
         if (mask) {
           float4* dst = grad2d + 3 * (size_t)s_id[j];

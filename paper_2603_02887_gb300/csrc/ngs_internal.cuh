@@ -150,13 +150,28 @@ __device__ __forceinline__ float fast_exp2(float x) {
   return y;
 }
 
-// log2 of aleph * K(p) for the splat (r0, r1) at pixel centre (px, py); FP32, fixed operation order.
-__device__ __forceinline__ float splat_log2_alpha(float px, float py, float4 r0, float4 r1, float& dx, float& dy) {
-  dx = __fsub_rn(px, r0.x);
+// Approximate reciprocal (PTX rcp.approx, within 1 ulp): only where the value feeds a gradient, never a
+// compositing decision.
+__device__ __forceinline__ float fast_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// log2 of aleph * K(p) for the splat (r0, r1) at pixel row py, given dx = px - u and adx = A' dx of the
+// pixel's column (so pixels of one column share them); FP32, fixed operation order.
+__device__ __forceinline__ float splat_log2_alpha_col(float dx, float adx, float py, float4 r0, float4 r1,
+                                                      float& dy) {
   dy = __fsub_rn(py, r0.y);
-  float t = __fmaf_rn(r0.w, dy, __fmul_rn(r0.z, dx));
+  float t = __fmaf_rn(r0.w, dy, adx);
   float q = __fmaf_rn(dx, t, __fmul_rn(__fmul_rn(r1.x, dy), dy));
   return __fadd_rn(r1.y, q);
+}
+
+// log2 of aleph * K(p) for the splat (r0, r1) at pixel centre (px, py); the same arithmetic.
+__device__ __forceinline__ float splat_log2_alpha(float px, float py, float4 r0, float4 r1, float& dx, float& dy) {
+  dx = __fsub_rn(px, r0.x);
+  return splat_log2_alpha_col(dx, __fmul_rn(r0.z, dx), py, r0, r1, dy);
 }
 
 // Quadratic slope term alpha (1 + c taubar), clamped at 0 (Table 1 with the [.]_+ of T).
