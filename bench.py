@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--chunk", type=int, default=None, help="records staged per round (default: autotuned)")
     p.add_argument("--schedule", default=None, choices=["tiles", "persistent"], help="(default: autotuned)")
     p.add_argument("--no-graphs", action="store_true", help="launch the render phases directly")
+    p.add_argument("--streams", type=int, default=2,
+                   help="renderer contexts, each on its own stream; the models take them in turn, so that one "
+                        "model's kernels run while the host waits for another's pair count")
     p.add_argument("--no-batched", action="store_true", help="skip the batched multi-view measurement")
     p.add_argument("--batched-gaussians", type=int, default=3_000_000)
     p.add_argument("--batched-views", type=int, default=32)
@@ -176,7 +179,11 @@ def run_ours(args):
     params = {k: torch.from_numpy(np.ascontiguousarray(scene[k])).to(dev) for k in PARAM_KEYS}
     r = Renderer(dev)
     opts, tuning = launch_options(args, r, params, [cam])
-    frames = {m: r.frame() for m in MODELS}
+    S = max(1, args.streams)
+    rs = [r] + [Renderer(dev) for _ in range(S - 1)]
+    streams = [torch.cuda.current_stream()] + [torch.cuda.Stream(dev) for _ in range(S - 1)]
+    owner = {m: i % S for i, m in enumerate(MODELS)}
+    frames = {m: rs[owner[m]].frame() for m in MODELS}
     images = {m: torch.empty((H, W, 3), device=dev) for m in MODELS}
     ods = {m: torch.empty((H, W), dtype=torch.int32, device=dev) for m in MODELS}
     grads = {m: {"d_" + k: torch.empty_like(params[k]) for k in PARAM_KEYS} for m in MODELS}
@@ -186,25 +193,41 @@ def run_ours(args):
     dl = {}
     for m in MODELS:
         tgt, _, f = r.render(target_params, cam, m, opts[m])
-        img, _, _ = r.render(params, cam, m, opts[m], frame=frames[m], image=images[m], overdraw=ods[m])
+        img, _, _ = rs[owner[m]].render(params, cam, m, opts[m], frame=frames[m], image=images[m], overdraw=ods[m])
         dl[m] = torch.sign(img - tgt).contiguous()
         r.recycle(f)
     del target_params
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step(per_model_events=None):
-        for m in MODELS:
-            ev = per_model_events[m] if per_model_events is not None else None
-            if ev:
-                ev[0].record()
-            r.render(params, cam, m, opts[m], frame=frames[m], image=images[m], overdraw=ods[m])
-            if ev:
-                ev[1].record()
-            r.backward(frames[m], params, dl[m], out=grads[m])
-            if ev:
-                ev[2].record()
+    main = streams[0]
 
-    r.set_graphs(not args.no_graphs)
+    def step(per_model_events=None, serial=False):
+        # every stream starts after what the main stream holds, and the main stream ends after all of them;
+        # serial: each model also waits for the one before (no overlap, for the per-stage breakdown)
+        for st in streams[1:]:
+            st.wait_stream(main)
+        for m in MODELS:
+            k = owner[m]
+            rr = rs[k]
+            if serial:
+                streams[k].wait_stream(main)
+            with torch.cuda.stream(streams[k]):
+                ev = per_model_events[m] if per_model_events is not None else None
+                if ev:
+                    ev[0].record()
+                rr.render(params, cam, m, opts[m], frame=frames[m], image=images[m], overdraw=ods[m])
+                if ev:
+                    ev[1].record()
+                rr.backward(frames[m], params, dl[m], out=grads[m])
+                if ev:
+                    ev[2].record()
+            if serial:
+                main.wait_stream(streams[k])
+        for st in streams[1:]:
+            main.wait_stream(st)
+
+    for x in rs:
+        x.set_graphs(not args.no_graphs)
     for _ in range(args.warmup):
         flush.zero_()
         step()
@@ -215,9 +238,10 @@ def run_ours(args):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     model_ev = [{m: [torch.cuda.Event(enable_timing=True) for _ in range(3)] for m in MODELS} for _ in range(K)]
-    r.set_timing(True)
-    r.reset_stage_times()
-    launches0 = r.launch_count()
+    if S == 1:
+        r.set_timing(True)
+        r.reset_stage_times()
+    launches0 = sum(x.launch_count() for x in rs)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)  # nvidia-smi's first samples
@@ -237,23 +261,41 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    launches = r.launch_count() - launches0
-    stage = r.stage_times()
-    r.set_timing(False)
-    # replayed graph phases carry no stage events: the forward stages come from two more steps with direct
-    # launches (the backward stages, the dominant ones, are the timed region's own)
-    stage_direct = stage
-    if not args.no_graphs:
-        r.set_graphs(False)
-        r.set_timing(True)
-        r.reset_stage_times()
-        for _ in range(2):
+    launches = sum(x.launch_count() for x in rs) - launches0
+
+    def stage_steps(n, graphs):
+        # per-stage CUDA-event times of n further steps, models one after another
+        for x in rs:
+            x.set_graphs(graphs)
+            x.set_timing(True)
+            x.reset_stage_times()
+        for _ in range(n):
             flush.zero_()
-            step()
+            step(serial=True)
         torch.cuda.synchronize()
-        stage_direct = r.stage_times()
+        out = {}
+        for x in rs:
+            for k, v in x.stage_times().items():
+                out[k] = [a + b for a, b in zip(out[k], v)] if k in out else list(v)
+            x.set_timing(False)
+            x.set_graphs(not args.no_graphs)
+        return out
+
+    # Stage events: replayed graph phases carry none, so the forward stages come from two more steps with
+    # direct launches. With one stream the backward stages (the dominant ones) are the timed region's own;
+    # with several, overlapping kernels would inflate each other's event times, so they come from K more
+    # steps with the models one after another.
+    if S == 1:
+        stage = r.stage_times()
         r.set_timing(False)
-        r.set_graphs(not args.no_graphs)
+        stage_source = ("timed region" if args.no_graphs else
+                        "backward stages: timed region; forward stages: 2 further steps with direct launches")
+    else:
+        stage = stage_steps(K, not args.no_graphs)
+        stage_source = (f"{K} further steps with the models one after another" if args.no_graphs else
+                        f"backward stages: {K} further steps with the models one after another; "
+                        "forward stages: 2 further such steps with direct launches")
+    stage_direct = stage if args.no_graphs else stage_steps(2, False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = max_over_ranks(sum(step_ms), device=dev)
     ms_per_step = total_ms / K
@@ -293,18 +335,20 @@ def run_ours(args):
                    "launch_options": {m: {k: opts[m][k] for k in ("tile_w", "tile_h", "chunk", "schedule")}
                                       for m in MODELS},
                    "launch_options_source": tuning, "cuda_graphs": not args.no_graphs,
+                   "streams": S,
                    "step": "per model: render + path-replay backward",
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"views x{world}",
                    "pairs_per_view": int(frames["exp"].view()["n_pairs"])},
         "per_model": per_model,
         "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
-        "stage_ms_source": ("timed region" if args.no_graphs else
-                            "backward stages: timed region; forward stages: 2 further steps with direct launches"),
+        "stage_ms_source": stage_source,
         "gpu_launches": int(launches), "gpu_launches_per_step": round(launches / K, 1),
         "roofline": roof, "clocks": clk,
     }
     if not args.no_e2e:
-        line["e2e"] = run_e2e(args, r, scene, cam, opts, dl, dev, world)
+        line["e2e"] = run_e2e(args, rs, streams, owner, scene, cam, opts, dl, dev, world)
+    for x in rs[1:]:
+        x.close()
     if world == 1 and not (args.no_batched and args.no_serving and args.no_training):
         del params, frames, grads
     if not args.no_batched and world == 1:
@@ -583,11 +627,12 @@ def run_training(args, r, dev):
     return out
 
 
-def run_e2e(args, r, scene, cam, opts, dl, dev, world):
+def run_e2e(args, rs, streams, owner, scene, cam, opts, dl, dev, world):
     """Same metric through the public API with host buffers: each step copies the parameters and the
-    upstream gradients from pinned host memory, renders + backpropagates every model, and reads the
-    images, overdraw maps and gradients back to pinned host memory (on a second stream, overlapping the
-    next model's kernels; the timed region ends after the last read)."""
+    upstream gradients from pinned host memory, renders + backpropagates every model (on the renderer
+    contexts and streams of the device-timed step), and reads the images, overdraw maps and gradients back
+    to pinned host memory (on one more stream, overlapping the next model's kernels; the timed region ends
+    after the last read)."""
     import torch
 
     from paper_2603_02887_gb300.render import PARAM_KEYS
@@ -600,11 +645,11 @@ def run_e2e(args, r, scene, cam, opts, dl, dev, world):
     out_img = {m: torch.empty((H, W, 3)).pin_memory() for m in MODELS}
     out_od = {m: torch.empty((H, W), dtype=torch.int32).pin_memory() for m in MODELS}
     out_g = {m: {k: torch.empty(v.shape).pin_memory() for k, v in host.items()} for m in MODELS}
-    frames = {m: r.frame() for m in MODELS}
+    frames = {m: rs[owner[m]].frame() for m in MODELS}
     h2d = sum(v.numel() * 4 for v in host.values()) + sum(v.numel() * 4 for v in host_dl.values())
     d2h = sum(H * W * 16 + sum(v.numel() * 4 for v in host.values()) for _ in MODELS)
 
-    main = torch.cuda.current_stream()
+    main = streams[0]
     copy = torch.cuda.Stream()  # device-to-host reads of a model's results overlap the next model's kernels
     dev_img = {m: torch.empty((H, W, 3), device=dev) for m in MODELS}
     dev_od = {m: torch.empty((H, W), dtype=torch.int32, device=dev) for m in MODELS}
@@ -613,16 +658,23 @@ def run_e2e(args, r, scene, cam, opts, dl, dev, world):
     def step():
         for k in PARAM_KEYS:
             dev_p[k].copy_(host[k], non_blocking=True)
+        for st in streams[1:]:
+            st.wait_stream(main)
         for m in MODELS:
-            dev_dl[m].copy_(host_dl[m], non_blocking=True)
-            img, od, f = r.render(dev_p, cam, m, opts[m], frame=frames[m], image=dev_img[m], overdraw=dev_od[m])
-            g = r.backward(f, dev_p, dev_dl[m], out=dev_g[m])
-            copy.wait_stream(main)
+            st = streams[owner[m]]
+            with torch.cuda.stream(st):
+                dev_dl[m].copy_(host_dl[m], non_blocking=True)
+                img, od, f = rs[owner[m]].render(dev_p, cam, m, opts[m], frame=frames[m], image=dev_img[m],
+                                                 overdraw=dev_od[m])
+                g = rs[owner[m]].backward(f, dev_p, dev_dl[m], out=dev_g[m])
+            copy.wait_stream(st)
             with torch.cuda.stream(copy):
                 out_img[m].copy_(img, non_blocking=True)
                 out_od[m].copy_(od, non_blocking=True)
                 for k in PARAM_KEYS:
                     out_g[m][k].copy_(g["d_" + k], non_blocking=True)
+        for st in streams[1:]:
+            main.wait_stream(st)
         main.wait_stream(copy)  # the next step overwrites the buffers these copies read
 
     for _ in range(max(1, args.warmup)):
@@ -636,8 +688,8 @@ def run_e2e(args, r, scene, cam, opts, dl, dev, world):
     e.record()  # after main has waited for the last copies
     torch.cuda.synchronize()
     ms = s.elapsed_time(e) / K
-    for f in frames.values():
-        r.recycle(f)
+    for m, f in frames.items():
+        rs[owner[m]].recycle(f)
     return {"value": round(world * len(MODELS) * W * H / (ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
             "ms_per_step": round(ms, 3), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": K}
 
