@@ -63,6 +63,24 @@ void stage_end(ngs_ctx* ctx, cudaStream_t s, int stage, cudaEvent_t start, int l
   ctx->pending.push_back({start, b, stage});
 }
 
+// Host <-> device traffic of a render without the copy engines: a render would otherwise wait for its
+// view table and its pair count behind whatever bulk copies other streams have queued on the engines.
+// The view table is read by a kernel from mapped pinned memory over the host link...
+__global__ void copy_words_kernel(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, uint32_t n) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+// ... and the scalars the host reads back (the pair count and the error word, loss sums, a densified count)
+// are written by a kernel into the context's mapped pinned mirror, read after synchronising with the stream.
+__global__ void publish_words_kernel(const uint64_t* __restrict__ src, uint64_t* dst, int n) {
+  if ((int)threadIdx.x < n) dst[threadIdx.x] = src[threadIdx.x];
+  __threadfence_system();
+}
+
+void publish_words(ngs_ctx* ctx, const uint64_t* src, int n, int slot, cudaStream_t s) {
+  publish_words_kernel<<<1, 32, 0, s>>>(src, ctx->d_h_total + slot, n);
+}
+
 static void free_buf(DevBuf& b) {
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
@@ -177,11 +195,15 @@ static int stage_views(ngs_ctx* ctx, ngs_frame* f) {
     if (f->h_views) cudaFreeHost(f->h_views);
     f->h_views = nullptr;
     f->h_views_cap = 0;
-    if (cudaMallocHost((void**)&f->h_views, bytes) != cudaSuccess) {
+    void* dev_alias = nullptr;
+    if (cudaHostAlloc((void**)&f->h_views, bytes, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(&dev_alias, f->h_views, 0) != cudaSuccess) {
       cudaGetLastError();
+      if (f->h_views) cudaFreeHost(f->h_views);
       f->h_views = nullptr;
-      return fail(ctx, NGS_ERR_OUT_OF_MEMORY, "pinned allocation of the view table failed");
+      return fail(ctx, NGS_ERR_OUT_OF_MEMORY, "mapped pinned allocation of the view table failed");
     }
+    f->d_h_views = static_cast<const uint32_t*>(dev_alias);
     f->h_views_cap = f->view_host.size();
   }
   NGS_TRY(ensure(ctx, f->views, bytes));
@@ -204,14 +226,19 @@ struct RenderPlan {
 static void phase1(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, cudaStream_t s) {
   const RenderParams& rp = pl.rp;
   const ViewParams* views = f->views.as<ViewParams>();
-  cudaMemcpyAsync(f->views.p, f->h_views, sizeof(ViewParams) * f->view_host.size(), cudaMemcpyHostToDevice, s);
   cudaEvent_t ev;
-  // 1. projection of every (view, Gaussian): splat records, FP32 depth keys (all-ones for splats that take
-  //    no tile), tile counts
+  // 1. the view table to the device; projection of every (view, Gaussian): splat records, FP32 depth keys
+  //    (all-ones for splats that take no tile), tile counts
   stage_begin(ctx, s, 0, &ev);
+  {
+    static_assert(sizeof(ViewParams) % 4 == 0, "the view table is copied in 4-byte words");
+    const uint32_t words = (uint32_t)(sizeof(ViewParams) * f->view_host.size() / 4);
+    copy_words_kernel<<<std::min((words + 255) / 256, 64u), 256, 0, s>>>(f->d_h_views, f->views.as<uint32_t>(),
+                                                                          words);
+  }
   launch_project(*pl.g, views, f->view_host[0].cam, rp, f->rec.as<float4>(), f->gkeys[0].as<uint32_t>(),
                  f->tile_count.as<uint32_t>(), f->gvals[0].as<uint32_t>(), s);
-  stage_end(ctx, s, 0, ev, pl.n ? 1 : 0);
+  stage_end(ctx, s, 0, ev, pl.n ? 2 : 1);
   // 2. stable sort of each view's splats by FP32 depth (ties keep Gaussian order)
   stage_begin(ctx, s, 1, &ev);
   int launches = 0;
@@ -227,8 +254,8 @@ static void phase1(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, cudaStream_
   launch_scan_counts(f->tile_count.as<uint32_t>(), f->gvals[f->g_final].as<uint32_t>(), pl.R,
                      f->offsets.as<uint32_t>(), ctx->scan_tmp.as<uint64_t>(), ctx->total.as<uint64_t>(), s,
                      &launches);
-  cudaMemcpyAsync(ctx->h_total, ctx->total.p, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
-  stage_end(ctx, s, 2, ev, launches);
+  publish_words(ctx, ctx->total.as<uint64_t>(), 2, kMirrorTotal, s);
+  stage_end(ctx, s, 2, ev, launches + 1);
 }
 
 // Phase 2: key emission, tile sort, tile ranges (+ work list), composite. `cap` items are covered by the
@@ -485,12 +512,13 @@ int ngs::render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, co
   cudaError_t e = cudaEventRecord(f->views_uploaded, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("reading the pair count: ") + cudaGetErrorString(e));
-  if (ctx->h_total[1] != 0) {  // a bounds check fired in an earlier call on this context
+  const volatile uint64_t* mirror = ctx->h_total + kMirrorTotal;  // written by publish_words
+  if (mirror[1] != 0) {  // a bounds check fired in an earlier call on this context
     cudaMemsetAsync(ctx->total.as<uint64_t>() + 1, 0, sizeof(uint64_t), s);
     return fail(ctx, NGS_ERR_DEVICE_CHECK, "a kernel bounds check fired in an earlier call on this context; its "
                                            "output was not valid");
   }
-  const uint64_t P = *ctx->h_total;
+  const uint64_t P = mirror[0];
   if (P >= (1ull << 31)) return fail(ctx, NGS_ERR_INVALID_ARG, "more than 2^31 (tile, Gaussian) pairs");
   const uint32_t np = (uint32_t)P;
   if (admit) NGS_TRY(admit(admit_user, 1, sizeof(uint32_t) * 4 * (size_t)np));
@@ -556,9 +584,11 @@ NGS_API int ngs_create(ngs_ctx** out) {
   if (!ctx) return NGS_ERR_OUT_OF_MEMORY;
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_total, 2 * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&ctx->h_total, kMirrorWords * sizeof(uint64_t), cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&ctx->d_h_total, ctx->h_total, 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    if (ctx->h_total) cudaFreeHost(ctx->h_total);
     delete ctx;
     return NGS_ERR_CUDA;
   }

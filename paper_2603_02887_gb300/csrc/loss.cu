@@ -11,6 +11,7 @@
 // divided by the 3 H W terms of the mean. Four separable passes: horizontal moments, vertical moments +
 // per-pixel s / a / b / c (+ the L1 term), horizontal a / b / c, vertical a / b / c + the gradient.
 #include <math.h>
+#include <string.h>
 
 #include "ngs_internal.cuh"
 
@@ -202,11 +203,16 @@ extern "C" NGS_API int ngs_loss_l1_ssim(ngs_ctx* ctx, const float* image, const 
   ctx->launches += launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("loss launch: ") + cudaGetErrorString(e));
-  if (loss_out) {  // one synchronisation: the scalar loss to the host
-    double h[2];
-    e = cudaMemcpyAsync(h, sums, sizeof h, cudaMemcpyDeviceToHost, s);
+  if (loss_out) {  // one synchronisation: the scalar loss to the host (through the mapped mirror)
+    publish_words(ctx, reinterpret_cast<const uint64_t*>(sums), 2, kMirrorLoss, s);
+    ctx->launches += 1;
+    e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("loss read-back: ") + cudaGetErrorString(e));
+    const volatile uint64_t* mirror = ctx->h_total + kMirrorLoss;
+    const uint64_t w[2] = {mirror[0], mirror[1]};
+    double h[2];
+    memcpy(h, w, sizeof h);
     const double n = 3.0 * (double)npix;
     loss_out[0] = (1.0 - lambda) * (h[1] / n) + lambda * (1.0 - h[0] / n);
     loss_out[1] = h[1] / n;  // L1

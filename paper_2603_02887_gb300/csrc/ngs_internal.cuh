@@ -206,7 +206,9 @@ struct ngs_ctx {
   ngs::DevBuf flush;     // autotuner: scratch cleared between timed calls to evict L2
   ngs::DevBuf loss_tmp;  // image loss: moment and partial-derivative planes
   ngs::DevBuf densify_tmp, densify_totals;  // split / prune decisions, scans and totals
-  uint64_t* h_total = nullptr;  // pinned mirror of `total` (2 words)
+  uint64_t* h_total = nullptr;    // pinned, mapped mirror of the scalars read back (kMirrorWords words),
+                                  // written by publish_words
+  uint64_t* d_h_total = nullptr;  // its device-side address
   bool timing = false;
   struct Pending { cudaEvent_t a, b; int stage; };
   std::vector<Pending> pending;
@@ -240,7 +242,8 @@ struct ngs_frame {
   std::vector<ngs::ViewParams> view_host;  // the views of the last render (host copy)
   std::vector<int64_t> pix_base;           // [n_views + 1]
   std::vector<uint32_t> tile_base;         // [n_views + 1]
-  ngs::ViewParams* h_views = nullptr;      // pinned staging of the view table
+  ngs::ViewParams* h_views = nullptr;      // pinned, mapped staging of the view table
+  const uint32_t* d_h_views = nullptr;     // its device-side address
   size_t h_views_cap = 0;
   cudaEvent_t views_uploaded = nullptr;    // recorded after the last upload from h_views
   ngs::DevBuf views;                       // device view table
@@ -279,6 +282,11 @@ int check_model(ngs_ctx* ctx, const ngs_model* model);
 // error / allocation helpers (api.cu)
 int fail(ngs_ctx* ctx, int code, const std::string& msg);
 int ensure(ngs_ctx* ctx, DevBuf& b, size_t bytes);
+// Slots of the context's mapped mirror: the pair count and the device error word of the last render, the
+// loss sums (two doubles), the densified Gaussian count.
+constexpr int kMirrorTotal = 0, kMirrorLoss = 2, kMirrorDensify = 4, kMirrorWords = 8;
+// Copy n (<= 32) 64-bit device words into mirror slots [slot, slot + n) with one kernel on stream s.
+void publish_words(ngs_ctx* ctx, const uint64_t* src, int n, int slot, cudaStream_t s);
 void stage_begin(ngs_ctx* ctx, cudaStream_t s, int stage, cudaEvent_t* out);
 void stage_end(ngs_ctx* ctx, cudaStream_t s, int stage, cudaEvent_t start, int launches);
 

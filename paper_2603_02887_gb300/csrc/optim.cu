@@ -299,12 +299,12 @@ NGS_API int ngs_densify(ngs_ctx* ctx, int64_t n, int32_t sh_degree, const ngs_gr
   densify_apply_kernel<<<blocks, 256, 0, s>>>(da, outc, pos, n);
   launches += 1;
   ctx->launches += launches;
-  uint64_t h = 0;
+  publish_words(ctx, &totals[2], 1, kMirrorDensify, s);  // the new count, through the mapped mirror
+  ctx->launches += 1;
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, &totals[2], sizeof h, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("densify: ") + cudaGetErrorString(e));
-  *n_out = (int64_t)h;
+  *n_out = (int64_t)static_cast<volatile uint64_t*>(ctx->h_total)[kMirrorDensify];
   return NGS_OK;
 }
 
