@@ -631,67 +631,109 @@ def run_e2e(args, rs, streams, owner, scene, cam, opts, dl, dev, world):
     """Same metric through the public API with host buffers: each step copies the parameters and the
     upstream gradients from pinned host memory, renders + backpropagates every model (on the renderer
     contexts and streams of the device-timed step), and reads the images, overdraw maps and gradients back
-    to pinned host memory (on one more stream, overlapping the next model's kernels; the timed region ends
-    after the last read)."""
+    to pinned host memory. Steps are pipelined over two sets of buffers: step i + 1's uploads run during
+    step i's kernels, and its kernels while step i's results are read back (one stream uploads, one reads
+    back; both copy directions run at once). The timed region holds every step's uploads and ends after
+    the last step's last read."""
     import torch
 
     from paper_2603_02887_gb300.render import PARAM_KEYS
 
     H, W = cam["height"], cam["width"]
+    NB = 2
     host = {k: torch.from_numpy(np.ascontiguousarray(scene[k])).pin_memory() for k in PARAM_KEYS}
     host_dl = {m: dl[m].cpu().pin_memory() for m in MODELS}
-    dev_p = {k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in host.items()}
-    dev_dl = {m: torch.empty_like(dl[m]) for m in MODELS}
-    out_img = {m: torch.empty((H, W, 3)).pin_memory() for m in MODELS}
-    out_od = {m: torch.empty((H, W), dtype=torch.int32).pin_memory() for m in MODELS}
-    out_g = {m: {k: torch.empty(v.shape).pin_memory() for k, v in host.items()} for m in MODELS}
-    frames = {m: rs[owner[m]].frame() for m in MODELS}
+    sets = []
+    for _ in range(NB):
+        sets.append(dict(
+            p={k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in host.items()},
+            dl={m: torch.empty_like(dl[m]) for m in MODELS},
+            img={m: torch.empty((H, W, 3), device=dev) for m in MODELS},
+            od={m: torch.empty((H, W), dtype=torch.int32, device=dev) for m in MODELS},
+            g={m: {"d_" + k: torch.empty(v.shape, device=dev) for k, v in host.items()} for m in MODELS},
+            out_img={m: torch.empty((H, W, 3)).pin_memory() for m in MODELS},
+            out_od={m: torch.empty((H, W), dtype=torch.int32).pin_memory() for m in MODELS},
+            out_g={m: {k: torch.empty(v.shape).pin_memory() for k, v in host.items()} for m in MODELS},
+            frames={m: rs[owner[m]].frame() for m in MODELS},
+            compute_done=[], reads_done=None, inputs=None))
     h2d = sum(v.numel() * 4 for v in host.values()) + sum(v.numel() * 4 for v in host_dl.values())
     d2h = sum(H * W * 16 + sum(v.numel() * 4 for v in host.values()) for _ in MODELS)
 
     main = streams[0]
-    copy = torch.cuda.Stream()  # device-to-host reads of a model's results overlap the next model's kernels
-    dev_img = {m: torch.empty((H, W, 3), device=dev) for m in MODELS}
-    dev_od = {m: torch.empty((H, W), dtype=torch.int32, device=dev) for m in MODELS}
-    dev_g = {m: {"d_" + k: torch.empty(v.shape, device=dev) for k, v in host.items()} for m in MODELS}
+    up = torch.cuda.Stream()    # host-to-device copies
+    down = torch.cuda.Stream()  # device-to-host copies
 
-    def step():
-        for k in PARAM_KEYS:
-            dev_p[k].copy_(host[k], non_blocking=True)
-        for st in streams[1:]:
-            st.wait_stream(main)
+    def upload(i):
+        # step i's inputs into its set; they overwrite inputs that step i - NB's kernels read
+        b = sets[i % NB]
+        up.wait_stream(main)
+        for ev in b["compute_done"]:
+            up.wait_event(ev)
+        with torch.cuda.stream(up):
+            for k in PARAM_KEYS:
+                b["p"][k].copy_(host[k], non_blocking=True)
+            for m in MODELS:
+                b["dl"][m].copy_(host_dl[m], non_blocking=True)
+        b["inputs"] = torch.cuda.Event()
+        b["inputs"].record(up)
+
+    def step(i, last):
+        b = sets[i % NB]
+        if i + 1 < last:
+            upload(i + 1)  # the next step's uploads run during this step's kernels
+        for st in streams:
+            st.wait_event(b["inputs"])
+            if b["reads_done"] is not None:  # the kernels overwrite outputs that step i - NB's reads copy
+                st.wait_event(b["reads_done"])
         for m in MODELS:
             st = streams[owner[m]]
             with torch.cuda.stream(st):
-                dev_dl[m].copy_(host_dl[m], non_blocking=True)
-                img, od, f = rs[owner[m]].render(dev_p, cam, m, opts[m], frame=frames[m], image=dev_img[m],
-                                                 overdraw=dev_od[m])
-                g = rs[owner[m]].backward(f, dev_p, dev_dl[m], out=dev_g[m])
-            copy.wait_stream(st)
-            with torch.cuda.stream(copy):
-                out_img[m].copy_(img, non_blocking=True)
-                out_od[m].copy_(od, non_blocking=True)
+                img, od, f = rs[owner[m]].render(b["p"], cam, m, opts[m], frame=b["frames"][m], image=b["img"][m],
+                                                 overdraw=b["od"][m])
+                g = rs[owner[m]].backward(f, b["p"], b["dl"][m], out=b["g"][m])
+            down.wait_stream(st)
+            with torch.cuda.stream(down):
+                b["out_img"][m].copy_(img, non_blocking=True)
+                b["out_od"][m].copy_(od, non_blocking=True)
                 for k in PARAM_KEYS:
-                    out_g[m][k].copy_(g["d_" + k], non_blocking=True)
-        for st in streams[1:]:
-            main.wait_stream(st)
-        main.wait_stream(copy)  # the next step overwrites the buffers these copies read
+                    b["out_g"][m][k].copy_(g["d_" + k], non_blocking=True)
+        b["compute_done"] = []
+        for st in streams:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            b["compute_done"].append(ev)
+        b["reads_done"] = torch.cuda.Event()
+        b["reads_done"].record(down)
 
-    for _ in range(max(1, args.warmup)):
-        step()
+    def drain():
+        for st in (*streams, up, down):
+            main.wait_stream(st)
+
+    W0 = max(NB, args.warmup)
+    upload(0)
+    for i in range(W0):
+        step(i, W0)
+    drain()
     torch.cuda.synchronize()
     K = max(3, args.steps // 2)
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s.record()
-    for _ in range(K):
-        step()
-    e.record()  # after main has waited for the last copies
+    s.record(main)
+    for st in (*streams[1:], up, down):
+        st.wait_stream(main)
+    upload(0)  # every step's uploads are inside the timed region
+    for i in range(K):
+        step(i, K)
+    drain()
+    e.record(main)  # after the last reads
     torch.cuda.synchronize()
     ms = s.elapsed_time(e) / K
-    for m, f in frames.items():
-        rs[owner[m]].recycle(f)
+    for b in sets:
+        for m, f in b["frames"].items():
+            rs[owner[m]].recycle(f)
     return {"value": round(world * len(MODELS) * W * H / (ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
-            "ms_per_step": round(ms, 3), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": K}
+            "ms_per_step": round(ms, 3), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": K,
+            "pipelining": f"{NB} buffer sets: a step's uploads overlap the previous step's kernels, its kernels "
+                          "the previous step's reads"}
 
 
 # ---------------------------------------------------------------------------------------------------
