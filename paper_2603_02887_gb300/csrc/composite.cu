@@ -30,6 +30,8 @@
 // shuffles and added to the per-Gaussian buffer with one atomic-add instruction per warp and splat.
 #include <algorithm>
 
+#include <type_traits>
+
 #include "ngs_internal.cuh"
 
 namespace ngs {
@@ -457,6 +459,216 @@ __device__ __forceinline__ bool bwd_step(BwdPixel& p, float dx, float adx, float
   return true;
 }
 
+// ---- backward, packed form (exponential and quadratic) -----------------------------------------------
+//
+// The thread's two pixels (x, y) and (x, y + 4) step through each list entry together in FP32x2
+// instructions (add / mul / fma .f32x2, one instruction for both pixels). Each lane rounds exactly like
+// the scalar forward, so alpha and every compositing decision are bit-identical. A pixel that does not
+// composite the entry (past its stop, or alpha < alpha_min) gets alpha = 0, which leaves its running sums
+// exactly as they were and contributes zero.
+
+// Replay staging of one chunk: every per-splat operand duplicated, so one 16-byte shared load gives the
+// operand pairs {a, a, b, b} of two FP32x2 instructions.
+template <int CH>
+struct PairStageBuf {
+  float4 q0[CH];  // {-u, -u, -v, -v}
+  float4 q1[CH];  // {A', A', B', B'}
+  float4 q2[CH];  // {C', C', L, L}
+  float4 q3[CH];  // {E0, E0, E1, E1}
+  float2 q4[CH];  // {E2, E2}
+};
+
+// The packed form is used while its staging (72 B per record) stays within 40 KB of static shared memory.
+template <int KIND, int CH>
+constexpr bool kPairReplay = (KIND == NGS_MODEL_EXP || KIND == NGS_MODEL_QUAD) && sizeof(PairStageBuf<CH>) <= 40960;
+
+template <int B, int CH>
+__device__ __forceinline__ void stage_chunk_pairs(const float4* __restrict__ rec, const uint32_t* __restrict__ ids,
+                                                  const RenderParams& rp, uint32_t base, uint32_t end,
+                                                  PairStageBuf<CH>& sb, uint32_t* s_id) {
+#pragma unroll
+  for (int k = 0; k < (CH + B - 1) / B; ++k) {
+    const int slot = k * B + (int)threadIdx.x;
+    const uint32_t i = base + (uint32_t)slot;
+    if (slot < CH && i < end) {
+      const uint32_t id = ids[i];
+      s_id[slot] = id < rp.n_records ? id : 0u;
+      float4 r0, r1;
+      float e2;
+      stage_record(rec, id, rp, r0, r1, e2);
+      sb.q0[slot] = make_float4(-r0.x, -r0.x, -r0.y, -r0.y);
+      sb.q1[slot] = make_float4(r0.z, r0.z, r0.w, r0.w);
+      sb.q2[slot] = make_float4(r1.x, r1.x, r1.y, r1.y);
+      sb.q3[slot] = make_float4(r1.z, r1.z, r1.w, r1.w);
+      sb.q4[slot] = make_float2(e2, e2);
+    }
+  }
+}
+
+// Both pixels' replay state, lane 0 = pixel (x, y), lane 1 = pixel (x, y + 4).
+struct BwdPair {
+  float2 px, py;
+  uint32_t last0, last1;  // replay entries [range.x, last)
+  float2 g0, g1, g2;
+  float2 T, gacc, gL0;    // exponential: T_i, g.sum_{j<i} E_j pbar_j, g.L0
+  float2 S, tau, nEk, nTh;  // quadratic: S, taubar, -g.E_k, -g.Theta
+};
+
+__device__ __forceinline__ float2 lo_hi(float4 q, bool hi) { return hi ? make_float2(q.z, q.w) : make_float2(q.x, q.y); }
+
+// One list entry for both pixels: adds their contributions to v (the 9 per-splat sums, the dx moments
+// included) and returns whether either pixel composited the splat.
+template <int KIND>
+__device__ __forceinline__ bool bwd_pair_step(BwdPair& p, float4 q0, float4 q1, float4 q2, float4 q3, float2 q4,
+                                              uint32_t pos, const RenderParams& rp, float (&v)[9]) {
+  const float2 one = make_float2(1.f, 1.f), neg = make_float2(-1.f, -1.f);
+  // the quadratic form, as splat_log2_alpha_col computes it per pixel
+  const float2 dx = __fadd2_rn(p.px, lo_hi(q0, false));  // px - u, equal in both lanes
+  const float2 adx = __fmul2_rn(lo_hi(q1, false), dx);
+  const float2 dy = __fadd2_rn(p.py, lo_hi(q0, true));
+  const float2 t = __ffma2_rn(lo_hi(q1, true), dy, adx);
+  const float2 cdd = __fmul2_rn(__fmul2_rn(lo_hi(q2, false), dy), dy);
+  const float2 e = __fadd2_rn(lo_hi(q2, true), __ffma2_rn(dx, t, cdd));
+  const bool on0 = pos < p.last0 && e.x >= rp.log2_alpha_min;
+  const bool on1 = pos < p.last1 && e.y >= rp.log2_alpha_min;
+  if (!(on0 || on1)) return false;
+  const float raw0 = fast_exp2(e.x), raw1 = fast_exp2(e.y);
+  const float2 alpha = make_float2(on0 ? fminf(rp.alpha_max, raw0) : 0.f, on1 ? fminf(rp.alpha_max, raw1) : 0.f);
+  // w = dL/de: zero where alpha is clamped at alpha_max (it no longer depends on e) or not composited
+  bool live0 = on0 && raw0 < rp.alpha_max, live1 = on1 && raw1 < rp.alpha_max;
+  const float2 gE = __ffma2_rn(p.g2, q4, __ffma2_rn(p.g1, lo_hi(q3, true), __fmul2_rn(p.g0, lo_hi(q3, false))));
+  float2 dLda, wE;
+  if constexpr (KIND == NGS_MODEL_QUAD) {
+    const float2 ct = __ffma2_rn(make_float2(rp.c, rp.c), p.tau, one);  // 1 + c taubar_i
+    const float2 ptr = __fmul2_rn(alpha, ct);
+    const float2 pt = make_float2(fmaxf(ptr.x, 0.f), fmaxf(ptr.y, 0.f));
+    const float2 Sn = __fadd2_rn(p.S, pt);
+    const bool sat0 = Sn.x >= 1.0f, sat1 = Sn.y >= 1.0f;  // the saturating splat k: pbar_k = 1 - S
+    const float2 oms = __ffma2_rn(p.S, neg, one);
+    wE = make_float2(sat0 ? oms.x : pt.x, sat1 ? oms.y : pt.y);
+    live0 = live0 && !sat0;
+    live1 = live1 && !sat1;
+    // -g.Theta_i = -g.Theta_{i-1} + g.DeltaE_i alpha_i; dL0/dalpha_i = g.DeltaE_i (1 + c taubar_i) + c g.Theta_i
+    const float2 gd = __fadd2_rn(gE, p.nEk);
+    p.nTh = __ffma2_rn(gd, alpha, p.nTh);
+    dLda = __ffma2_rn(gd, ct, __fmul2_rn(make_float2(-rp.c, -rp.c), p.nTh));
+    p.S = make_float2(sat0 ? p.S.x : Sn.x, sat1 ? p.S.y : Sn.y);  // S stays below 1 for later entries
+    p.tau = __fadd2_rn(p.tau, alpha);
+  } else {
+    // dL0/dalpha_i = T_i g.E_i - (g.L0 - g.sum_{j<=i} E_j pbar_j) / (1 - alpha_i)
+    wE = __fmul2_rn(alpha, p.T);
+    p.gacc = __ffma2_rn(gE, wE, p.gacc);
+    const float2 oma = __ffma2_rn(alpha, neg, one);
+    const float2 rcp = make_float2(fast_rcp(oma.x), fast_rcp(oma.y));
+    dLda = __ffma2_rn(p.T, gE, __fmul2_rn(rcp, __ffma2_rn(p.gL0, neg, p.gacc)));
+    p.T = __fmul2_rn(p.T, oma);
+  }
+  const float2 wgt = __fmul2_rn(dLda, make_float2(live0 ? alpha.x : 0.f, live1 ? alpha.y : 0.f));
+  const float2 wdy = __fmul2_rn(wgt, dy);
+  const float2 wdyy = __fmul2_rn(wdy, dy);
+  const float2 c0 = __fmul2_rn(p.g0, wE), c1 = __fmul2_rn(p.g1, wE), c2 = __fmul2_rn(p.g2, wE);
+  v[5] = wgt.x + wgt.y;
+  v[1] = wdy.x + wdy.y;
+  v[4] = wdyy.x + wdyy.y;
+  v[0] = dx.x * v[5];
+  v[2] = dx.x * v[0];
+  v[3] = dx.x * v[1];
+  v[6] = c0.x + c0.y;
+  v[7] = c1.x + c1.y;
+  v[8] = c2.x + c2.y;
+  return true;
+}
+
+template <int TW, int TH, int KIND, int CH>
+__device__ __forceinline__ void backward_tile_pairs(const float4* __restrict__ rec, const uint32_t* __restrict__ ids,
+                                                    const uint2* __restrict__ ranges, const RenderParams& rp,
+                                                    const ViewParams* __restrict__ views,
+                                                    const float* __restrict__ dl_dimage,
+                                                    const float4* __restrict__ state, float4* __restrict__ grad2d,
+                                                    uint32_t tile, PairStageBuf<CH>& sb, uint32_t* s_id) {
+  using G = TileGeom<TW, TH, kBwdPix>;
+  constexpr int B = G::kThreads;
+  const TileView tv = tile_view(rp, views, (uint32_t)tile);
+  const int W = tv.W, H = tv.H;
+  const size_t pix_base = view_pix_base(rp, views, tv.view);
+  const int tx = tv.local % tv.tiles_x, ty = tv.local / tv.tiles_x;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint2 range = ranges[tile];
+  BwdPair p;
+  float px[2], py[2], g[2][3], gEk[2], gThe[2], gL0[2];
+  uint32_t last[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    int x, y;
+    G::pixel(tid, k, tx * TW, ty * TH, x, y);
+    px[k] = (float)x + 0.5f;
+    py[k] = (float)y + 0.5f;
+    last[k] = range.x;
+    g[k][0] = g[k][1] = g[k][2] = 0.f;
+    gEk[k] = gThe[k] = gL0[k] = 0.f;
+    if (x < W && y < H) {
+      const size_t pix = pix_base + (size_t)y * W + x;
+      const float4 s0 = state[2 * pix], s1 = state[2 * pix + 1];
+      last[k] = range.x + (__float_as_uint(s0.x) & 0x7FFFFFFFu);
+      g[k][0] = dl_dimage[3 * pix];
+      g[k][1] = dl_dimage[3 * pix + 1];
+      g[k][2] = dl_dimage[3 * pix + 2];
+      if constexpr (KIND == NGS_MODEL_QUAD) {
+        gEk[k] = g[k][0] * s0.y + g[k][1] * s0.z + g[k][2] * s0.w;
+        // Theta_{-1} = A - E_k taubar_k
+        gThe[k] = g[k][0] * (s1.x - s0.y * s1.w) + g[k][1] * (s1.y - s0.z * s1.w) + g[k][2] * (s1.z - s0.w * s1.w);
+      } else {
+        gL0[k] = g[k][0] * s0.y + g[k][1] * s0.z + g[k][2] * s0.w;
+      }
+      if (g[k][0] == 0.f && g[k][1] == 0.f && g[k][2] == 0.f) last[k] = range.x;
+    }
+  }
+  p.px = make_float2(px[0], px[0]);  // one column: px[1] == px[0]
+  p.py = make_float2(py[0], py[1]);
+  p.last0 = last[0];
+  p.last1 = last[1];
+  p.g0 = make_float2(g[0][0], g[1][0]);
+  p.g1 = make_float2(g[0][1], g[1][1]);
+  p.g2 = make_float2(g[0][2], g[1][2]);
+  p.T = make_float2(1.f, 1.f);
+  p.gacc = make_float2(0.f, 0.f);
+  p.gL0 = make_float2(gL0[0], gL0[1]);
+  p.S = p.tau = make_float2(0.f, 0.f);
+  p.nEk = make_float2(-gEk[0], -gEk[1]);
+  p.nTh = make_float2(-gThe[0], -gThe[1]);
+  const uint32_t my_last = max(p.last0, p.last1);
+  const uint32_t warp_last = __reduce_max_sync(kFull, my_last);
+  for (uint32_t base = range.x; base < range.y; base += CH) {
+    if (__syncthreads_count(base >= my_last) == B) break;
+    stage_chunk_pairs<B, CH>(rec, ids, rp, base, range.y, sb, s_id);
+    __syncthreads();
+    if (base < warp_last) {
+      const int cnt = (int)(min(warp_last, min(base + (uint32_t)CH, range.y)) - base);
+      for (int j = 0; j < cnt; ++j) {
+        float v[9];
+        const bool on = bwd_pair_step<KIND>(p, sb.q0[j], sb.q1[j], sb.q2[j], sb.q3[j], sb.q4[j], base + j, rp, v);
+        const uint32_t mask = __ballot_sync(kFull, on);
+        if (mask) {
+          float4* dst = grad2d + 3 * (size_t)s_id[j];
+          if (__popc(mask) <= kDirectLanes) {
+            if (on) {
+              atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
+              atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
+              atomicAdd(reinterpret_cast<float*>(dst + 2), v[8]);
+            }
+          } else {
+            if (!on) {
+#pragma unroll
+              for (int k = 0; k < 9; ++k) v[k] = 0.f;
+            }
+            warp_reduce9_add(v, reinterpret_cast<float*>(dst), lane);
+          }
+        }
+      }
+    }
+  }
+}
+
 template <int TW, int TH, int KIND, int CH>
 __device__ __forceinline__ void backward_tile(const float4* __restrict__ rec, const uint32_t* __restrict__ ids,
                                               const uint2* __restrict__ ranges, const RenderParams& rp,
@@ -568,17 +780,24 @@ __global__ void __launch_bounds__(TW* TH / kBwdPix) composite_backward_kernel(co
                                                                         float4* __restrict__ grad2d,
                                                                         const uint32_t* __restrict__ work,
                                                                         uint32_t* counter) {
-  __shared__ StageBuf<CH> sb;
+  using Buf = std::conditional_t<kPairReplay<KIND, CH>, PairStageBuf<CH>, StageBuf<CH>>;
+  __shared__ Buf sb;
   __shared__ uint32_t s_id[CH];
+  auto one_tile = [&](uint32_t tile) {
+    if constexpr (kPairReplay<KIND, CH>)
+      backward_tile_pairs<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, dl_dimage, state, grad2d, tile, sb, s_id);
+    else
+      backward_tile<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, dl_dimage, state, grad2d, tile, sb, s_id);
+  };
   if constexpr (PERSIST) {
     __shared__ uint32_t s_next;
     for (;;) {
       const uint32_t tile = next_tile(work, counter, rp.n_tiles, &s_next);
       if (tile >= rp.n_tiles) break;
-      backward_tile<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, dl_dimage, state, grad2d, tile, sb, s_id);
+      one_tile(tile);
     }
   } else {
-    backward_tile<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, dl_dimage, state, grad2d, blockIdx.x, sb, s_id);
+    one_tile(blockIdx.x);
   }
 }
 
