@@ -116,6 +116,47 @@ __device__ __forceinline__ uint32_t next_tile(const uint32_t* __restrict__ work,
   return w < n_tiles ? (work ? work[w] : w) : n_tiles;
 }
 
+// Staging of one chunk for the packed (two pixels per thread) forward and replay: every per-splat operand
+// duplicated, so one 16-byte shared load gives the operand pairs {a, a, b, b} of two FP32x2 instructions.
+template <int CH>
+struct PairStageBuf {
+  float4 q0[CH];  // {-u, -u, -v, -v}
+  float4 q1[CH];  // {A', A', B', B'}
+  float4 q2[CH];  // {C', C', L, L}
+  float4 q3[CH];  // {E0, E0, E1, E1}
+  float2 q4[CH];  // {E2, E2}
+};
+
+// The packed form (exponential and quadratic models) is used while its staging (72 B per record) stays
+// within 40 KB of static shared memory.
+template <int KIND, int CH>
+constexpr bool kPairForm = (KIND == NGS_MODEL_EXP || KIND == NGS_MODEL_QUAD) && sizeof(PairStageBuf<CH>) <= 40960;
+
+template <int B, int CH>
+__device__ __forceinline__ void stage_chunk_pairs(const float4* __restrict__ rec, const uint32_t* __restrict__ ids,
+                                                  const RenderParams& rp, uint32_t base, uint32_t end,
+                                                  PairStageBuf<CH>& sb, uint32_t* s_id) {
+#pragma unroll
+  for (int k = 0; k < (CH + B - 1) / B; ++k) {
+    const int slot = k * B + (int)threadIdx.x;
+    const uint32_t i = base + (uint32_t)slot;
+    if (slot < CH && i < end) {
+      const uint32_t id = ids[i];
+      if (s_id) s_id[slot] = id < rp.n_records ? id : 0u;
+      float4 r0, r1;
+      float e2;
+      stage_record(rec, id, rp, r0, r1, e2);
+      sb.q0[slot] = make_float4(-r0.x, -r0.x, -r0.y, -r0.y);
+      sb.q1[slot] = make_float4(r0.z, r0.z, r0.w, r0.w);
+      sb.q2[slot] = make_float4(r1.x, r1.x, r1.y, r1.y);
+      sb.q3[slot] = make_float4(r1.z, r1.z, r1.w, r1.w);
+      sb.q4[slot] = make_float2(e2, e2);
+    }
+  }
+}
+
+__device__ __forceinline__ float2 lo_hi(float4 q, bool hi) { return hi ? make_float2(q.z, q.w) : make_float2(q.x, q.y); }
+
 template <int TW, int TH, int KIND, int CH>
 __device__ __forceinline__ void forward_tile(const float4* __restrict__ rec, const uint32_t* __restrict__ ids,
                                              const uint2* __restrict__ ranges, const RenderParams& rp,
@@ -293,8 +334,154 @@ __device__ __forceinline__ void forward_tile(const float4* __restrict__ rec, con
   }
 }
 
+// Packed forward (exponential and quadratic): two pixels per thread, (x, y) and (x, y + 4), stepping through
+// each entry together in FP32x2 instructions. Each lane rounds exactly like the one-pixel form above, so
+// the image, the stop index and the replay state are the same bits. A pixel that has stopped, or that
+// does not composite the entry, gets alpha = 0, which leaves its sums exactly unchanged.
+template <int TW, int TH, int KIND, int CH>
+__device__ __forceinline__ void forward_tile_pairs(const float4* __restrict__ rec, const uint32_t* __restrict__ ids,
+                                                   const uint2* __restrict__ ranges, const RenderParams& rp,
+                                                   const ViewParams* __restrict__ views, float* __restrict__ image,
+                                                   int32_t* __restrict__ overdraw, float4* __restrict__ state,
+                                                   uint32_t tile, PairStageBuf<CH>& sb) {
+  using G = TileGeom<TW, TH, 2>;
+  constexpr int B = G::kThreads;
+  const TileView tv = tile_view(rp, views, (uint32_t)tile);
+  const int W = tv.W, H = tv.H;
+  const int tx = tv.local % tv.tiles_x, ty = tv.local / tv.tiles_x;
+  int x, y;
+  G::pixel(threadIdx.x, 0, tx * TW, ty * TH, x, y);  // the second pixel is (x, y + 4)
+  const bool in0 = x < W && y < H, in1 = x < W && y + 4 < H;
+  const float2 one = make_float2(1.f, 1.f), neg = make_float2(-1.f, -1.f), zero = make_float2(0.f, 0.f);
+  const float2 px = make_float2((float)x + 0.5f, (float)x + 0.5f);
+  const float2 py = make_float2((float)y + 0.5f, (float)(y + 4) + 0.5f);
+  const uint2 range = ranges[tile];
+  bool done0 = !in0, done1 = !in1;
+  int od0 = 0, od1 = 0;
+  uint32_t stop0 = range.y - range.x, stop1 = stop0;  // entries walked (n of the replay state)
+  bool sat0 = false, sat1 = false;
+  float2 C0 = zero, C1 = zero, C2 = zero;
+  float2 S = zero, tau = zero, A0 = zero, A1 = zero, A2 = zero;  // quadratic
+  float Ek[2][3] = {{rp.bg[0], rp.bg[1], rp.bg[2]}, {rp.bg[0], rp.bg[1], rp.bg[2]}};
+  float2 T = one;  // exponential
+  const float amax = rp.alpha_max, l2min = rp.log2_alpha_min;
+  const float2 c2 = make_float2(rp.c, rp.c);
+  for (uint32_t base = range.x; base < range.y; base += CH) {
+    if (__syncthreads_count(done0 && done1) == B) break;
+    stage_chunk_pairs<B, CH>(rec, ids, rp, base, range.y, sb, nullptr);
+    __syncthreads();
+    const int cnt = (int)min((uint32_t)CH, range.y - base);
+    if (__any_sync(kFull, !(done0 && done1))) {
+      for (int j = 0; j < cnt && !(done0 && done1); ++j) {
+        const float4 q0 = sb.q0[j], q1 = sb.q1[j], q2 = sb.q2[j];
+        const float2 dx = __fadd2_rn(px, lo_hi(q0, false));
+        const float2 adx = __fmul2_rn(lo_hi(q1, false), dx);
+        const float2 dy = __fadd2_rn(py, lo_hi(q0, true));
+        const float2 t = __ffma2_rn(lo_hi(q1, true), dy, adx);
+        const float2 cdd = __fmul2_rn(__fmul2_rn(lo_hi(q2, false), dy), dy);
+        const float2 e = __fadd2_rn(lo_hi(q2, true), __ffma2_rn(dx, t, cdd));
+        const bool on0 = !done0 && e.x >= l2min, on1 = !done1 && e.y >= l2min;
+        if (!(on0 || on1)) continue;
+        const float4 q3 = sb.q3[j];
+        const float2 E0 = lo_hi(q3, false), E1 = lo_hi(q3, true), E2 = sb.q4[j];
+        const float2 alpha = make_float2(on0 ? fminf(amax, fast_exp2(e.x)) : 0.f, on1 ? fminf(amax, fast_exp2(e.y)) : 0.f);
+        const uint32_t pos = base + j - range.x;
+        bool c0, c1;  // composited (the overdraw count)
+        if constexpr (KIND == NGS_MODEL_QUAD) {
+          const float2 ptr = __fmul2_rn(alpha, __ffma2_rn(c2, tau, one));
+          const float2 pt = make_float2(fmaxf(ptr.x, 0.f), fmaxf(ptr.y, 0.f));
+          const float2 Sn = __fadd2_rn(S, pt);
+          const bool s0 = on0 && Sn.x >= 1.0f, s1 = on1 && Sn.y >= 1.0f;  // the saturating splat k
+          const float2 oms = __ffma2_rn(S, neg, one);                     // pbar_k = 1 - S (Eq. nexp_p)
+          const float2 wc = make_float2(s0 ? oms.x : pt.x, s1 ? oms.y : pt.y);
+          const float2 wa = make_float2(s0 ? 0.f : alpha.x, s1 ? 0.f : alpha.y);
+          C0 = __ffma2_rn(E0, wc, C0);
+          C1 = __ffma2_rn(E1, wc, C1);
+          C2 = __ffma2_rn(E2, wc, C2);
+          A0 = __ffma2_rn(E0, wa, A0);
+          A1 = __ffma2_rn(E1, wa, A1);
+          A2 = __ffma2_rn(E2, wa, A2);
+          S = make_float2(s0 ? S.x : Sn.x, s1 ? S.y : Sn.y);
+          tau = __fadd2_rn(tau, wa);
+          if (s0) {
+            Ek[0][0] = E0.x, Ek[0][1] = E1.x, Ek[0][2] = E2.x;
+            sat0 = done0 = true;
+            stop0 = pos + 1;
+          }
+          if (s1) {
+            Ek[1][0] = E0.y, Ek[1][1] = E1.y, Ek[1][2] = E2.y;
+            sat1 = done1 = true;
+            stop1 = pos + 1;
+          }
+          c0 = on0;
+          c1 = on1;
+        } else {
+          // stop before the splat that would take T below t_eps
+          const float2 testT = __fmul2_rn(T, __ffma2_rn(alpha, neg, one));
+          const bool st0 = on0 && testT.x < rp.t_eps, st1 = on1 && testT.y < rp.t_eps;
+          if (st0) {
+            done0 = true;
+            stop0 = pos;
+          }
+          if (st1) {
+            done1 = true;
+            stop1 = pos;
+          }
+          c0 = on0 && !st0;
+          c1 = on1 && !st1;
+          const float2 w = __fmul2_rn(make_float2(c0 ? alpha.x : 0.f, c1 ? alpha.y : 0.f), T);
+          C0 = __ffma2_rn(E0, w, C0);
+          C1 = __ffma2_rn(E1, w, C1);
+          C2 = __ffma2_rn(E2, w, C2);
+          T = make_float2(c0 ? testT.x : T.x, c1 ? testT.y : T.y);
+        }
+        od0 += c0;
+        od1 += c1;
+        if (rp.max_splats > 0) {
+          if (c0 && !done0 && od0 == rp.max_splats) {
+            done0 = true;
+            stop0 = pos + 1;
+          }
+          if (c1 && !done1 && od1 == rp.max_splats) {
+            done1 = true;
+            stop1 = pos + 1;
+          }
+        }
+      }
+    }
+  }
+  const size_t pbase = view_pix_base(rp, views, tv.view);
+  float* const out_image = view_image(rp, views, tv.view, image);
+  int32_t* const out_overdraw = view_overdraw(rp, views, tv.view, overdraw);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    if (!(k ? in1 : in0)) continue;
+    const size_t lpix = (size_t)(y + 4 * k) * W + x;  // pixel within the view
+    const size_t pix = pbase + lpix;                  // packed pixel of the replay state
+    const float c0v = k ? C0.y : C0.x, c1v = k ? C1.y : C1.x, c2v = k ? C2.y : C2.x;
+    const bool sat = k ? sat1 : sat0;
+    const float Tend = KIND == NGS_MODEL_EXP ? (k ? T.y : T.x) : (sat ? 0.f : 1.f - (k ? S.y : S.x));
+    const float L0 = c0v + rp.bg[0] * Tend, L1 = c1v + rp.bg[1] * Tend, L2 = c2v + rp.bg[2] * Tend;
+    out_image[3 * lpix] = L0;
+    out_image[3 * lpix + 1] = L1;
+    out_image[3 * lpix + 2] = L2;
+    if (out_overdraw) out_overdraw[lpix] = k ? od1 : od0;
+    const uint32_t nbits = (k ? stop1 : stop0) | (sat ? 0x80000000u : 0u);
+    if constexpr (KIND == NGS_MODEL_QUAD) {
+      state[2 * pix] = make_float4(__uint_as_float(nbits), Ek[k][0], Ek[k][1], Ek[k][2]);
+      state[2 * pix + 1] = make_float4(k ? A0.y : A0.x, k ? A1.y : A1.x, k ? A2.y : A2.x, k ? tau.y : tau.x);
+    } else {
+      state[2 * pix] = make_float4(__uint_as_float(nbits), L0, L1, L2);
+      state[2 * pix + 1] = make_float4(Tend, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+template <int TW, int TH, int KIND, int CH>
+constexpr int kFwdThreads = TW * TH / (kPairForm<KIND, CH> ? 2 : 1);
+
 template <int TW, int TH, int KIND, int CH, bool PERSIST>
-__global__ void __launch_bounds__(TW* TH) composite_forward_kernel(const float4* __restrict__ rec,
+__global__ void __launch_bounds__(kFwdThreads<TW, TH, KIND, CH>) composite_forward_kernel(const float4* __restrict__ rec,
                                                                    const uint32_t* __restrict__ ids,
                                                                    const uint2* __restrict__ ranges, RenderParams rp,
                                                                    const ViewParams* __restrict__ views,
@@ -303,16 +490,23 @@ __global__ void __launch_bounds__(TW* TH) composite_forward_kernel(const float4*
                                                                    float4* __restrict__ state,
                                                                    const uint32_t* __restrict__ work,
                                                                    uint32_t* counter) {
-  __shared__ StageBuf<CH> sb;
+  using Buf = std::conditional_t<kPairForm<KIND, CH>, PairStageBuf<CH>, StageBuf<CH>>;
+  __shared__ Buf sb;
+  auto one_tile = [&](uint32_t tile) {
+    if constexpr (kPairForm<KIND, CH>)
+      forward_tile_pairs<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, image, overdraw, state, tile, sb);
+    else
+      forward_tile<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, image, overdraw, state, tile, sb);
+  };
   if constexpr (PERSIST) {
     __shared__ uint32_t s_next;
     for (;;) {
       const uint32_t tile = next_tile(work, counter, rp.n_tiles, &s_next);
       if (tile >= rp.n_tiles) break;
-      forward_tile<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, image, overdraw, state, tile, sb);
+      one_tile(tile);
     }
   } else {
-    forward_tile<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, image, overdraw, state, blockIdx.x, sb);
+    one_tile(blockIdx.x);
   }
 }
 
@@ -467,44 +661,6 @@ __device__ __forceinline__ bool bwd_step(BwdPixel& p, float dx, float adx, float
 // composite the entry (past its stop, or alpha < alpha_min) gets alpha = 0, which leaves its running sums
 // exactly as they were and contributes zero.
 
-// Replay staging of one chunk: every per-splat operand duplicated, so one 16-byte shared load gives the
-// operand pairs {a, a, b, b} of two FP32x2 instructions.
-template <int CH>
-struct PairStageBuf {
-  float4 q0[CH];  // {-u, -u, -v, -v}
-  float4 q1[CH];  // {A', A', B', B'}
-  float4 q2[CH];  // {C', C', L, L}
-  float4 q3[CH];  // {E0, E0, E1, E1}
-  float2 q4[CH];  // {E2, E2}
-};
-
-// The packed form is used while its staging (72 B per record) stays within 40 KB of static shared memory.
-template <int KIND, int CH>
-constexpr bool kPairReplay = (KIND == NGS_MODEL_EXP || KIND == NGS_MODEL_QUAD) && sizeof(PairStageBuf<CH>) <= 40960;
-
-template <int B, int CH>
-__device__ __forceinline__ void stage_chunk_pairs(const float4* __restrict__ rec, const uint32_t* __restrict__ ids,
-                                                  const RenderParams& rp, uint32_t base, uint32_t end,
-                                                  PairStageBuf<CH>& sb, uint32_t* s_id) {
-#pragma unroll
-  for (int k = 0; k < (CH + B - 1) / B; ++k) {
-    const int slot = k * B + (int)threadIdx.x;
-    const uint32_t i = base + (uint32_t)slot;
-    if (slot < CH && i < end) {
-      const uint32_t id = ids[i];
-      s_id[slot] = id < rp.n_records ? id : 0u;
-      float4 r0, r1;
-      float e2;
-      stage_record(rec, id, rp, r0, r1, e2);
-      sb.q0[slot] = make_float4(-r0.x, -r0.x, -r0.y, -r0.y);
-      sb.q1[slot] = make_float4(r0.z, r0.z, r0.w, r0.w);
-      sb.q2[slot] = make_float4(r1.x, r1.x, r1.y, r1.y);
-      sb.q3[slot] = make_float4(r1.z, r1.z, r1.w, r1.w);
-      sb.q4[slot] = make_float2(e2, e2);
-    }
-  }
-}
-
 // Both pixels' replay state, lane 0 = pixel (x, y), lane 1 = pixel (x, y + 4).
 struct BwdPair {
   float2 px, py;
@@ -513,8 +669,6 @@ struct BwdPair {
   float2 T, gacc, gL0;    // exponential: T_i, g.sum_{j<i} E_j pbar_j, g.L0
   float2 S, tau, nEk, nTh;  // quadratic: S, taubar, -g.E_k, -g.Theta
 };
-
-__device__ __forceinline__ float2 lo_hi(float4 q, bool hi) { return hi ? make_float2(q.z, q.w) : make_float2(q.x, q.y); }
 
 // One list entry for both pixels: adds their contributions to v (the 9 per-splat sums, the dx moments
 // included) and returns whether either pixel composited the splat.
@@ -780,11 +934,11 @@ __global__ void __launch_bounds__(TW* TH / kBwdPix) composite_backward_kernel(co
                                                                         float4* __restrict__ grad2d,
                                                                         const uint32_t* __restrict__ work,
                                                                         uint32_t* counter) {
-  using Buf = std::conditional_t<kPairReplay<KIND, CH>, PairStageBuf<CH>, StageBuf<CH>>;
+  using Buf = std::conditional_t<kPairForm<KIND, CH>, PairStageBuf<CH>, StageBuf<CH>>;
   __shared__ Buf sb;
   __shared__ uint32_t s_id[CH];
   auto one_tile = [&](uint32_t tile) {
-    if constexpr (kPairReplay<KIND, CH>)
+    if constexpr (kPairForm<KIND, CH>)
       backward_tile_pairs<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, dl_dimage, state, grad2d, tile, sb, s_id);
     else
       backward_tile<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, dl_dimage, state, grad2d, tile, sb, s_id);
@@ -823,7 +977,7 @@ template <int TW, int TH, int KIND, int CH>
 void forward_launch(const float4* rec, const uint32_t* ids, const uint2* ranges, const RenderParams& rp,
                     const ViewParams* views, float* image, int32_t* overdraw, float4* state, const Launch& L,
                     cudaStream_t s) {
-  constexpr int threads = TileGeom<TW, TH, 1>::kThreads;
+  constexpr int threads = kFwdThreads<TW, TH, KIND, CH>;
   auto k = L.counter ? composite_forward_kernel<TW, TH, KIND, CH, true> : composite_forward_kernel<TW, TH, KIND, CH, false>;
   k<<<grid_for(k, threads, L, rp.n_tiles), threads, 0, s>>>(rec, ids, ranges, rp, views, image, overdraw, state,
                                                              L.work, L.counter);
