@@ -263,15 +263,15 @@ def run_ours(args):
     clk = clocks.stop()
     launches = sum(x.launch_count() for x in rs) - launches0
 
-    def stage_steps(n, graphs):
-        # per-stage CUDA-event times of n further steps, models one after another
+    def stage_steps(n, graphs, events=None):
+        # per-stage CUDA-event times of n further steps, models one after another (and per-model events)
         for x in rs:
             x.set_graphs(graphs)
             x.set_timing(True)
             x.reset_stage_times()
-        for _ in range(n):
+        for i in range(n):
             flush.zero_()
-            step(serial=True)
+            step(events[i] if events else None, serial=True)
         torch.cuda.synchronize()
         out = {}
         for x in rs:
@@ -291,7 +291,8 @@ def run_ours(args):
         stage_source = ("timed region" if args.no_graphs else
                         "backward stages: timed region; forward stages: 2 further steps with direct launches")
     else:
-        stage = stage_steps(K, not args.no_graphs)
+        model_ev = [{m: [torch.cuda.Event(enable_timing=True) for _ in range(3)] for m in MODELS} for _ in range(K)]
+        stage = stage_steps(K, not args.no_graphs, model_ev)
         stage_source = (f"{K} further steps with the models one after another" if args.no_graphs else
                         f"backward stages: {K} further steps with the models one after another; "
                         "forward stages: 2 further such steps with direct launches")
@@ -340,6 +341,9 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"views x{world}",
                    "pairs_per_view": int(frames["exp"].view()["n_pairs"])},
         "per_model": per_model,
+        "per_model_source": ("timed region" if S == 1 else
+                             f"{K} further steps with the models one after another (the timed region overlaps "
+                             "two models' kernels)"),
         "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
         "stage_ms_source": stage_source,
         "gpu_launches": int(launches), "gpu_launches_per_step": round(launches / K, 1),
