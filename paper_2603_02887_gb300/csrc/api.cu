@@ -67,18 +67,20 @@ void stage_end(ngs_ctx* ctx, cudaStream_t s, int stage, cudaEvent_t start, int l
 // view table and its pair count behind whatever bulk copies other streams have queued on the engines.
 // The view table is read by a kernel from mapped pinned memory over the host link...
 __global__ void copy_words_kernel(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, uint32_t n) {
+  pdl_wait();
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
 }
 
 // ... and the scalars the host reads back (the pair count and the error word, loss sums, a densified count)
 // are written by a kernel into the context's mapped pinned mirror, read after synchronising with the stream.
 __global__ void publish_words_kernel(const uint64_t* __restrict__ src, uint64_t* dst, int n) {
+  pdl_wait();
   if ((int)threadIdx.x < n) dst[threadIdx.x] = src[threadIdx.x];
   __threadfence_system();
 }
 
 void publish_words(ngs_ctx* ctx, const uint64_t* src, int n, int slot, cudaStream_t s) {
-  publish_words_kernel<<<1, 32, 0, s>>>(src, ctx->d_h_total + slot, n);
+  launch_pdl(publish_words_kernel, 1, 32, 0, s, src, ctx->d_h_total + slot, n);
 }
 
 static void free_buf(DevBuf& b) {
@@ -233,8 +235,8 @@ static void phase1(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, cudaStream_
   {
     static_assert(sizeof(ViewParams) % 4 == 0, "the view table is copied in 4-byte words");
     const uint32_t words = (uint32_t)(sizeof(ViewParams) * f->view_host.size() / 4);
-    copy_words_kernel<<<std::min((words + 255) / 256, 64u), 256, 0, s>>>(f->d_h_views, f->views.as<uint32_t>(),
-                                                                          words);
+    launch_pdl(copy_words_kernel, std::min((words + 255) / 256, 64u), 256, 0, s, f->d_h_views, f->views.as<uint32_t>(),
+               words);
   }
   launch_project(*pl.g, views, f->view_host[0].cam, rp, f->rec.as<float4>(), f->gkeys[0].as<uint32_t>(),
                  f->tile_count.as<uint32_t>(), f->gvals[0].as<uint32_t>(), s);

@@ -496,6 +496,7 @@ __global__ void __launch_bounds__(kFwdThreads<TW, TH, KIND, CH>) composite_forwa
                                                                    float4* __restrict__ state,
                                                                    const uint32_t* __restrict__ work,
                                                                    uint32_t* counter) {
+  pdl_wait();
   using Buf = std::conditional_t<kPairFwd<TW, TH, KIND, CH>, PairStageBuf<CH>, StageBuf<CH>>;
   __shared__ Buf sb;
   auto one_tile = [&](uint32_t tile) {
@@ -940,6 +941,7 @@ __global__ void __launch_bounds__(TW* TH / kBwdPix) composite_backward_kernel(co
                                                                         float4* __restrict__ grad2d,
                                                                         const uint32_t* __restrict__ work,
                                                                         uint32_t* counter) {
+  pdl_wait();
   using Buf = std::conditional_t<kPairForm<KIND, CH>, PairStageBuf<CH>, StageBuf<CH>>;
   __shared__ Buf sb;
   __shared__ uint32_t s_id[CH];
@@ -985,8 +987,8 @@ void forward_launch(const float4* rec, const uint32_t* ids, const uint2* ranges,
                     cudaStream_t s) {
   constexpr int threads = kFwdThreads<TW, TH, KIND, CH>;
   auto k = L.counter ? composite_forward_kernel<TW, TH, KIND, CH, true> : composite_forward_kernel<TW, TH, KIND, CH, false>;
-  k<<<grid_for(k, threads, L, rp.n_tiles), threads, 0, s>>>(rec, ids, ranges, rp, views, image, overdraw, state,
-                                                             L.work, L.counter);
+  launch_pdl(k, grid_for(k, threads, L, rp.n_tiles), threads, 0, s, rec, ids, ranges, rp, views, image, overdraw, state,
+             L.work, L.counter);
 }
 
 template <int TW, int TH, int KIND, int CH>
@@ -996,8 +998,8 @@ void backward_launch(const float4* rec, const uint32_t* ids, const uint2* ranges
   constexpr int threads = TileGeom<TW, TH, kBwdPix>::kThreads;
   auto k =
       L.counter ? composite_backward_kernel<TW, TH, KIND, CH, true> : composite_backward_kernel<TW, TH, KIND, CH, false>;
-  k<<<grid_for(k, threads, L, rp.n_tiles), threads, 0, s>>>(rec, ids, ranges, rp, views, dl, state, grad2d, L.work,
-                                                             L.counter);
+  launch_pdl(k, grid_for(k, threads, L, rp.n_tiles), threads, 0, s, rec, ids, ranges, rp, views, dl, state, grad2d,
+             L.work, L.counter);
 }
 
 template <int TW, int TH, int KIND>

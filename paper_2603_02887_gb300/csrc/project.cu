@@ -334,6 +334,7 @@ template <int DEG, bool VEC>
 __global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, const ViewParams* __restrict__ views,
                                                       CamParams cam0, RenderParams rp, float4* rec,
                                                       uint32_t* depth_key, uint32_t* tile_count, uint32_t* order) {
+  pdl_wait();
   const uint32_t view = blockIdx.x % rp.n_views;
   int i = (blockIdx.x / rp.n_views) * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
@@ -562,6 +563,7 @@ __global__ void __launch_bounds__(128, MULTI ? 1 : 4) project_backward_kernel(ng
                                                                CamParams cam0, RenderParams rp,
                                                                const uint32_t* tile_count, const float4* grad2d,
                                                                ngs_grads out) {
+  pdl_wait();
   constexpr int K = (DEG + 1) * (DEG + 1);
   // One view with 16-byte SH rows: each warp moves its 32 Gaussians' SH blocks (contiguous in memory)
   // between global and shared memory with coalesced 16-byte accesses; each thread then reads its
@@ -639,8 +641,8 @@ void launch_project(const ngs_gaussians& g, const ViewParams* views, const CamPa
   if (g.n == 0) return;
   unsigned blocks = (unsigned)((g.n + 255) / 256) * rp.n_views;
   bool vec = ((uintptr_t)g.sh & 15) == 0;
-#define NGS_PROJECT(D, V) project_kernel<D, V><<<blocks, 256, 0, s>>>(g, views, cam0, rp, rec, depth_key, tile_count, \
-                                                                    order)
+#define NGS_PROJECT(D, V) \
+  launch_pdl(project_kernel<D, V>, blocks, 256, 0, s, g, views, cam0, rp, rec, depth_key, tile_count, order)
   switch (rp.sh_degree) {
     case 0: NGS_PROJECT(0, false); break;
     case 1:
@@ -668,9 +670,9 @@ static void project_backward_views(const ngs_gaussians& g, const ViewParams* vie
                                    const ngs_grads& out, cudaStream_t s) {
   int blocks = (int)((g.n + 127) / 128);
   if (rp.n_views > 1)
-    project_backward_kernel<DEG, VEC, true><<<blocks, 128, 0, s>>>(g, views, cam0, rp, tile_count, grad2d, out);
+    launch_pdl(project_backward_kernel<DEG, VEC, true>, blocks, 128, 0, s, g, views, cam0, rp, tile_count, grad2d, out);
   else
-    project_backward_kernel<DEG, VEC, false><<<blocks, 128, 0, s>>>(g, views, cam0, rp, tile_count, grad2d, out);
+    launch_pdl(project_backward_kernel<DEG, VEC, false>, blocks, 128, 0, s, g, views, cam0, rp, tile_count, grad2d, out);
 }
 
 void launch_project_backward(const ngs_gaussians& g, const ViewParams* views, const CamParams& cam0,

@@ -76,6 +76,7 @@ template <typename K, int ITEMS>
 __global__ void __launch_bounds__(kThreads) upsweep_kernel(const K* __restrict__ keys, uint32_t seg_len,
                                                            const uint32_t* __restrict__ n_dev, int shift,
                                                            uint32_t* __restrict__ hist, uint32_t nblocks) {
+  pdl_wait();
   __shared__ uint32_t s_hist[kWarps][kDigits];
   int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t seg = blockIdx.x / nblocks, blk = blockIdx.x - seg * nblocks;
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(kThreads) upsweep_kernel(const K* __restrict__
 // One block per (segment, digit): exclusive scan of that digit's per-block counts; the digit's total goes
 // to totals[segment][digit] (stored after the histograms).
 __global__ void __launch_bounds__(1024) scan_digit_kernel(uint32_t* hist, uint32_t nblocks, uint32_t* totals) {
+  pdl_wait();
   __shared__ uint32_t s_warp[32];
   uint32_t* row = hist + (size_t)blockIdx.x * nblocks;
   uint32_t carry = 0;
@@ -127,6 +129,7 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(const K* __restrict
                                                              uint32_t seg_len, const uint32_t* __restrict__ n_dev,
                                                              int shift, const uint32_t* __restrict__ hist,
                                                              const uint32_t* __restrict__ totals, uint32_t nblocks) {
+  pdl_wait();
   constexpr int kTile = SortTile<ITEMS>::kTile, kItems = ITEMS;
   const uint32_t seg = blockIdx.x / nblocks, blk = blockIdx.x - seg * nblocks;
   const uint32_t n = segment_count(seg_len, n_dev);
@@ -222,10 +225,10 @@ int radix_sort(K* keys[2], uint32_t* vals[2], uint32_t seg_len, uint32_t nseg, c
   // at most 24 KB of dynamic shared memory (for 64-bit keys), within the default limit without an opt-in
   size_t smem = (sizeof(K) + sizeof(uint32_t)) * kTile;
   for (int shift = begin_bit; shift < end_bit; shift += 8) {
-    upsweep_kernel<K, ITEMS><<<grid, kThreads, 0, s>>>(keys[cur], seg_len, n_dev, shift, hist, nblocks);
-    scan_digit_kernel<<<kDigits * nseg, 1024, 0, s>>>(hist, nblocks, totals);
-    downsweep_kernel<K, ITEMS><<<grid, kThreads, smem, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1],
-                                                            seg_len, n_dev, shift, hist, totals, nblocks);
+    launch_pdl(upsweep_kernel<K, ITEMS>, grid, kThreads, 0, s, keys[cur], seg_len, n_dev, shift, hist, nblocks);
+    launch_pdl(scan_digit_kernel, kDigits * nseg, 1024, 0, s, hist, nblocks, totals);
+    launch_pdl(downsweep_kernel<K, ITEMS>, grid, kThreads, smem, s, keys[cur], vals[cur], keys[cur ^ 1],
+               vals[cur ^ 1], seg_len, n_dev, shift, hist, totals, nblocks);
     cur ^= 1;
     *launches += 3;
   }
@@ -241,6 +244,7 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ count,
                                                                    const uint32_t* __restrict__ order, uint32_t n,
                                                                    uint64_t* __restrict__ block_sums) {
+  pdl_wait();
   __shared__ uint64_t s_warp[kScanThreads / 32];
   uint64_t sum = 0;
   uint32_t base = blockIdx.x * (uint32_t)kScanTile;
@@ -255,6 +259,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_
 }
 
 __global__ void __launch_bounds__(1024) scan_block_sums_kernel(uint64_t* block_sums, uint32_t nblocks, uint64_t* total) {
+  pdl_wait();
   __shared__ uint64_t s_warp[32];
   uint64_t carry = 0;
   for (uint32_t base = 0; base < nblocks; base += 1024) {
@@ -271,6 +276,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const uint32_t
                                                                   const uint32_t* __restrict__ order, uint32_t n,
                                                                   const uint64_t* __restrict__ block_offsets,
                                                                   uint32_t* __restrict__ offsets) {
+  pdl_wait();
   __shared__ uint32_t s_warp[kScanThreads / 32];
   uint32_t base = blockIdx.x * (uint32_t)kScanTile + threadIdx.x * kScanItems;  // blocked arrangement
   uint32_t v[kScanItems], local = 0;
@@ -343,6 +349,7 @@ __global__ void __launch_bounds__(256) tile_bucket_scatter_kernel(const uint2* _
                                                                   const uint32_t* __restrict__ counts,
                                                                   uint32_t* __restrict__ cursors,
                                                                   uint32_t* __restrict__ work) {
+  pdl_wait();
   __shared__ uint32_t s_start[kCostBuckets];
   if (threadIdx.x == 0) {
     uint32_t run = 0;
@@ -369,7 +376,7 @@ void launch_tile_order(const uint2* ranges, uint32_t ntiles, uint32_t* sched, ui
   if (ntiles == 0) return;
   const unsigned blocks = (ntiles + 255) / 256;
   tile_bucket_count_kernel<<<blocks, 256, 0, s>>>(ranges, ntiles, sched + 2);
-  tile_bucket_scatter_kernel<<<blocks, 256, 0, s>>>(ranges, ntiles, sched + 2, sched + 2 + kCostBuckets, work);
+  launch_pdl(tile_bucket_scatter_kernel, blocks, 256, 0, s, ranges, ntiles, sched + 2, sched + 2 + kCostBuckets, work);
   *launches += 2;
 }
 
@@ -398,9 +405,9 @@ void launch_scan_counts(const uint32_t* tile_count, const uint32_t* order, uint3
     return;
   }
   uint32_t nblocks = (n + kScanTile - 1) / kScanTile;
-  scan_reduce_kernel<<<nblocks, kScanThreads, 0, s>>>(tile_count, order, n, block_sums);
-  scan_block_sums_kernel<<<1, 1024, 0, s>>>(block_sums, nblocks, total);
-  scan_final_kernel<<<nblocks, kScanThreads, 0, s>>>(tile_count, order, n, block_sums, offsets);
+  launch_pdl(scan_reduce_kernel, nblocks, kScanThreads, 0, s, tile_count, order, n, block_sums);
+  launch_pdl(scan_block_sums_kernel, 1, 1024, 0, s, block_sums, nblocks, total);
+  launch_pdl(scan_final_kernel, nblocks, kScanThreads, 0, s, tile_count, order, n, block_sums, offsets);
   *launches += 3;
 }
 
