@@ -267,6 +267,10 @@ static void phase2(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, uint32_t ca
   const RenderParams& rp = pl.rp;
   const ViewParams* views = f->views.as<ViewParams>();
   cudaEvent_t ev;
+  // zeroing first, so that the kernels from the emission to the composite follow one another directly
+  // (programmatic dependent launches)
+  cudaMemsetAsync(f->ranges.p, 0, sizeof(uint2) * (size_t)pl.ntiles, s);
+  if (rp.schedule == NGS_SCHEDULE_PERSISTENT) cudaMemsetAsync(f->sched.p, 0, sizeof(uint32_t) * kSchedWords, s);
   stage_begin(ctx, s, 2, &ev);
   launch_emit_pairs(f->rec.as<float4>(), f->gvals[f->g_final].as<uint32_t>(), f->offsets.as<uint32_t>(), views, rp,
                     f->ptile[0].as<uint32_t>(), f->pvals[0].as<uint32_t>(), s);
@@ -292,7 +296,6 @@ static void phase2(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, uint32_t ca
   const uint32_t* work = nullptr;
   uint32_t* counter = nullptr;
   if (rp.schedule == NGS_SCHEDULE_PERSISTENT) {
-    cudaMemsetAsync(f->sched.p, 0, sizeof(uint32_t) * kSchedWords, s);
     launch_tile_order(f->ranges.as<uint2>(), pl.ntiles, f->sched.as<uint32_t>(), f->work.as<uint32_t>(), s,
                       &launches);
     work = f->work.as<uint32_t>();

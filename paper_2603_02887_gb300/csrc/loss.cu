@@ -28,7 +28,9 @@ struct Window {
 
 // moments per pixel and channel: 5 x 3 planes, [plane][pixel]
 __global__ void ssim_hmoments_kernel(Window win, const float* __restrict__ x, const float* __restrict__ y, int W,
-                                     int H, float* __restrict__ hm) {
+                                     int H, float* __restrict__ hm, double* __restrict__ sums) {
+  pdl_wait();
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < 2) sums[threadIdx.x] = 0.0;  // summed by the next kernel
   const int px = blockIdx.x * blockDim.x + threadIdx.x, py = blockIdx.y;
   if (px >= W) return;
   const size_t npix = (size_t)W * H, pix = (size_t)py * W + px;
@@ -59,6 +61,7 @@ __global__ void ssim_hmoments_kernel(Window win, const float* __restrict__ x, co
 __global__ void ssim_vmap_kernel(Window win, const float* __restrict__ hm, const float* __restrict__ x,
                                  const float* __restrict__ y, int W, int H, float* __restrict__ abc,
                                  double* __restrict__ sums) {
+  pdl_wait();
   const int px = blockIdx.x * blockDim.x + threadIdx.x, py = blockIdx.y;
   const size_t npix = (size_t)W * H;
   float s_sum = 0.f, l1_sum = 0.f;
@@ -113,6 +116,7 @@ __global__ void ssim_vmap_kernel(Window win, const float* __restrict__ hm, const
 }
 
 __global__ void ssim_habc_kernel(Window win, const float* __restrict__ abc, int W, int H, float* __restrict__ habc) {
+  pdl_wait();
   const int px = blockIdx.x * blockDim.x + threadIdx.x, py = blockIdx.y;
   if (px >= W) return;
   const size_t npix = (size_t)W * H, pix = (size_t)py * W + px;
@@ -134,6 +138,7 @@ __global__ void ssim_habc_kernel(Window win, const float* __restrict__ abc, int 
 __global__ void ssim_grad_kernel(Window win, const float* __restrict__ habc, const float* __restrict__ x,
                                  const float* __restrict__ y, int W, int H, float w_l1, float w_ssim,
                                  float* __restrict__ dl) {
+  pdl_wait();
   const int px = blockIdx.x * blockDim.x + threadIdx.x, py = blockIdx.y;
   if (px >= W) return;
   const size_t npix = (size_t)W * H, pix = (size_t)py * W + px;
@@ -188,16 +193,15 @@ extern "C" NGS_API int ngs_loss_l1_ssim(ngs_ctx* ctx, const float* image, const 
   float* abc = hm + 15 * npix;  // 9 planes after the 15 moment planes
   double* sums = reinterpret_cast<double*>(hm + 24 * npix);
   float* habc = hm;  // the moment planes are free again once the map is computed
-  cudaMemsetAsync(sums, 0, 2 * sizeof(double), s);
   const dim3 block(256), grid((width + 255) / 256, height);
-  ssim_hmoments_kernel<<<grid, block, 0, s>>>(win, image, target, width, height, hm);
-  ssim_vmap_kernel<<<grid, block, 0, s>>>(win, hm, image, target, width, height, abc, sums);
+  launch_pdl(ssim_hmoments_kernel, grid, block, 0, s, win, image, target, width, height, hm, sums);
+  launch_pdl(ssim_vmap_kernel, grid, block, 0, s, win, hm, image, target, width, height, abc, sums);
   int launches = 2;
   if (dl_dimage) {
     const float nterms = 3.f * (float)npix;
-    ssim_habc_kernel<<<grid, block, 0, s>>>(win, abc, width, height, habc);
-    ssim_grad_kernel<<<grid, block, 0, s>>>(win, habc, image, target, width, height, (1.f - lambda) / nterms,
-                                            lambda / nterms, dl_dimage);
+    launch_pdl(ssim_habc_kernel, grid, block, 0, s, win, abc, width, height, habc);
+    launch_pdl(ssim_grad_kernel, grid, block, 0, s, win, habc, image, target, width, height, (1.f - lambda) / nterms,
+               lambda / nterms, dl_dimage);
     launches += 2;
   }
   ctx->launches += launches;

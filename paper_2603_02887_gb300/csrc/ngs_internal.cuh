@@ -350,8 +350,9 @@ void launch_emit_pairs(const float4* rec, const uint32_t* order, const uint32_t*
 // keys[i] = global tile of pair i << 32 | bits(depth of record vals[i]) (diagnostics).
 void launch_compose_keys(const uint32_t* tiles, const uint32_t* vals, const float4* rec, const ViewParams* views,
                          uint32_t n_per_view, uint32_t n_views, uint32_t npairs, uint64_t* keys, cudaStream_t s);
-// [start, end) of every global tile's pairs (zero-length ranges stay (0, 0)); npairs_cap items are
-// covered by the grid, of which the first *npairs_dev are valid if npairs_dev is not null.
+// [start, end) of every global tile's pairs into `ranges`, which the caller has zeroed (zero-length ranges
+// stay (0, 0)); npairs_cap items are covered by the grid, of which the first *npairs_dev are valid if
+// npairs_dev is not null.
 void launch_tile_ranges(const uint32_t* tiles, const uint32_t* vals, const ViewParams* views, uint32_t n_per_view,
                         uint32_t n_views, uint32_t npairs_cap, const uint32_t* npairs_dev, uint32_t ntiles,
                         uint2* ranges, cudaStream_t s);

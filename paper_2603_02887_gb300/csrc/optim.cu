@@ -42,6 +42,7 @@ struct AdamArgs {
 };
 
 __global__ void adam_kernel(AdamArgs a, int64_t total) {
+  pdl_wait();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t i;
     const int gi = group_of(e, a.end, i);
@@ -58,6 +59,7 @@ __global__ void adam_kernel(AdamArgs a, int64_t total) {
 
 __global__ void accumulate_kernel(const float* __restrict__ d_means, int64_t n, float* __restrict__ accum,
                                   float* __restrict__ count) {
+  pdl_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float x = d_means[3 * i], y = d_means[3 * i + 1], z = d_means[3 * i + 2];
     const float norm = sqrtf(x * x + y * y + z * z);
@@ -223,7 +225,7 @@ NGS_API int ngs_adam_step(ngs_ctx* ctx, int64_t n, int32_t sh_degree, const ngs_
   a.c1 = (float)(1.0 / (1.0 - pow((double)cfg->beta1, (double)cfg->step)));
   a.c2 = (float)(1.0 / (1.0 - pow((double)cfg->beta2, (double)cfg->step)));
   a.bounded = cfg->bounded != 0;
-  adam_kernel<<<grid_for(acc), 256, 0, (cudaStream_t)stream>>>(a, acc);
+  launch_pdl(adam_kernel, grid_for(acc), 256, 0, (cudaStream_t)stream, a, acc);
   ctx->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("adam launch: ") + cudaGetErrorString(e));
@@ -236,7 +238,7 @@ NGS_API int ngs_accumulate_grad_norm(ngs_ctx* ctx, int64_t n, const float* d_mea
   if (n < 0 || (n > 0 && (!d_means || !accum || !count)))
     return fail(ctx, NGS_ERR_INVALID_ARG, "accumulate: null array or n < 0");
   if (n == 0) return NGS_OK;
-  accumulate_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(d_means, n, accum, count);
+  launch_pdl(accumulate_kernel, grid_for(n), 256, 0, (cudaStream_t)stream, d_means, n, accum, count);
   ctx->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("accumulate launch: ") + cudaGetErrorString(e));

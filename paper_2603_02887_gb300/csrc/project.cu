@@ -379,6 +379,7 @@ __global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, const Vie
 __global__ void __launch_bounds__(256) emit_pairs_kernel(const float4* rec, const uint32_t* order,
                                                          const uint32_t* offsets, const ViewParams* __restrict__ views,
                                                          RenderParams rp, uint32_t* tiles, uint32_t* vals) {
+  pdl_wait();
   uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= rp.n_records) return;
   uint32_t off = offsets[s], end = offsets[s + 1];
@@ -661,7 +662,7 @@ void launch_project(const ngs_gaussians& g, const ViewParams* views, const CamPa
 void launch_emit_pairs(const float4* rec, const uint32_t* order, const uint32_t* offsets, const ViewParams* views,
                        const RenderParams& rp, uint32_t* tiles, uint32_t* vals, cudaStream_t s) {
   if (rp.n_records == 0) return;
-  emit_pairs_kernel<<<(rp.n_records + 255) / 256, 256, 0, s>>>(rec, order, offsets, views, rp, tiles, vals);
+  launch_pdl(emit_pairs_kernel, (rp.n_records + 255) / 256, 256, 0, s, rec, order, offsets, views, rp, tiles, vals);
 }
 
 template <int DEG, bool VEC>

@@ -308,6 +308,7 @@ __global__ void tile_ranges_kernel(const uint32_t* __restrict__ tiles, const uin
                                    const ViewParams* __restrict__ views, uint32_t n_per_view, uint32_t n_views,
                                    uint32_t npairs_cap, const uint32_t* __restrict__ npairs_dev,
                                    uint2* __restrict__ ranges) {
+  pdl_wait();
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t npairs = npairs_dev ? min(*npairs_dev, npairs_cap) : npairs_cap;
   if (i >= npairs) return;
@@ -336,6 +337,7 @@ __device__ __forceinline__ uint32_t cost_bucket(uint2 r) {
 
 __global__ void __launch_bounds__(256) tile_bucket_count_kernel(const uint2* __restrict__ ranges, uint32_t ntiles,
                                                                 uint32_t* __restrict__ counts) {
+  pdl_wait();
   __shared__ uint32_t s_cnt[kCostBuckets];
   if (threadIdx.x < kCostBuckets) s_cnt[threadIdx.x] = 0;
   __syncthreads();
@@ -375,7 +377,7 @@ void launch_tile_order(const uint2* ranges, uint32_t ntiles, uint32_t* sched, ui
                        int* launches) {
   if (ntiles == 0) return;
   const unsigned blocks = (ntiles + 255) / 256;
-  tile_bucket_count_kernel<<<blocks, 256, 0, s>>>(ranges, ntiles, sched + 2);
+  launch_pdl(tile_bucket_count_kernel, blocks, 256, 0, s, ranges, ntiles, sched + 2);
   launch_pdl(tile_bucket_scatter_kernel, blocks, 256, 0, s, ranges, ntiles, sched + 2, sched + 2 + kCostBuckets, work);
   *launches += 2;
 }
@@ -414,10 +416,9 @@ void launch_scan_counts(const uint32_t* tile_count, const uint32_t* order, uint3
 void launch_tile_ranges(const uint32_t* tiles, const uint32_t* vals, const ViewParams* views, uint32_t n_per_view,
                         uint32_t n_views, uint32_t npairs_cap, const uint32_t* npairs_dev, uint32_t ntiles,
                         uint2* ranges, cudaStream_t s) {
-  cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, s);
   if (npairs_cap == 0) return;
-  tile_ranges_kernel<<<(npairs_cap + 255) / 256, 256, 0, s>>>(tiles, vals, views, n_per_view, n_views, npairs_cap,
-                                                              npairs_dev, ranges);
+  launch_pdl(tile_ranges_kernel, (npairs_cap + 255) / 256, 256, 0, s, tiles, vals, views, n_per_view, n_views,
+             npairs_cap, npairs_dev, ranges);
 }
 
 void launch_compose_keys(const uint32_t* tiles, const uint32_t* vals, const float4* rec, const ViewParams* views,
