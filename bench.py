@@ -31,6 +31,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MODELS = ("exp", "sub", "lin", "sup")
+# ngs_autotune's pick for this workload on GB300 (render + backward; the bench re-tunes with --autotune):
+# fixed so that runs are reproducible and the recorded ncu traffic (profiles/composite_traffic.json)
+# applies to the launches timed.
+TUNED_OPTIONS = "exp=8x8/64/persistent,sub=16x16/128/persistent,lin=16x16/128/persistent,sup=16x16/128/persistent"
 METRIC = "Mpix/s fwd & fwd+bwd per transmittance model; overdraw/pixel; p50/p99 latency"
 WORKLOAD = "single view, 500k clustered Gaussians (SH 3, FP32), 1920x1080, 4 transmittance models, fwd+bwd"
 
@@ -47,6 +51,10 @@ def parse():
     p.add_argument("--tile", default=None, help="fixed tile shape WxH (default: autotuned per model)")
     p.add_argument("--chunk", type=int, default=None, help="records staged per round (default: autotuned)")
     p.add_argument("--schedule", default=None, choices=["tiles", "persistent"], help="(default: autotuned)")
+    p.add_argument("--options", default=TUNED_OPTIONS,
+                   help="per-model launch options, model=WxH/chunk/schedule, comma-separated (models not named "
+                        "are autotuned); the default is what ngs_autotune picked for this workload on GB300")
+    p.add_argument("--autotune", action="store_true", help="autotune every model's launch options instead")
     p.add_argument("--no-graphs", action="store_true", help="launch the render phases directly")
     p.add_argument("--streams", type=int, default=2,
                    help="renderer contexts, each on its own stream; the models take them in turn, so that one "
@@ -324,7 +332,7 @@ def run_ours(args):
         for k in ("project", "depth_sort", "scan_emit", "tile_sort", "tile_ranges", "composite_fwd"):
             stage_ms[k] = stage_direct[k][0] / 2
     dominant = max(stage_ms, key=stage_ms.get)
-    roof = roofline(dominant, stage_ms, frames, ods, args.gaussians, measured_peaks(), clk)
+    roof = roofline(dominant, stage_ms, frames, ods, args.gaussians, measured_peaks(), clk, opts)
 
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world, "steps": K,
@@ -396,7 +404,41 @@ def _walked_and_composited(frame, od):
     return walked, float(od.double().sum())
 
 
-def roofline(dominant, stage_ms, frames, ods, n_gauss, peaks, clk):
+TRAFFIC_RECORD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "composite_traffic.json")
+TRAFFIC_SOURCES = ("paper_2603_02887_gb300/csrc/composite.cu", "paper_2603_02887_gb300/csrc/ngs_internal.cuh")
+
+
+def _options_key(o):
+    return f"{o['tile_w']}x{o['tile_h']}/{o['chunk']}/{'persistent' if int(o['schedule']) == 1 else 'tiles'}"
+
+
+def measured_traffic(kernel, opts):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture (profiles/composite_traffic.json),
+    averaged over the models, if that capture was taken of the current compositing sources and of these
+    per-model launch options; else (None, reason)."""
+    import hashlib
+    try:
+        with open(TRAFFIC_RECORD) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None, "no ncu capture recorded"
+    h = hashlib.sha256()
+    root = os.path.dirname(os.path.abspath(__file__))
+    for p in TRAFFIC_SOURCES:
+        with open(os.path.join(root, p), "rb") as f:
+            h.update(f.read())
+    entry = rec.get("kernels", {}).get(kernel)
+    if entry is None:
+        return None, f"no ncu capture of {kernel} recorded"
+    if rec.get("source_sha256") != h.hexdigest():
+        return None, "the compositing sources changed since the recorded ncu capture"
+    per = entry.get("bytes_per_launch", {})
+    if any(m not in per or rec.get("options", {}).get(m) != _options_key(opts[m]) for m in MODELS):
+        return None, "the recorded ncu capture used other launch options"
+    return float(np.mean([per[m] for m in MODELS])), rec.get("command", "")
+
+
+def roofline(dominant, stage_ms, frames, ods, n_gauss, peaks, clk, opts=None):
     """Roofline of the dominant stage, per launch (one launch per model per step).
 
     Compositing stages are bound by FP32 issue: achieved = algorithmic FLOPs / CUDA-event time against
@@ -416,8 +458,12 @@ def roofline(dominant, stage_ms, frames, ods, n_gauss, peaks, clk):
         t = stage_ms[dominant] / len(frames) * 1e-3
         achieved = flops / t / 1e12
         peak = sm_count * 128 * 2 * 2070e6 / 1e12
+        traffic, note = measured_traffic(dominant, opts) if opts else (None, "launch options unknown")
         out = {"bound": "alu", "kernel": dominant, "achieved": round(achieved, 3), "peak": round(peak, 2),
-               "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+               "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+               "traffic": None if traffic is None else round(traffic),
+               "traffic_source": note if traffic is None else "ncu dram__bytes_read.sum + dram__bytes_write.sum per "
+                                                                "launch, mean over the models: " + note,
                "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts and max clock)",
                "flops_per_launch": flops}
         if clk.get("sm_mhz"):
@@ -447,11 +493,26 @@ def launch_options(args, r, params, cams, reps=2):
     from paper_2603_02887_gb300.render import default_options
     if fixed:
         return {m: default_options(**fixed) for m in MODELS}, "command line"
+    given = {}
+    for item in ("" if args.autotune else (args.options or "")).split(","):
+        if item.strip():
+            m, spec = item.split("=")
+            tile, chunk, sched = spec.split("/")
+            tw, th = (int(v) for v in tile.split("x"))
+            given[m.strip()] = default_options(tile_w=tw, tile_h=th, chunk=int(chunk),
+                                               schedule={"tiles": 0, "persistent": 1}[sched])
     out = {}
     for m in MODELS:
-        best, _ = r.autotune(params, cams, m, backward=True, reps=reps)
-        out[m] = best
-    return out, f"autotuned (render + backward, median of {reps} with L2 cleared before each, 18 candidates per model)"
+        if m in given:
+            out[m] = given[m]
+        else:
+            best, _ = r.autotune(params, cams, m, backward=True, reps=reps)
+            out[m] = best
+    tuned = f"autotuned (render + backward, median of {reps} with L2 cleared before each, 18 candidates per model)"
+    if not given:
+        return out, tuned
+    src = "fixed (--options; ngs_autotune's pick for this workload)" if args.options == TUNED_OPTIONS else "--options"
+    return out, src if len(given) == len(MODELS) else f"{src} for {sorted(given)}, else {tuned}"
 
 
 def run_batched(args, r, dev, single_view_models):
