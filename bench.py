@@ -480,6 +480,20 @@ def roofline(dominant, stage_ms, frames, ods, n_gauss, peaks, clk, opts=None):
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
 
+def parse_options(spec=TUNED_OPTIONS) -> dict:
+    """Per-model launch options from `model=WxH/chunk/schedule,...` (the bench's default: TUNED_OPTIONS)."""
+    from paper_2603_02887_gb300.render import default_options
+    out = {}
+    for item in (spec or "").split(","):
+        if item.strip():
+            m, opt = item.split("=")
+            tile, chunk, sched = opt.split("/")
+            tw, th = (int(v) for v in tile.split("x"))
+            out[m.strip()] = default_options(tile_w=tw, tile_h=th, chunk=int(chunk),
+                                             schedule={"tiles": 0, "persistent": 1}[sched])
+    return out
+
+
 def launch_options(args, r, params, cams, reps=2):
     """Per-model launch options: the fixed ones given on the command line, else the library's autotuner
     (render + backward timed under every tile shape x chunk x schedule on this very workload)."""
@@ -493,14 +507,7 @@ def launch_options(args, r, params, cams, reps=2):
     from paper_2603_02887_gb300.render import default_options
     if fixed:
         return {m: default_options(**fixed) for m in MODELS}, "command line"
-    given = {}
-    for item in ("" if args.autotune else (args.options or "")).split(","):
-        if item.strip():
-            m, spec = item.split("=")
-            tile, chunk, sched = spec.split("/")
-            tw, th = (int(v) for v in tile.split("x"))
-            given[m.strip()] = default_options(tile_w=tw, tile_h=th, chunk=int(chunk),
-                                               schedule={"tiles": 0, "persistent": 1}[sched])
+    given = {} if args.autotune else parse_options(args.options)
     out = {}
     for m in MODELS:
         if m in given:

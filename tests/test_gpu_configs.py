@@ -1,5 +1,6 @@
 """GPU parity at the full sizes of the benchmark configurations, in the launch configuration bench.py
-times (16x16 tiles), on outputs the FP64 oracle computes one by one: windows of the full frame.
+times (its per-model launch options: exponential 8x8 tiles, quadratic 16x16, persistent schedule), on
+outputs the FP64 oracle computes one by one: windows of the full frame.
 
 * single large view: 500k clustered Gaussians (SH 3) at 1920x1080, forward for the four models, on three
   windows (centre, an off-centre region, and a stretch of the bottom edge, where the 16-pixel tiles are
@@ -19,6 +20,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
+import bench  # noqa: E402
 import oracle  # noqa: E402
 from paper_2603_02887_gb300 import synth  # noqa: E402
 from paper_2603_02887_gb300.render import PARAM_KEYS, Renderer  # noqa: E402
@@ -26,6 +28,7 @@ from tests.gpu_util import describe_mismatch, grad_mismatch, upload  # noqa: E40
 
 MODELS = ["exp", "sub", "lin", "sup"]
 NT = os.cpu_count() or 4
+OPTS = bench.parse_options()  # the launch options bench.py times
 
 
 @pytest.fixture(scope="module")
@@ -44,7 +47,7 @@ def single_view():
 def test_single_view_500k_1080p_windows(rnd, single_view, model):
     scene, cam = single_view
     params = upload(scene)
-    image, overdraw, _ = rnd.render(params, cam, model)
+    image, overdraw, _ = rnd.render(params, cam, model, OPTS[model])
     img, od = image.cpu().numpy(), overdraw.cpu().numpy()
     for win in ((936, 516, 48, 48), (400, 300, 40, 40), (900, 1080 - 13, 64, 13)):
         x0, y0, w, h = win
@@ -68,7 +71,7 @@ def test_differentiation_1m_crop_gradients(rnd, diff_scene, model):
     win = (520, 300, 256, 256)
     x0, y0, w, h = win
     params = upload(scene)
-    image, overdraw, frame = rnd.render(params, cam, model)
+    image, overdraw, frame = rnd.render(params, cam, model, OPTS[model])
     ref0 = oracle.render(scene, cam, model, window=win, nthreads=NT)
     ok = ~ref0["fragile"]
     err = np.abs(image.cpu().numpy()[y0:y0 + h, x0:x0 + w] - ref0["image"])[ok]
@@ -98,7 +101,7 @@ def test_differentiation_1m_finite_differences(rnd, diff_scene):
     x0, y0, w, h = win
     model = "sup"
     params = upload(scene)
-    _, od0, frame = rnd.render(params, cam, model)
+    _, od0, frame = rnd.render(params, cam, model, OPTS[model])
     g = np.zeros((cam["height"], cam["width"], 3), np.float32)
     g[y0:y0 + h, x0:x0 + w] = synth.upstream_gradient(h, w, seed=12)
     gt = torch.from_numpy(g).cuda()
@@ -121,7 +124,7 @@ def test_differentiation_1m_finite_differences(rnd, diff_scene):
         losses, ods = [], []
         for sgn in (1, -1):
             flat[gi, j] = th + sgn * hstep
-            img, od, _ = rnd.render(params, cam, model)
+            img, od, _ = rnd.render(params, cam, model, OPTS[model])
             losses.append(float((img.double() * gt.double()).sum()))
             ods.append(od)
         flat[gi, j] = th

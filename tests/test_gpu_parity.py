@@ -122,9 +122,9 @@ def test_tile_shapes_bit_identical(rnd):
             assert np.array_equal(img, outs[0][0]) and np.array_equal(od, outs[0][1]), model
 
 
-def _backward_check(rnd, scene, cam, model, seed=3):
+def _backward_check(rnd, scene, cam, model, seed=3, options=None):
     params = upload(scene)
-    image, overdraw, frame = rnd.render(params, cam, model)
+    image, overdraw, frame = rnd.render(params, cam, model, options)
     ref0 = oracle.render(scene, cam, model, nthreads=NT)
     g = synth.upstream_gradient(cam["height"], cam["width"], seed=seed).astype(np.float64)
     g *= ~ref0["fragile"][..., None]
@@ -151,6 +151,15 @@ def test_backward_matches_oracle_tiny(rnd, model):
 def test_backward_matches_oracle_clustered(rnd, model):
     _backward_check(rnd, synth.clustered_scene(6000, seed=6, sh_degree=3), synth.outside_camera(160, 120, 12.0),
                     model)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_backward_matches_oracle_bench_options(rnd, model):
+    """The replay in the launch configuration bench.py times for this model (exponential: 8x8 tiles, chunk
+    64; quadratic: 16x16, chunk 128; persistent schedule), on a scene spanning many tiles."""
+    import bench
+    _backward_check(rnd, synth.clustered_scene(6000, seed=8, sh_degree=3), synth.outside_camera(150, 110, 12.0),
+                    model, options=bench.parse_options()[model])
 
 
 def test_forward_is_deterministic(rnd):
