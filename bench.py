@@ -56,6 +56,8 @@ def parse():
                         "are autotuned); the default is what ngs_autotune picked for this workload on GB300")
     p.add_argument("--autotune", action="store_true", help="autotune every model's launch options instead")
     p.add_argument("--no-graphs", action="store_true", help="launch the render phases directly")
+    p.add_argument("--no-async", action="store_true",
+                   help="synchronous renders (the host waits for each render's pair count)")
     p.add_argument("--streams", type=int, default=2,
                    help="renderer contexts, each on its own stream; the models take them in turn, so that one "
                         "model's kernels run while the host waits for another's pair count")
@@ -204,6 +206,8 @@ def run_ours(args):
         img, _, _ = rs[owner[m]].render(params, cam, m, opts[m], frame=frames[m], image=images[m], overdraw=ods[m])
         dl[m] = torch.sign(img - tgt).contiguous()
         r.recycle(f)
+        # asynchronous renders from here on: the render above set the frame's pair capacity
+        frames[m].set_async(not args.no_async)
     del target_params
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -270,6 +274,8 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     launches = sum(x.launch_count() for x in rs) - launches0
+    for f in frames.values():  # raises if an asynchronous render exceeded its frame's capacity
+        f.status()
 
     def stage_steps(n, graphs, events=None):
         # per-stage CUDA-event times of n further steps, models one after another (and per-model events)
@@ -344,7 +350,7 @@ def run_ours(args):
                    "launch_options": {m: {k: opts[m][k] for k in ("tile_w", "tile_h", "chunk", "schedule")}
                                       for m in MODELS},
                    "launch_options_source": tuning, "cuda_graphs": not args.no_graphs,
-                   "streams": S,
+                   "streams": S, "async_renders": not args.no_async,
                    "step": "per model: render + path-replay backward",
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"views x{world}",
                    "pairs_per_view": int(frames["exp"].view()["n_pairs"])},
@@ -728,6 +734,8 @@ def run_e2e(args, rs, streams, owner, scene, cam, opts, dl, dev, world):
             out_g={m: {k: torch.empty(v.shape).pin_memory() for k, v in host.items()} for m in MODELS},
             frames={m: rs[owner[m]].frame() for m in MODELS},
             compute_done=[], reads_done=None, inputs=None))
+        for f in sets[-1]["frames"].values():  # asynchronous after each frame's first render
+            f.set_async(not args.no_async)
     h2d = sum(v.numel() * 4 for v in host.values()) + sum(v.numel() * 4 for v in host_dl.values())
     d2h = sum(H * W * 16 + sum(v.numel() * 4 for v in host.values()) for _ in MODELS)
 
@@ -799,6 +807,9 @@ def run_e2e(args, rs, streams, owner, scene, cam, opts, dl, dev, world):
     e.record(main)  # after the last reads
     torch.cuda.synchronize()
     ms = s.elapsed_time(e) / K
+    for b in sets:
+        for f in b["frames"].values():  # raises if an asynchronous render exceeded its frame's capacity
+            f.status()
     for b in sets:
         for m, f in b["frames"].items():
             rs[owner[m]].recycle(f)

@@ -42,6 +42,9 @@ extern "C" {
 #define NGS_ERR_DEVICE_CHECK (-5)  /* a kernel's own bounds check fired (in this or an earlier call   */
                                    /* on the context; reported at the next render); that output was  */
                                    /* not valid                                                       */
+#define NGS_ERR_CAPACITY (-6)      /* an asynchronous render met more (tile, Gaussian) pairs than its */
+                                   /* frame's capacity: its output is not valid; the capacity has     */
+                                   /* grown, so rendering again succeeds (ngs_frame_status)           */
 
 /* ---- transmittance models (Table 1) ----------------------------------------------------------- */
 #define NGS_MODEL_EXP 0  /* T = exp(-tau): pbar_i = alpha_i prod_{j<i}(1 - alpha_j) (standard 3DGS)      */
@@ -160,13 +163,31 @@ NGS_API const char* ngs_last_error(const ngs_ctx* ctx);
 NGS_API int ngs_frame_create(ngs_ctx* ctx, ngs_frame** out);
 NGS_API void ngs_frame_destroy(ngs_frame* frame);
 
+/* Asynchronous renders into a frame (off by default). With `enable` set, ngs_render and ngs_render_batch
+ * into this frame enqueue the whole pipeline without the host synchronisation after binning: the pair
+ * buffers are sized from the frame's pair capacity (the largest pair count its earlier renders met, plus a
+ * quarter) and the kernels after binning read the count from device memory. A render whose count exceeds
+ * the capacity writes only the pairs that fit, so its image and replay state are not valid; it is reported
+ * by ngs_frame_status. A frame without a capacity yet (no earlier render) renders synchronously, which sets
+ * one. Results of a render that fits are bit-identical to the synchronous render.
+ * Errors: NGS_ERR_INVALID_ARG for a NULL frame. */
+NGS_API int ngs_frame_set_async(ngs_frame* frame, int enable);
+
+/* Waits for the frame's last render and reports every render into the frame since the previous call:
+ * NGS_OK; NGS_ERR_CAPACITY if an asynchronous one exceeded the frame's pair capacity (the capacity then
+ * grows to the count met plus a quarter, so rendering again succeeds); NGS_ERR_DEVICE_CHECK if a kernel
+ * bounds check fired. *pairs (may be NULL) receives the last render's pair count. Clears what it reports.
+ * Errors: NGS_ERR_INVALID_ARG for a NULL frame or a frame that holds no render; NGS_ERR_CUDA. */
+NGS_API int ngs_frame_status(ngs_frame* frame, int64_t* pairs);
+
 /* Render (Eq. generalized_gaussian with pbar_i from Eq. nexp_p):
  *   image[y][x][3] = sum_i E_i pbar_i + L_b Tbar_end over the splats i of pixel (x, y), front to back by
  *   (FP32 view depth, Gaussian index); overdraw[y][x] = number of splats composited at that pixel,
  *   the saturating one included (Fig. 2 "Overdraws"; Table 3 "Avg. OD").
  * `image` is [height][width][3] FP32 and `overdraw` [height][width] int32, both caller-owned device
  * memory; overdraw may be NULL. The frame is overwritten. One host synchronisation happens after
- * binning, to read the number of (tile, Gaussian) pairs and size the sort buffers.
+ * binning, to read the number of (tile, Gaussian) pairs and size the sort buffers (none for a frame in
+ * asynchronous mode that has a capacity, see ngs_frame_set_async).
  * Errors: NGS_ERR_INVALID_ARG for NULL pointers, n < 0, sh_degree outside 0..3, width/height outside
  * 1..16384, an unsupported tile shape, chunk or schedule, kind/param outside the table above. */
 NGS_API int ngs_render(ngs_ctx* ctx, ngs_frame* frame, const ngs_gaussians* g, const ngs_camera* cam,

@@ -14,6 +14,7 @@ NGS_ERR_INVALID_ARG = -1
 NGS_ERR_OUT_OF_MEMORY = -2
 NGS_ERR_CUDA = -3
 NGS_ERR_DEVICE_CHECK = -5
+NGS_ERR_CAPACITY = -6
 NGS_MODEL_EXP = 0
 NGS_MODEL_QUAD = 1
 NGS_MODEL_BLEND = 2
@@ -103,6 +104,8 @@ SIGNATURES = {
     "ngs_last_error": (C.c_char_p, [C.c_void_p]),
     "ngs_frame_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     "ngs_frame_destroy": (None, [C.c_void_p]),
+    "ngs_frame_set_async": (C.c_int, [C.c_void_p, C.c_int]),
+    "ngs_frame_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "ngs_render": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.POINTER(Camera), C.POINTER(Model),
                              C.POINTER(Options), C.c_void_p, C.c_void_p, C.c_void_p]),
     "ngs_render_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Gaussians), C.POINTER(Camera), C.c_int32,
@@ -164,10 +167,17 @@ def load():
 
 
 class NGSError(RuntimeError):
-    pass
+    def __init__(self, msg: str, code: int = 0):
+        super().__init__(msg)
+        self.code = code
+
+
+class CapacityExceeded(NGSError):
+    """An asynchronous render met more pairs than its frame's capacity (which has now grown): render again."""
 
 
 def check(rc: int, ctx) -> None:
     if rc != NGS_OK:
         msg = load().ngs_last_error(ctx)
-        raise NGSError(f"ngs error {rc}: {msg.decode() if msg else ''}")
+        cls = CapacityExceeded if rc == NGS_ERR_CAPACITY else NGSError
+        raise cls(f"ngs error {rc}: {msg.decode() if msg else ''}", rc)

@@ -79,6 +79,21 @@ __global__ void publish_words_kernel(const uint64_t* __restrict__ src, uint64_t*
   __threadfence_system();
 }
 
+// End of an asynchronous render: folds its pair count and error bits into the frame's mapped status
+// (the capacity bit when the count exceeded `cap`) and clears the context's error word for the next render.
+// One thread: the status words are read, modified and written in host memory.
+__global__ void finish_async_kernel(uint64_t* total, uint64_t* status, uint32_t cap) {
+  pdl_wait();
+  if (threadIdx.x != 0) return;
+  const uint64_t count = total[0];
+  const uint64_t err = total[1] | (count > cap ? (uint64_t)kCheckCapacity : 0ull);
+  status[0] = count > status[0] ? count : status[0];
+  status[1] |= err;
+  status[2] = count;
+  total[1] = 0;
+  __threadfence_system();
+}
+
 void publish_words(ngs_ctx* ctx, const uint64_t* src, int n, int slot, cudaStream_t s) {
   launch_pdl(publish_words_kernel, 1, 32, 0, s, src, ctx->d_h_total + slot, n);
 }
@@ -263,7 +278,7 @@ static void phase1(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, cudaStream_
 // Phase 2: key emission, tile sort, tile ranges (+ work list), composite. `cap` items are covered by the
 // sort's grid; with np_dev (graph replays) the kernels read the actual pair count from the device.
 static void phase2(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, uint32_t cap, const uint32_t* np_dev,
-                   cudaStream_t s) {
+                   bool async, cudaStream_t s) {
   const RenderParams& rp = pl.rp;
   const ViewParams* views = f->views.as<ViewParams>();
   cudaEvent_t ev;
@@ -273,7 +288,7 @@ static void phase2(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, uint32_t ca
   if (rp.schedule == NGS_SCHEDULE_PERSISTENT) cudaMemsetAsync(f->sched.p, 0, sizeof(uint32_t) * kSchedWords, s);
   stage_begin(ctx, s, 2, &ev);
   launch_emit_pairs(f->rec.as<float4>(), f->gvals[f->g_final].as<uint32_t>(), f->offsets.as<uint32_t>(), views, rp,
-                    f->ptile[0].as<uint32_t>(), f->pvals[0].as<uint32_t>(), s);
+                    f->ptile[0].as<uint32_t>(), f->pvals[0].as<uint32_t>(), cap, s);
   stage_end(ctx, s, 2, ev, pl.R ? 1 : 0);
   // 4. stable sort of the pairs by view-local tile: the (view, depth) order inside each local tile is kept,
   //    so every (view, tile) list is contiguous and in the order of the 64-bit (tile << 32 | depth) keys
@@ -307,6 +322,10 @@ static void phase2(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, uint32_t ca
   launch_composite_forward(f->rec.as<float4>(), f->pvals[f->p_final].as<uint32_t>(), f->ranges.as<uint2>(), rp, views,
                            pl.image, pl.overdraw, f->state.as<float4>(), work, counter, ctx->num_sms, s);
   stage_end(ctx, s, 5, ev, 1);
+  if (async) {
+    launch_pdl(finish_async_kernel, 1, 32, 0, s, ctx->total.as<uint64_t>(), f->d_status, cap);
+    ctx->launches += 1;
+  }
 }
 
 // Serialised launch arguments of a phase: a captured graph is replayed only while they are unchanged.
@@ -513,28 +532,37 @@ int ngs::render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, co
     k1.add(b->p);
   k1.add(f->h_views);
   k1.add(ctx->h_total);
+  // asynchronous: no host synchronisation; phase 2 is sized by the frame's capacity (set by earlier renders)
+  const bool async = f->async && f->pair_cap > 0 && !admit;
   NGS_TRY(run_phase(ctx, f, 0, k1, s, [&](cudaStream_t st) { phase1(ctx, f, pl, st); }));
   cudaError_t e = cudaEventRecord(f->views_uploaded, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("reading the pair count: ") + cudaGetErrorString(e));
-  const volatile uint64_t* mirror = ctx->h_total + kMirrorTotal;  // written by publish_words
-  if (mirror[1] != 0) {  // a bounds check fired in an earlier call on this context
-    cudaMemsetAsync(ctx->total.as<uint64_t>() + 1, 0, sizeof(uint64_t), s);
-    return fail(ctx, NGS_ERR_DEVICE_CHECK, "a kernel bounds check fired in an earlier call on this context; its "
-                                           "output was not valid");
-  }
-  const uint64_t P = mirror[0];
-  if (P >= (1ull << 31)) return fail(ctx, NGS_ERR_INVALID_ARG, "more than 2^31 (tile, Gaussian) pairs");
-  const uint32_t np = (uint32_t)P;
-  if (admit) NGS_TRY(admit(admit_user, 1, sizeof(uint32_t) * 4 * (size_t)np));
-
-  // phase 2: exact sizes, or, for graph replays, a capacity that a replay reuses while the count fits
-  uint32_t cap = np;
+  uint32_t np = 0, cap = 0;
   const uint32_t* np_dev = nullptr;
-  if (ctx->graphs) {
-    if (np > f->pair_cap) f->pair_cap = (uint32_t)std::min<uint64_t>((uint64_t)np + np / 4 + 1024, (1ull << 31) - 1);
+  if (async) {
+    if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("render: ") + cudaGetErrorString(e));
     cap = f->pair_cap;
     np_dev = reinterpret_cast<const uint32_t*>(ctx->total.p);  // low word of the pair count (< 2^31)
+  } else {
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("reading the pair count: ") + cudaGetErrorString(e));
+    const volatile uint64_t* mirror = ctx->h_total + kMirrorTotal;  // written by publish_words
+    if (mirror[1] != 0) {  // a bounds check fired in an earlier call on this context
+      cudaMemsetAsync(ctx->total.as<uint64_t>() + 1, 0, sizeof(uint64_t), s);
+      return fail(ctx, NGS_ERR_DEVICE_CHECK, "a kernel bounds check fired in an earlier call on this context; its "
+                                             "output was not valid");
+    }
+    const uint64_t P = mirror[0];
+    if (P >= (1ull << 31)) return fail(ctx, NGS_ERR_INVALID_ARG, "more than 2^31 (tile, Gaussian) pairs");
+    np = (uint32_t)P;
+    if (admit) NGS_TRY(admit(admit_user, 1, sizeof(uint32_t) * 4 * (size_t)np));
+    // the capacity that graph replays and asynchronous renders reuse while the count fits
+    if (np > f->pair_cap) f->pair_cap = (uint32_t)std::min<uint64_t>((uint64_t)np + np / 4 + 1024, (1ull << 31) - 1);
+    // phase 2: exact sizes, or, for graph replays, the capacity
+    cap = np;
+    if (ctx->graphs) {
+      cap = f->pair_cap;
+      np_dev = reinterpret_cast<const uint32_t*>(ctx->total.p);
+    }
   }
   for (int k = 0; k < 2; ++k) {
     NGS_TRY(ensure(ctx, f->ptile[k], sizeof(uint32_t) * (size_t)std::max(cap, 1u)));
@@ -545,6 +573,7 @@ int ngs::render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, co
   k2.add(rp);
   k2.add(cap);
   k2.add(np_dev);
+  k2.add(async);
   k2.add(f->g_final);
   k2.add(n_views == 1 ? pl.image : nullptr);  // a batch reads its outputs from the view table
   k2.add(n_views == 1 ? pl.overdraw : nullptr);
@@ -556,10 +585,17 @@ int ngs::render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, co
   for (const DevBuf* b : {&f->rec, &f->gvals[0], &f->gvals[1], &f->offsets, &f->views, &f->ptile[0], &f->ptile[1],
                           &f->pvals[0], &f->pvals[1], &ctx->hist, &f->ranges, &f->work, &f->sched, &f->state})
     k2.add(b->p);
-  NGS_TRY(run_phase(ctx, f, 1, k2, s, [&](cudaStream_t st) { phase2(ctx, f, pl, cap, np_dev, st); }));
+  if (async) k2.add(f->d_status);
+  NGS_TRY(run_phase(ctx, f, 1, k2, s, [&](cudaStream_t st) { phase2(ctx, f, pl, cap, np_dev, async, st); }));
+  if (async) {
+    e = cudaEventRecord(f->done, s);
+    if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("render: ") + cudaGetErrorString(e));
+    f->pending = true;
+  }
+  f->last_async = async;
 
   f->n = pl.n;
-  f->pairs = np;
+  if (!async) f->pairs = np;  // an asynchronous render's count is known once ngs_frame_status has read it
   f->n_views = n_views;
   f->n_pixels = (int64_t)pix_total;
   f->rp = rp;
@@ -642,9 +678,58 @@ NGS_API void ngs_frame_destroy(ngs_frame* f) {
   for (DevBuf* b : bufs) free_buf(*b);
   if (f->h_views) cudaFreeHost(f->h_views);
   if (f->views_uploaded) cudaEventDestroy(f->views_uploaded);
+  if (f->h_status) cudaFreeHost(f->h_status);
+  if (f->done) cudaEventDestroy(f->done);
   for (GraphSlot& g : f->graph)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   delete f;
+}
+
+NGS_API int ngs_frame_set_async(ngs_frame* f, int enable) {
+  if (!f) return NGS_ERR_INVALID_ARG;
+  if (enable && !f->h_status) {
+    void* dev_alias = nullptr;
+    cudaError_t e = cudaHostAlloc((void**)&f->h_status, 3 * sizeof(uint64_t), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&dev_alias, f->h_status, 0);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (f->h_status) cudaFreeHost(f->h_status);
+      f->h_status = nullptr;
+      f->done = nullptr;
+      return fail(f->ctx, NGS_ERR_CUDA, std::string("asynchronous frame: ") + cudaGetErrorString(e));
+    }
+    memset(f->h_status, 0, 3 * sizeof(uint64_t));
+    f->d_status = static_cast<uint64_t*>(dev_alias);
+  }
+  f->async = enable != 0;
+  return NGS_OK;
+}
+
+NGS_API int ngs_frame_status(ngs_frame* f, int64_t* pairs) {
+  if (!f) return NGS_ERR_INVALID_ARG;
+  if (!f->has_render) return fail(f->ctx, NGS_ERR_INVALID_ARG, "frame holds no render");
+  int rc = NGS_OK;
+  if (f->pending) {
+    cudaError_t e = cudaEventSynchronize(f->done);
+    if (e != cudaSuccess) return fail(f->ctx, NGS_ERR_CUDA, std::string("frame status: ") + cudaGetErrorString(e));
+    volatile uint64_t* st = f->h_status;  // written by finish_async_kernel
+    const uint64_t most = st[0], err = st[1], last = st[2];
+    st[0] = 0;
+    st[1] = 0;
+    f->pending = false;
+    if (f->last_async) f->pairs = (int64_t)last;
+    if (err & kCheckCapacity) {
+      f->pair_cap = (uint32_t)std::min<uint64_t>(most + most / 4 + 1024, (1ull << 31) - 1);
+      rc = fail(f->ctx, NGS_ERR_CAPACITY, "an asynchronous render met " + std::to_string(most) +
+                                              " pairs, more than its frame's capacity; the capacity has grown");
+    } else if (err) {
+      rc = fail(f->ctx, NGS_ERR_DEVICE_CHECK, "a kernel bounds check fired in an asynchronous render; its output "
+                                              "was not valid");
+    }
+  }
+  if (pairs) *pairs = f->pairs;
+  return rc;
 }
 
 NGS_API int ngs_render(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, const ngs_camera* cam,
@@ -709,6 +794,11 @@ NGS_API int ngs_frame_view_get(const ngs_frame* fc, ngs_frame_view* out) {
   if (!fc->has_render) return NGS_ERR_INVALID_ARG;
   // the hot path sorts 32-bit tile indices; the 64-bit keys are composed here, after the device is idle
   ngs_frame* f = const_cast<ngs_frame*>(fc);
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(f->ctx, NGS_ERR_CUDA, "frame view: device error");
+  if (f->pending && f->last_async) {  // an asynchronous render's count (its status stays unread)
+    const uint64_t last = static_cast<volatile uint64_t*>(f->h_status)[2];
+    f->pairs = (int64_t)std::min<uint64_t>(last, f->pair_cap);
+  }
   uint32_t np = (uint32_t)f->pairs;
   if (ensure(f->ctx, f->keys64, sizeof(uint64_t) * (size_t)std::max(np, 1u)) != NGS_OK) return NGS_ERR_OUT_OF_MEMORY;
   cudaError_t e = cudaDeviceSynchronize();

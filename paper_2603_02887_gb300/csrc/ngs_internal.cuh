@@ -58,7 +58,8 @@ struct RenderParams {
   uint32_t* check;       // device error word: kernels OR in a kCheck* bit when a bounds check fires
 };
 
-constexpr uint32_t kCheckIndex = 1u;  // a sorted pair named a splat record index >= n_records
+constexpr uint32_t kCheckIndex = 1u;     // a sorted pair named a splat record index >= n_records
+constexpr uint32_t kCheckCapacity = 2u;  // an asynchronous render met more pairs than its capacity
 
 // Geometry of the view holding global tile t. A single view takes it from the kernel parameters (no
 // dependent load before the tile's work starts); a batch looks it up in the view table.
@@ -281,7 +282,16 @@ struct ngs_frame {
   ngs::DevBuf work;    // persistent schedule: tiles by descending pair count
   ngs::DevBuf sched;   // persistent schedule: kSchedWords counters (see launch_tile_order)
   ngs::GraphSlot graph[2];  // phase 1 (projection .. pair count) and phase 2 (emission .. composite)
-  uint32_t pair_cap = 0;    // pair capacity of the captured phase 2
+  uint32_t pair_cap = 0;    // pair capacity of the captured phase 2 and of asynchronous renders
+  // asynchronous renders (ngs_frame_set_async): a kernel at the end of each one writes its status into a
+  // mapped pinned mirror: [0] the largest pair count since the last ngs_frame_status, [1] the error bits
+  // since then (kCheck*), [2] the last render's pair count; `done` is recorded after it
+  bool async = false;
+  bool pending = false;              // an asynchronous render whose status has not been read
+  bool last_async = false;           // the last render was asynchronous
+  uint64_t* h_status = nullptr;
+  uint64_t* d_status = nullptr;
+  cudaEvent_t done = nullptr;
   int g_final = 0;  // which gvals[] holds the depth-sorted Gaussian order
   int p_final = 0;  // which ptile[]/pvals[] hold the sorted pairs
 };
@@ -345,8 +355,9 @@ size_t scan_tmp_words(uint32_t n);
 // the records are in (view, depth) order, so sorting the pairs stably by the local tile alone orders them by
 // (local tile, view, depth): every (view, tile) list is contiguous and in the order of the 64-bit keys
 // (global tile << 32 | depth bits).
+// Pairs at slots >= cap are not written (an asynchronous render whose count exceeds its capacity).
 void launch_emit_pairs(const float4* rec, const uint32_t* order, const uint32_t* offsets, const ViewParams* views,
-                       const RenderParams& rp, uint32_t* tiles, uint32_t* vals, cudaStream_t s);
+                       const RenderParams& rp, uint32_t* tiles, uint32_t* vals, uint32_t cap, cudaStream_t s);
 // keys[i] = global tile of pair i << 32 | bits(depth of record vals[i]) (diagnostics).
 void launch_compose_keys(const uint32_t* tiles, const uint32_t* vals, const float4* rec, const ViewParams* views,
                          uint32_t n_per_view, uint32_t n_views, uint32_t npairs, uint64_t* keys, cudaStream_t s);

@@ -378,12 +378,13 @@ __global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, const Vie
 
 __global__ void __launch_bounds__(256) emit_pairs_kernel(const float4* rec, const uint32_t* order,
                                                          const uint32_t* offsets, const ViewParams* __restrict__ views,
-                                                         RenderParams rp, uint32_t* tiles, uint32_t* vals) {
+                                                         RenderParams rp, uint32_t* tiles, uint32_t* vals,
+                                                         uint32_t cap) {
   pdl_wait();
   uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= rp.n_records) return;
-  uint32_t off = offsets[s], end = offsets[s + 1];
-  if (off == end) return;
+  uint32_t off = offsets[s], end = min(offsets[s + 1], cap);  // slots past the capacity are not written
+  if (off >= end) return;
   uint32_t id = order[s];
   const uint32_t view = id / rp.n_gaussians;
   rp.tiles_x = views[view].tiles_x;
@@ -660,9 +661,10 @@ void launch_project(const ngs_gaussians& g, const ViewParams* views, const CamPa
 }
 
 void launch_emit_pairs(const float4* rec, const uint32_t* order, const uint32_t* offsets, const ViewParams* views,
-                       const RenderParams& rp, uint32_t* tiles, uint32_t* vals, cudaStream_t s) {
+                       const RenderParams& rp, uint32_t* tiles, uint32_t* vals, uint32_t cap, cudaStream_t s) {
   if (rp.n_records == 0) return;
-  launch_pdl(emit_pairs_kernel, (rp.n_records + 255) / 256, 256, 0, s, rec, order, offsets, views, rp, tiles, vals);
+  launch_pdl(emit_pairs_kernel, (rp.n_records + 255) / 256, 256, 0, s, rec, order, offsets, views, rp, tiles, vals,
+             cap);
 }
 
 template <int DEG, bool VEC>

@@ -128,6 +128,18 @@ class Frame:
             base += h * w
         return out
 
+    def set_async(self, enable: bool = True):
+        """Asynchronous renders into this frame (no host synchronisation after binning; ngs_frame_set_async)."""
+        _abi.check(_abi.load().ngs_frame_set_async(self.handle, int(bool(enable))), self.renderer.ctx)
+
+    def status(self) -> int:
+        """Wait for the frame's last render; return its pair count. Raises _abi.CapacityExceeded if an
+        asynchronous render since the last call met more pairs than the frame's capacity (then render again),
+        _abi.NGSError for other errors (ngs_frame_status)."""
+        n = C.c_int64()
+        _abi.check(_abi.load().ngs_frame_status(self.handle, C.byref(n)), self.renderer.ctx)
+        return int(n.value)
+
     def release(self):
         if self.handle:
             _abi.load().ngs_frame_destroy(self.handle)
@@ -173,6 +185,7 @@ class Renderer:
         return self._pool.pop() if self._pool else Frame(self)
 
     def recycle(self, frame: Frame):
+        frame.set_async(False)
         self._pool.append(frame)
 
     # calls --------------------------------------------------------------------------------------
