@@ -58,9 +58,9 @@ def parse():
     p.add_argument("--no-graphs", action="store_true", help="launch the render phases directly")
     p.add_argument("--no-async", action="store_true",
                    help="synchronous renders (the host waits for each render's pair count)")
-    p.add_argument("--streams", type=int, default=2,
-                   help="renderer contexts, each on its own stream; the models take them in turn, so that one "
-                        "model's kernels run while the host waits for another's pair count")
+    p.add_argument("--streams", type=int, default=4,
+                   help="renderer contexts, each on its own stream; the models take them in turn, so that their "
+                        "kernels overlap (with asynchronous renders, one per model measured best on GB300)")
     p.add_argument("--no-batched", action="store_true", help="skip the batched multi-view measurement")
     p.add_argument("--batched-gaussians", type=int, default=3_000_000)
     p.add_argument("--batched-views", type=int, default=32)
