@@ -500,7 +500,7 @@ def parse_options(spec=TUNED_OPTIONS) -> dict:
     return out
 
 
-def launch_options(args, r, params, cams, reps=2):
+def launch_options(args, r, params, cams, reps=2, use_options=True):
     """Per-model launch options: the fixed ones given on the command line, else the library's autotuner
     (render + backward timed under every tile shape x chunk x schedule on this very workload)."""
     fixed = {}
@@ -513,7 +513,8 @@ def launch_options(args, r, params, cams, reps=2):
     from paper_2603_02887_gb300.render import default_options
     if fixed:
         return {m: default_options(**fixed) for m in MODELS}, "command line"
-    given = {} if args.autotune else parse_options(args.options)
+    # --options holds the single view's tuned options: other workloads (use_options=False) tune their own
+    given = {} if args.autotune or not use_options else parse_options(args.options)
     out = {}
     for m in MODELS:
         if m in given:
@@ -543,10 +544,10 @@ def run_batched(args, r, dev, single_view_models):
     params = {k: torch.from_numpy(np.ascontiguousarray(scene[k])).to(dev) for k in PARAM_KEYS}
     del scene
     npix = sum(c["width"] * c["height"] for c in cams)
-    opts, tuning = launch_options(args, r, params, cams, reps=3)
+    opts, tuning = launch_options(args, r, params, cams, reps=3, use_options=False)
     # the one-view-at-a-time form gets its own tuning, on the largest view
     big = max(cams, key=lambda c: c["width"] * c["height"])
-    vopts, _ = launch_options(args, r, params, [big], reps=3)
+    vopts, _ = launch_options(args, r, params, [big], reps=3, use_options=False)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     out = {"gaussians": args.batched_gaussians, "views": len(cams), "mpix_per_batch": round(npix / 1e6, 3),
            "resolutions": sorted({f"{c['width']}x{c['height']}" for c in cams}), "launch_options_source": tuning,
