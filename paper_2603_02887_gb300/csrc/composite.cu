@@ -74,9 +74,11 @@ struct TileGeom {
 // The forward keeps one pixel per thread (a thread retires with its pixel); the replay takes two, so that
 // the warp reduces once per 64 pixels.
 constexpr int kBwdPix = 2;
-// Replay: a splat hit by at most this many lanes of a warp is added by those lanes directly (measured on
-// GB300: 24 beats 4, 16 and 32 at 500k Gaussians / 1080p).
-constexpr int kDirectLanes = 24;
+// Replay: a splat hit by at most this many lanes of a warp is added by those lanes directly; more go through
+// the warp reduction (32 atomics on one address serialise). Measured on GB300 with the packed replay at
+// 500k Gaussians / 1080p: on 8x8 tiles 16 beats 8, 12, 24 and 32 (exponential replay 0.351 ms against
+// 0.379 at 24 and 0.80 at 32), on 16x16 tiles 16 and 24 tie.
+constexpr int kDirectLanes = 16;
 
 // ---- forward ---------------------------------------------------------------------------------------
 
