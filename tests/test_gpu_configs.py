@@ -1,6 +1,6 @@
 """GPU parity at the full sizes of the benchmark configurations, in the launch configuration bench.py
-times (its per-model launch options: exponential 8x8 tiles, quadratic 16x16, persistent schedule), on
-outputs the FP64 oracle computes one by one: windows of the full frame.
+times (its per-model launch options, bench.TUNED_OPTIONS: exponential on 8x8 tiles, the quadratic models
+on 16x16), on outputs the FP64 oracle computes one by one: windows of the full frame.
 
 * single large view: 500k clustered Gaussians (SH 3) at 1920x1080, forward for the four models, on three
   windows (centre, an off-centre region, and a stretch of the bottom edge, where the 16-pixel tiles are

@@ -155,8 +155,8 @@ def test_backward_matches_oracle_clustered(rnd, model):
 
 @pytest.mark.parametrize("model", MODELS)
 def test_backward_matches_oracle_bench_options(rnd, model):
-    """The replay in the launch configuration bench.py times for this model (exponential: 8x8 tiles, chunk
-    32; quadratic: 16x16, chunk 128; persistent schedule), on a scene spanning many tiles."""
+    """The replay in the launch configuration bench.py times for this model (bench.TUNED_OPTIONS:
+    exponential on 8x8 tiles, the quadratic models on 16x16), on a scene spanning many tiles."""
     import bench
     _backward_check(rnd, synth.clustered_scene(6000, seed=8, sh_degree=3), synth.outside_camera(150, 110, 12.0),
                     model, options=bench.parse_options()[model])
