@@ -238,8 +238,8 @@ struct RenderPlan {
   int32_t* overdraw;
 };
 
-// Phase 1: view table upload, projection, depth sort, scan of the tile counts, and the copy of the pair
-// count (and the device error word) to pinned host memory. Launches only.
+// Phase 1: view table upload, projection, depth sort, scan of the tile counts, and the pair count (and the
+// device error word) written into the context's mapped pinned mirror. Launches only.
 static void phase1(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, cudaStream_t s) {
   const RenderParams& rp = pl.rp;
   const ViewParams* views = f->views.as<ViewParams>();
@@ -265,7 +265,7 @@ static void phase1(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, cudaStream_
     f->g_final = radix_sort_u32(k2, v2, pl.n, rp.n_views, nullptr, 0, 32, ctx->hist.as<uint32_t>(), s, &launches);
   }
   stage_end(ctx, s, 1, ev, launches);
-  // 3. exclusive scan of the tile counts in (view, depth) order; the pair count goes to the host
+  // 3. exclusive scan of the tile counts in (view, depth) order; the pair count goes to the host mirror
   stage_begin(ctx, s, 2, &ev);
   launches = 0;
   launch_scan_counts(f->tile_count.as<uint32_t>(), f->gvals[f->g_final].as<uint32_t>(), pl.R,
