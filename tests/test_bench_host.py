@@ -1,0 +1,76 @@
+"""Host-side logic of bench.py (no GPU): per-model launch options and the guard on the recorded ncu traffic,
+which is reported only while the compositing sources and the launch options match the capture."""
+import hashlib
+import json
+import os
+
+import pytest
+
+import bench
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    from paper_2603_02887_gb300 import build
+
+    build.build()  # the options come from ngs_default_options (no GPU needed)
+
+
+def test_tuned_options_parse_for_every_model():
+    opts = bench.parse_options()
+    assert set(opts) == set(bench.MODELS)
+    for o in opts.values():
+        assert (o["tile_w"], o["tile_h"]) in ((8, 8), (16, 16), (16, 32))
+        assert o["chunk"] in (o["tile_w"] * o["tile_h"] // 2, o["tile_w"] * o["tile_h"], 2 * o["tile_w"] * o["tile_h"])
+        assert o["schedule"] in (0, 1)
+        assert bench._options_key(o) in bench.TUNED_OPTIONS
+    custom = bench.parse_options("exp=16x32/256/tiles")
+    assert list(custom) == ["exp"] and custom["exp"]["schedule"] == 0 and custom["exp"]["tile_h"] == 32
+
+
+def _record(tmp_path, sha, options, per_model):
+    rec = {"source_sha256": sha, "options": options, "command": "ncu ...",
+           "kernels": {"composite_bwd": {"bytes_per_launch": per_model}}}
+    p = tmp_path / "traffic.json"
+    p.write_text(json.dumps(rec))
+    return str(p)
+
+
+def _current_sha():
+    h = hashlib.sha256()
+    root = os.path.dirname(os.path.abspath(bench.__file__))
+    for p in bench.TRAFFIC_SOURCES:
+        with open(os.path.join(root, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+@pytest.fixture
+def opts():
+    return bench.parse_options()
+
+
+def test_traffic_reported_when_sources_and_options_match(tmp_path, monkeypatch, opts):
+    per = {m: 100.0 + 10 * i for i, m in enumerate(bench.MODELS)}
+    keys = {m: bench._options_key(o) for m, o in opts.items()}
+    monkeypatch.setattr(bench, "TRAFFIC_RECORD", _record(tmp_path, _current_sha(), keys, per))
+    value, note = bench.measured_traffic("composite_bwd", opts)
+    assert value == pytest.approx(sum(per.values()) / len(per))
+    assert note == "ncu ..."
+
+
+def test_traffic_null_when_sources_changed(tmp_path, monkeypatch, opts):
+    keys = {m: bench._options_key(o) for m, o in opts.items()}
+    monkeypatch.setattr(bench, "TRAFFIC_RECORD", _record(tmp_path, "0" * 64, keys, {m: 1.0 for m in bench.MODELS}))
+    value, note = bench.measured_traffic("composite_bwd", opts)
+    assert value is None and "changed" in note
+
+
+def test_traffic_null_for_other_options_or_kernel(tmp_path, monkeypatch, opts):
+    keys = {m: bench._options_key(o) for m, o in opts.items()}
+    keys["exp"] = "16x32/1024/tiles"
+    monkeypatch.setattr(bench, "TRAFFIC_RECORD", _record(tmp_path, _current_sha(), keys, {m: 1.0 for m in bench.MODELS}))
+    assert bench.measured_traffic("composite_bwd", opts)[0] is None
+    assert bench.measured_traffic("composite_fwd", opts)[0] is None
+    monkeypatch.setattr(bench, "TRAFFIC_RECORD", str(tmp_path / "absent.json"))
+    assert bench.measured_traffic("composite_bwd", opts)[0] is None
