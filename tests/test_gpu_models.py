@@ -3,7 +3,6 @@ al.'s lerp of the linear and exponential lists (gamma = 0.5 as in the paper's fi
 and the quadratic model with c outside the three experiment values (c = 1 as in Fig. 2, and c = -0.3).
 Same bars as the four main models: images <= 1e-4 and overdraw exact on non-fragile pixels, gradients
 within the relative criterion with the oracle's error scale, tile shapes and batches bit-identical."""
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
