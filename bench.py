@@ -418,25 +418,56 @@ def _options_key(o):
     return f"{o['tile_w']}x{o['tile_h']}/{o['chunk']}/{'persistent' if int(o['schedule']) == 1 else 'tiles'}"
 
 
+def code_digest(paths) -> str:
+    """SHA-256 of the sources' code: comments and whitespace removed, string and character literals kept,
+    so that a comment edit does not invalidate a recorded capture while any change to the code does."""
+    import hashlib
+    h = hashlib.sha256()
+    root = os.path.dirname(os.path.abspath(__file__))
+    for p in paths:
+        with open(os.path.join(root, p), encoding="utf-8") as f:
+            src = f.read()
+        out, i, n = [], 0, len(src)
+        while i < n:
+            c = src[i]
+            if c in "\"'":  # a literal, copied with its escapes
+                j = i + 1
+                while j < n and src[j] != c:
+                    j += 2 if src[j] == "\\" else 1
+                out.append(src[i:j + 1])
+                i = j + 1
+            elif src.startswith("//", i):  # a comment counts as whitespace
+                j = src.find("\n", i)
+                i = n if j < 0 else j
+                out.append(" ")
+            elif src.startswith("/*", i):
+                j = src.find("*/", i + 2)
+                i = n if j < 0 else j + 2
+                out.append(" ")
+            elif c.isspace():
+                out.append(" ")
+                i += 1
+            else:
+                out.append(c)
+                i += 1
+        h.update(" ".join("".join(out).split()).encode())  # whitespace runs -> one space
+        h.update(b"\0")
+    return h.hexdigest()
+
+
 def measured_traffic(kernel, opts):
     """DRAM bytes per launch of `kernel` from the committed ncu capture (profiles/composite_traffic.json),
     averaged over the models, if that capture was taken of the current compositing sources and of these
     per-model launch options; else (None, reason)."""
-    import hashlib
     try:
         with open(TRAFFIC_RECORD) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None, "no ncu capture recorded"
-    h = hashlib.sha256()
-    root = os.path.dirname(os.path.abspath(__file__))
-    for p in TRAFFIC_SOURCES:
-        with open(os.path.join(root, p), "rb") as f:
-            h.update(f.read())
     entry = rec.get("kernels", {}).get(kernel)
     if entry is None:
         return None, f"no ncu capture of {kernel} recorded"
-    if rec.get("source_sha256") != h.hexdigest():
+    if rec.get("code_sha256") != code_digest(TRAFFIC_SOURCES):
         return None, "the compositing sources changed since the recorded ncu capture"
     per = entry.get("bytes_per_launch", {})
     if any(m not in per or rec.get("options", {}).get(m) != _options_key(opts[m]) for m in MODELS):

@@ -1,10 +1,14 @@
 // Per-tile front-to-back compositing (forward) and its path-replay adjoint (backward).
 //
 // One CTA per screen tile of any view of the batch (global tile index -> view by binary search over the
-// views' first tiles). Forward: one thread per pixel, warps on 8 x 4 pixel blocks whose pixels are close
-// and tend to saturate together. Replay: two pixels per thread, (x, y) and (x, y + 4), so that a warp covers
-// an 8 x 8 block and reduces the sum of both pixels' contributions once per 64 pixels. The tile's
-// depth-sorted splat list is walked in chunks of one record (48 B) per pixel staged in shared memory.
+// views' first tiles), or persistent CTAs over a work list. The tile's depth-sorted splat list is walked in
+// chunks of records staged in shared memory (half, one or two per pixel).
+// Replay, and the forward of the exponential model (and of the quadratic ones on tiles of >= 256 pixels):
+// two pixels per thread, (x, y) and (x, y + 4), so that a warp covers an 8 x 8 block; the two step through
+// each entry together in packed FP32x2 instructions (add / mul / fma .rn.f32x2), each lane rounding like
+// the one-pixel form, with the splat operands staged in duplicated pairs. The replay reduces both pixels'
+// contributions once per 64 pixels. Other forwards: one thread per pixel, warps on 8 x 4 pixel blocks
+// whose pixels are close and tend to saturate together.
 //
 // Forward, per pixel (Eq. generalized_gaussian with pbar_i from Eq. nexp_p and Table 1):
 //   alpha_i = min(alpha_max, aleph_i K_i(p)), skipped when alpha_i < alpha_min;
@@ -26,8 +30,9 @@
 //                of DeltaE_l alpha_l P_l and B their total (saved by the forward pass);
 //   Vicini:      (1 - g) x the linear adjoint + g x the exponential adjoint, each over its own list;
 // then w = dL/d(log2 alpha) and its moments w, w dx, w dy, w dx^2, w dx dy, w dy^2 (which determine the
-// gradient of the splat record, see the projection backward) and dL/dE, reduced over the warp's pixels with
-// shuffles and added to the per-Gaussian buffer with one atomic-add instruction per warp and splat.
+// gradient of the splat record, see the projection backward) and dL/dE: added to the per-Gaussian buffer by
+// each lane that hit the splat when at most kDirectLanes did, else reduced over the warp with shuffles and
+// added with one atomic-add instruction per value.
 #include <algorithm>
 
 #include <type_traits>

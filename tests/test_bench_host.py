@@ -1,8 +1,6 @@
 """Host-side logic of bench.py (no GPU): per-model launch options and the guard on the recorded ncu traffic,
 which is reported only while the compositing sources and the launch options match the capture."""
-import hashlib
 import json
-import os
 
 import pytest
 
@@ -29,7 +27,7 @@ def test_tuned_options_parse_for_every_model():
 
 
 def _record(tmp_path, sha, options, per_model):
-    rec = {"source_sha256": sha, "options": options, "command": "ncu ...",
+    rec = {"code_sha256": sha, "options": options, "command": "ncu ...",
            "kernels": {"composite_bwd": {"bytes_per_launch": per_model}}}
     p = tmp_path / "traffic.json"
     p.write_text(json.dumps(rec))
@@ -37,12 +35,20 @@ def _record(tmp_path, sha, options, per_model):
 
 
 def _current_sha():
-    h = hashlib.sha256()
-    root = os.path.dirname(os.path.abspath(bench.__file__))
-    for p in bench.TRAFFIC_SOURCES:
-        with open(os.path.join(root, p), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()
+    return bench.code_digest(bench.TRAFFIC_SOURCES)
+
+
+def test_code_digest_ignores_comments_only(tmp_path, monkeypatch):
+    root = tmp_path
+    (root / "a.cu").write_text("int f(int x) {\n  return x + 1;  // one\n}\n/* note */\n")
+    (root / "b.cu").write_text("int f(int x) { return x + 1; }\n")
+    (root / "c.cu").write_text("int f(int x) { return x + 2; }\n")
+    (root / "d.cu").write_text("int f(int x) { return x+1; }\n")
+    monkeypatch.setattr(bench, "__file__", str(root / "bench.py"))
+    dig = {k: bench.code_digest([k + ".cu"]) for k in "abcd"}
+    assert dig["a"] == dig["b"]  # comments and layout do not count
+    assert dig["c"] != dig["b"]  # code does
+    assert dig["d"] != dig["b"]  # nor is whitespace between tokens dropped entirely
 
 
 @pytest.fixture
