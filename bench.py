@@ -55,6 +55,9 @@ def parse():
                    help="per-model launch options, model=WxH/chunk/schedule, comma-separated (models not named "
                         "are autotuned); the default is what ngs_autotune picked for this workload on GB300")
     p.add_argument("--autotune", action="store_true", help="autotune every model's launch options instead")
+    p.add_argument("--record-traffic", metavar="CSV", default=None,
+                   help="write profiles/composite_traffic.json from the ncu CSV of the timed step's compositing "
+                        "launches and exit (the capture: TRAFFIC_COMMAND, with the same --options)")
     p.add_argument("--no-graphs", action="store_true", help="launch the render phases directly")
     p.add_argument("--no-async", action="store_true",
                    help="synchronous renders (the host waits for each render's pair count)")
@@ -384,7 +387,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-# algorithmic work per unit ("Roofline"): FLOPs count an FMA as 2
+# algorithmic work per unit: FLOPs count an FMA as 2
 FLOP_TEST = 11                              # per walked list entry: d = p - mu, the quadratic form, the alpha test
 FLOP_FWD = {"quad": 20, "exp": 12}          # per composited splat, forward
 FLOP_BWD = {"quad": 50, "exp": 45}          # per composited splat, replay + chain to the splat record
@@ -453,6 +456,46 @@ def code_digest(paths) -> str:
         h.update(" ".join("".join(out).split()).encode())  # whitespace runs -> one space
         h.update(b"\0")
     return h.hexdigest()
+
+
+def record_traffic(csv_path, command, options=TUNED_OPTIONS, out=None):
+    """Write the traffic record from an ncu CSV (--metrics dram__bytes_read.sum,dram__bytes_write.sum,
+    gpu__time_duration.sum) of the timed step's compositing launches (one stream, models in MODELS order,
+    launched with `options`): DRAM bytes per launch and model, keyed by the compositing code's digest."""
+    import csv
+    import re
+
+    with open(csv_path) as f:
+        rows = list(csv.reader(f))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    h = rows[hi]
+    ki, vi, mi, ii = h.index("Kernel Name"), h.index("Metric Value"), h.index("Metric Name"), h.index("ID")
+    launches = {}
+    for r in rows[hi + 1:]:
+        if len(r) > vi:
+            d = launches.setdefault(int(r[ii]), {"name": r[ki]})
+            d[r[mi]] = float(r[vi].replace(",", ""))
+    order = [launches[k] for k in sorted(launches)]
+    rec = {"what": "DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the compositing "
+                   "kernels in the bench's timed step, one ncu capture (cold cache between passes)",
+           "command": command, "code_sha256": code_digest(TRAFFIC_SOURCES),
+           "code_digest": "bench.code_digest: SHA-256 of the sources with comments removed and whitespace runs "
+                          "collapsed, so that only a change to the code invalidates the capture",
+           "sources": list(TRAFFIC_SOURCES),
+           "options": {m: o for m, o in (item.split("=") for item in options.split(","))}, "kernels": {}}
+    for stage, pat in (("composite_bwd", "composite_backward"), ("composite_fwd", "composite_forward")):
+        ls = [l for l in order if pat in l["name"]]
+        if len(ls) != len(MODELS):
+            continue
+        name = lambda l: re.sub(r"\(.*$", "", l["name"].replace("void ", "").replace("<unnamed>::", ""))
+        rec["kernels"][stage] = {
+            "bytes_per_launch": {m: l["dram__bytes_read.sum"] + l["dram__bytes_write.sum"] for m, l in zip(MODELS, ls)},
+            "kernel": {m: name(l) for m, l in zip(MODELS, ls)},
+            "ncu_duration_ns": {m: l["gpu__time_duration.sum"] for m, l in zip(MODELS, ls)}}
+    text = json.dumps(rec, indent=1) + "\n"
+    with open(out or TRAFFIC_RECORD, "w") as f:
+        f.write(text)
+    return rec
 
 
 def measured_traffic(kernel, opts):
@@ -912,8 +955,17 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+TRAFFIC_COMMAND = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                   "--clock-control none --nvtx --nvtx-include timed/ -k regex:composite_ --csv python bench.py "
+                   "--steps 1 --warmup 3 --no-e2e --no-cpu-baseline --no-batched --no-serving --no-training "
+                   "--streams 1")
+
+
 def main():
     args = parse()
+    if args.record_traffic:
+        record_traffic(args.record_traffic, TRAFFIC_COMMAND, args.options)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
