@@ -80,3 +80,27 @@ def test_traffic_null_for_other_options_or_kernel(tmp_path, monkeypatch, opts):
     assert bench.measured_traffic("composite_fwd", opts)[0] is None
     monkeypatch.setattr(bench, "TRAFFIC_RECORD", str(tmp_path / "absent.json"))
     assert bench.measured_traffic("composite_bwd", opts)[0] is None
+
+
+def test_record_traffic_from_an_ncu_csv(tmp_path):
+    rows = ['"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size",'
+            '"Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"']
+    lid = 0
+    for i, m in enumerate(bench.MODELS):
+        for kind, base in (("composite_forward_kernel", 1000), ("composite_backward_kernel", 5000)):
+            name = f"void <unnamed>::{kind}<16, 16, 1, 128, 1>(const float4 *)"
+            for metric, val in (("dram__bytes_read.sum", base + i), ("dram__bytes_write.sum", 10 * (i + 1)),
+                                ("gpu__time_duration.sum", 7)):
+                rows.append(f'"{lid}","1","python","h","{name}","1","7","(128, 1, 1)","(9, 1, 1)","0","10.3",'
+                            f'"Command line profiler metrics","{metric}","byte","{val:,}"')
+            lid += 1
+    csv_path = tmp_path / "launches.csv"
+    csv_path.write_text("\n".join(rows) + "\n")
+    out = tmp_path / "rec.json"
+    rec = bench.record_traffic(str(csv_path), "ncu ...", bench.TUNED_OPTIONS, out=str(out))
+    assert json.loads(out.read_text()) == rec
+    for i, m in enumerate(bench.MODELS):
+        assert rec["kernels"]["composite_fwd"]["bytes_per_launch"][m] == 1000 + i + 10 * (i + 1)
+        assert rec["kernels"]["composite_bwd"]["bytes_per_launch"][m] == 5000 + i + 10 * (i + 1)
+    assert rec["code_sha256"] == bench.code_digest(bench.TRAFFIC_SOURCES)
+    assert set(rec["options"]) == set(bench.MODELS)
