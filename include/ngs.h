@@ -225,8 +225,9 @@ NGS_API int ngs_render_backward(ngs_ctx* ctx, const ngs_frame* frame, const ngs_
  * 12 MiB that every GPU loading the library holds until the process exits, and nothing is allocated.
  * Limits: at most 262,144 splat records, Gaussians x views (larger frames return NGS_ERR_INVALID_ARG with
  * a message naming the limit). All calls on a device share the array; each call clears what it uses first, and calls that
- * overlap on the GPU (unordered streams or threads) race on it. The first call on a device, with that
- * device current, looks up the array's address (cudaGetSymbolAddress); make it before any stream capture. */
+ * overlap on the GPU (unordered streams or threads) race on it. The context's device must be the current
+ * device (else NGS_ERR_INVALID_ARG). The first call on a device looks up the array's address there
+ * (cudaGetSymbolAddress); make it before any stream capture. */
 NGS_API int ngs_render_backward_static(ngs_ctx* ctx, const ngs_frame* frame, const ngs_gaussians* g,
                                        const float* dl_dimage, const ngs_grads* out, void* stream);
 

@@ -240,7 +240,7 @@ struct RenderPlan {
 
 // Phase 1: view table upload, projection, depth sort, scan of the tile counts, and the pair count (and the
 // device error word) written into the context's mapped pinned mirror. Launches only.
-static void phase1(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, cudaStream_t s) {
+static cudaError_t phase1(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, cudaStream_t s) {
   const RenderParams& rp = pl.rp;
   const ViewParams* views = f->views.as<ViewParams>();
   cudaEvent_t ev;
@@ -268,24 +268,27 @@ static void phase1(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, cudaStream_
   // 3. exclusive scan of the tile counts in (view, depth) order; the pair count goes to the host mirror
   stage_begin(ctx, s, 2, &ev);
   launches = 0;
-  launch_scan_counts(f->tile_count.as<uint32_t>(), f->gvals[f->g_final].as<uint32_t>(), pl.R,
-                     f->offsets.as<uint32_t>(), ctx->scan_tmp.as<uint64_t>(), ctx->total.as<uint64_t>(), s,
-                     &launches);
+  const cudaError_t e = launch_scan_counts(f->tile_count.as<uint32_t>(), f->gvals[f->g_final].as<uint32_t>(), pl.R,
+                                           f->offsets.as<uint32_t>(), ctx->scan_tmp.as<uint64_t>(),
+                                           ctx->total.as<uint64_t>(), s, &launches);
   publish_words(ctx, ctx->total.as<uint64_t>(), 2, kMirrorTotal, s);
   stage_end(ctx, s, 2, ev, launches + 1);
+  return e;
 }
 
 // Phase 2: key emission, tile sort, tile ranges (+ work list), composite. `cap` items are covered by the
 // sort's grid; with np_dev (graph replays) the kernels read the actual pair count from the device.
-static void phase2(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, uint32_t cap, const uint32_t* np_dev,
-                   bool async, cudaStream_t s) {
+static cudaError_t phase2(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, uint32_t cap, const uint32_t* np_dev,
+                          bool async, cudaStream_t s) {
   const RenderParams& rp = pl.rp;
   const ViewParams* views = f->views.as<ViewParams>();
   cudaEvent_t ev;
   // zeroing first, so that the kernels from the emission to the composite follow one another directly
   // (programmatic dependent launches)
-  cudaMemsetAsync(f->ranges.p, 0, sizeof(uint2) * (size_t)pl.ntiles, s);
-  if (rp.schedule == NGS_SCHEDULE_PERSISTENT) cudaMemsetAsync(f->sched.p, 0, sizeof(uint32_t) * kSchedWords, s);
+  cudaError_t e = cudaMemsetAsync(f->ranges.p, 0, sizeof(uint2) * (size_t)pl.ntiles, s);
+  if (e == cudaSuccess && rp.schedule == NGS_SCHEDULE_PERSISTENT)
+    e = cudaMemsetAsync(f->sched.p, 0, sizeof(uint32_t) * kSchedWords, s);
+  if (e != cudaSuccess) return e;
   stage_begin(ctx, s, 2, &ev);
   launch_emit_pairs(f->rec.as<float4>(), f->gvals[f->g_final].as<uint32_t>(), f->offsets.as<uint32_t>(), views, rp,
                     f->ptile[0].as<uint32_t>(), f->pvals[0].as<uint32_t>(), cap, s);
@@ -326,6 +329,7 @@ static void phase2(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, uint32_t ca
     launch_pdl(finish_async_kernel, 1, 32, 0, s, ctx->total.as<uint64_t>(), f->d_status, cap);
     ctx->launches += 1;
   }
+  return cudaSuccess;
 }
 
 // Serialised launch arguments of a phase: a captured graph is replayed only while they are unchanged.
@@ -342,9 +346,11 @@ struct KeyBuf {
 // the context's capture stream when the key changed.
 template <typename Fn>
 static int run_phase(ngs_ctx* ctx, ngs_frame* f, int which, const KeyBuf& key, cudaStream_t s, Fn&& launch) {
+  const char* what = which == 0 ? "render phase 1" : "render phase 2";
   if (!ctx->graphs) {
-    launch(s);
-    return check_launch(ctx, which == 0 ? "render phase 1" : "render phase 2");
+    cudaError_t e = launch(s);
+    if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return check_launch(ctx, what);
   }
   GraphSlot& g = f->graph[which];
   if (!g.exec || g.key != key.b) {
@@ -358,8 +364,9 @@ static int run_phase(ngs_ctx* ctx, ngs_frame* f, int which, const KeyBuf& key, c
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      launch(ctx->cap_stream);
+      const cudaError_t le = launch(ctx->cap_stream);
       e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+      if (le != cudaSuccess) e = le;
     }
     ctx->timing = timing;
     for (int i = 0; i < NGS_NUM_STAGES; ++i) {  // counted per replay below, not at capture
@@ -506,7 +513,11 @@ int ngs::render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, co
   NGS_TRY(ensure(ctx, ctx->scan_tmp, sizeof(uint64_t) * scan_tmp_words(R)));
   if (!ctx->total.p) {
     NGS_TRY(ensure(ctx, ctx->total, 2 * sizeof(uint64_t)));
-    cudaMemsetAsync(ctx->total.p, 0, 2 * sizeof(uint64_t), s);
+    const cudaError_t ze = cudaMemsetAsync(ctx->total.p, 0, 2 * sizeof(uint64_t), s);
+    if (ze != cudaSuccess) {
+      free_buf(ctx->total);  // zeroed on the next render's first use again
+      return fail(ctx, NGS_ERR_CUDA, std::string("clearing the pair count: ") + cudaGetErrorString(ze));
+    }
   }
   rp.check = reinterpret_cast<uint32_t*>(ctx->total.as<uint64_t>() + 1);
   NGS_TRY(ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(std::max(pl.n, 1u), (uint32_t)n_views)));
@@ -534,7 +545,7 @@ int ngs::render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, co
   k1.add(ctx->h_total);
   // asynchronous: no host synchronisation; phase 2 is sized by the frame's capacity (set by earlier renders)
   const bool async = f->async && f->pair_cap > 0 && !admit;
-  NGS_TRY(run_phase(ctx, f, 0, k1, s, [&](cudaStream_t st) { phase1(ctx, f, pl, st); }));
+  NGS_TRY(run_phase(ctx, f, 0, k1, s, [&](cudaStream_t st) { return phase1(ctx, f, pl, st); }));
   cudaError_t e = cudaEventRecord(f->views_uploaded, s);
   uint32_t np = 0, cap = 0;
   const uint32_t* np_dev = nullptr;
@@ -547,7 +558,9 @@ int ngs::render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, co
     if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("reading the pair count: ") + cudaGetErrorString(e));
     const volatile uint64_t* mirror = ctx->h_total + kMirrorTotal;  // written by publish_words
     if (mirror[1] != 0) {  // a bounds check fired in an earlier call on this context
-      cudaMemsetAsync(ctx->total.as<uint64_t>() + 1, 0, sizeof(uint64_t), s);
+      const cudaError_t ze = cudaMemsetAsync(ctx->total.as<uint64_t>() + 1, 0, sizeof(uint64_t), s);
+      if (ze != cudaSuccess)
+        return fail(ctx, NGS_ERR_CUDA, std::string("clearing the device error word: ") + cudaGetErrorString(ze));
       return fail(ctx, NGS_ERR_DEVICE_CHECK, "a kernel bounds check fired in an earlier call on this context; its "
                                              "output was not valid");
     }
@@ -586,7 +599,7 @@ int ngs::render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, co
                           &f->pvals[0], &f->pvals[1], &ctx->hist, &f->ranges, &f->work, &f->sched, &f->state})
     k2.add(b->p);
   if (async) k2.add(f->d_status);
-  NGS_TRY(run_phase(ctx, f, 1, k2, s, [&](cudaStream_t st) { phase2(ctx, f, pl, cap, np_dev, async, st); }));
+  NGS_TRY(run_phase(ctx, f, 1, k2, s, [&](cudaStream_t st) { return phase2(ctx, f, pl, cap, np_dev, async, st); }));
   if (async) {
     e = cudaEventRecord(f->done, s);
     if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("render: ") + cudaGetErrorString(e));
@@ -763,14 +776,17 @@ int ngs::backward_frame(ngs_ctx* ctx, const ngs_frame* f, const ngs_gaussians* g
     return fail(ctx, NGS_ERR_INVALID_ARG, "null gradient array");
   const uint32_t R = f->rp.n_records;
   NGS_TRY(ensure(ctx, ctx->grad2d, sizeof(float4) * 3 * (size_t)std::max(R, 1u)));
-  cudaMemsetAsync(ctx->grad2d.p, 0, sizeof(float4) * 3 * (size_t)R, s);
+  // the replay adds into the record gradients: a failed clear must not let it add onto stale values
+  cudaError_t e = cudaMemsetAsync(ctx->grad2d.p, 0, sizeof(float4) * 3 * (size_t)R, s);
+  if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("clearing the record gradients: ") + cudaGetErrorString(e));
   const ViewParams* views = f->views.as<ViewParams>();
   const uint32_t* work = nullptr;
   uint32_t* counter = nullptr;
   if (f->rp.schedule == NGS_SCHEDULE_PERSISTENT) {
     work = f->work.as<uint32_t>();
     counter = f->sched.as<uint32_t>() + 1;
-    cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+    e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("clearing the work counter: ") + cudaGetErrorString(e));
   }
   cudaEvent_t ev;
   stage_begin(ctx, s, 6, &ev);

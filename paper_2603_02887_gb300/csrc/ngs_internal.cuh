@@ -347,9 +347,9 @@ int radix_sort_u32(uint32_t* keys[2], uint32_t* vals[2], uint32_t seg_len, uint3
                    int begin_bit, int end_bit, uint32_t* hist, cudaStream_t s, int* launches);
 size_t radix_hist_words(uint32_t seg_len, uint32_t nseg);
 // exclusive scan of tile_count[order[i]] into offsets[0..n] (offsets[n] = total) and the total into
-// *total (uint64, device)
-void launch_scan_counts(const uint32_t* tile_count, const uint32_t* order, uint32_t n, uint32_t* offsets,
-                        uint64_t* block_sums, uint64_t* total, cudaStream_t s, int* launches);
+// *total (uint64, device); returns the error of its own runtime calls (n = 0 clears both with memsets)
+cudaError_t launch_scan_counts(const uint32_t* tile_count, const uint32_t* order, uint32_t n, uint32_t* offsets,
+                               uint64_t* block_sums, uint64_t* total, cudaStream_t s, int* launches);
 size_t scan_tmp_words(uint32_t n);
 // One (view-local tile, record index) pair per covered tile, in the order of `order` (n_records entries):
 // the records are in (view, depth) order, so sorting the pairs stably by the local tile alone orders them by

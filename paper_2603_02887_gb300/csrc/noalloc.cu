@@ -16,7 +16,9 @@
 //    (different streams or host threads without ordering between them) race on it;
 //  * the first call on a device, with that device current, looks up the array's device address with
 //    cudaGetSymbolAddress (host code cannot use the symbol itself as a device pointer); make that first
-//    call before any stream capture.
+//    call before any stream capture;
+//  * the context's device must be the current device (else NGS_ERR_INVALID_ARG): the array is looked up on
+//    the current device, and the frame's buffers live on the context's.
 #include <mutex>
 
 #include "ngs_internal.cuh"
@@ -31,11 +33,15 @@ static __device__ __align__(256) float4 g_static_grad2d[3 * kStaticMaxRecords];
 std::mutex g_mutex;
 void* g_device_ptr[kMaxDevices] = {};
 
-// Device address of g_static_grad2d on the current device (looked up once per device).
+// Device address of g_static_grad2d on the context's device, which must be current (looked up once per device).
 int static_scratch(ngs_ctx* ctx, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return ngs::fail(ctx, NGS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev != ctx->device)
+    return ngs::fail(ctx, NGS_ERR_INVALID_ARG, "ngs_render_backward_static: the context's device (" +
+                                                   std::to_string(ctx->device) + ") is not the current device (" +
+                                                   std::to_string(dev) + ")");
   if (dev < 0 || dev >= kMaxDevices) return ngs::fail(ctx, NGS_ERR_INVALID_ARG, "device index out of range");
   std::lock_guard<std::mutex> lock(g_mutex);
   if (!g_device_ptr[dev]) {
@@ -79,13 +85,21 @@ extern "C" NGS_API int ngs_render_backward_static(ngs_ctx* ctx, const ngs_frame*
   if (f->rp.schedule == NGS_SCHEDULE_PERSISTENT) {  // the frame's own work list and counter (no allocation)
     work = f->work.as<uint32_t>();
     counter = f->sched.as<uint32_t>() + 1;
-    cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+    e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("clearing the work counter: ") + cudaGetErrorString(e));
   }
   launch_composite_backward(f->rec.as<float4>(), f->pvals[f->p_final].as<uint32_t>(), f->ranges.as<uint2>(), f->rp,
                             views, dl_dimage, f->state.as<float4>(), grad2d, work, counter, ctx->num_sms, s);
-  launch_project_backward(*g, views, f->view_host[0].cam, f->rp, f->tile_count.as<uint32_t>(), grad2d, *out, s);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("backward launch: ") + cudaGetErrorString(e));
-  ctx->launches += n ? 2 : 1;
+  if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("composite backward: ") + cudaGetErrorString(e));
+  ctx->launches += 1;
+  ctx->stage_launches[6] += 1;
+  if (n) {
+    launch_project_backward(*g, views, f->view_host[0].cam, f->rp, f->tile_count.as<uint32_t>(), grad2d, *out, s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("projection backward: ") + cudaGetErrorString(e));
+    ctx->launches += 1;
+    ctx->stage_launches[7] += 1;
+  }
   return NGS_OK;
 }

@@ -283,13 +283,15 @@ NGS_API int ngs_densify(ngs_ctx* ctx, int64_t n, int32_t sh_degree, const ngs_gr
   densify_decide_kernel<<<blocks, 256, 0, s>>>(params->d_opacity_logits, params->d_log_scales, accum, count, n, *cfg,
                                                decision, cand);
   launches += 2;
-  launch_scan_counts(cand, iota, un, rank, ctx->scan_tmp.as<uint64_t>(), &totals[0], s, &launches);
-  cudaMemsetAsync(&totals[1], 0, sizeof(uint64_t), s);
+  cudaError_t me = launch_scan_counts(cand, iota, un, rank, ctx->scan_tmp.as<uint64_t>(), &totals[0], s, &launches);
+  if (me == cudaSuccess) me = cudaMemsetAsync(&totals[1], 0, sizeof(uint64_t), s);
+  if (me != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("densify: ") + cudaGetErrorString(me));
   count_pruned_kernel<<<blocks, 256, 0, s>>>(decision, n, &totals[1]);
   densify_allowed_kernel<<<1, 1, 0, s>>>(&totals[0], &totals[1], n, cfg->max_gaussians, allowed);
   densify_count_kernel<<<blocks, 256, 0, s>>>(decision, rank, allowed, n, outc);
   launches += 3;
-  launch_scan_counts(outc, iota, un, pos, ctx->scan_tmp.as<uint64_t>(), &totals[2], s, &launches);
+  me = launch_scan_counts(outc, iota, un, pos, ctx->scan_tmp.as<uint64_t>(), &totals[2], s, &launches);
+  if (me != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("densify: ") + cudaGetErrorString(me));
   DensifyArgs da;
   da.src = ptrs(*params);
   da.src_m = ptrs(*m);

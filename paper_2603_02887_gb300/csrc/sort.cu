@@ -405,18 +405,19 @@ int radix_sort_u32(uint32_t* keys[2], uint32_t* vals[2], uint32_t seg_len, uint3
 
 size_t scan_tmp_words(uint32_t n) { return (size_t)(n + kScanTile - 1) / kScanTile + 1; }
 
-void launch_scan_counts(const uint32_t* tile_count, const uint32_t* order, uint32_t n, uint32_t* offsets,
-                        uint64_t* block_sums, uint64_t* total, cudaStream_t s, int* launches) {
+cudaError_t launch_scan_counts(const uint32_t* tile_count, const uint32_t* order, uint32_t n, uint32_t* offsets,
+                               uint64_t* block_sums, uint64_t* total, cudaStream_t s, int* launches) {
   if (n == 0) {
-    cudaMemsetAsync(offsets, 0, sizeof(uint32_t), s);
-    cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
-    return;
+    cudaError_t e = cudaMemsetAsync(offsets, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
+    return e;
   }
   uint32_t nblocks = (n + kScanTile - 1) / kScanTile;
   launch_pdl(scan_reduce_kernel, nblocks, kScanThreads, 0, s, tile_count, order, n, block_sums);
   launch_pdl(scan_block_sums_kernel, 1, 1024, 0, s, block_sums, nblocks, total);
   launch_pdl(scan_final_kernel, nblocks, kScanThreads, 0, s, tile_count, order, n, block_sums, offsets);
   *launches += 3;
+  return cudaSuccess;
 }
 
 void launch_tile_ranges(const uint32_t* tiles, const uint32_t* vals, const ViewParams* views, uint32_t n_per_view,

@@ -45,7 +45,13 @@ extern "C" NGS_API int ngs_autotune(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussi
         o.schedule = sched;
         times.clear();
         for (int r = -1; r < reps && rc == NGS_OK; ++r) {
-          if (r >= 0 && flush_bytes > 0) cudaMemsetAsync(ctx->flush.p, r & 0xFF, (size_t)flush_bytes, s);
+          if (r >= 0 && flush_bytes > 0) {
+            const cudaError_t fe = cudaMemsetAsync(ctx->flush.p, r & 0xFF, (size_t)flush_bytes, s);
+            if (fe != cudaSuccess) {
+              rc = fail(ctx, NGS_ERR_CUDA, std::string("autotune: clearing L2: ") + cudaGetErrorString(fe));
+              break;
+            }
+          }
           if (r >= 0) cudaEventRecord(e0, s);
           rc = render_views(ctx, f, g, cams, n_views, model, &o, images, overdraw, s);
           if (rc == NGS_OK && with_backward) rc = backward_frame(ctx, f, g, dl_dimage, grads, s);
