@@ -35,7 +35,7 @@ EXP, QUAD, BLEND, VICINI = 0, 1, 2, 3
 MODELS = {"exp": (EXP, 0.0), "sub": (QUAD, -0.5), "lin": (QUAD, 0.0), "sup": (QUAD, 0.5)}
 
 DEFAULT_OPTS = dict(alpha_min=1.0 / 255.0, alpha_max=0.99, t_eps=1e-4, dilation=0.3, near_plane=0.2,
-                    background=(0.0, 0.0, 0.0), max_splats=0, fragile_rel=1e-4)
+                    background=(0.0, 0.0, 0.0), max_splats=0)
 
 
 def build(force: bool = False) -> str:
@@ -66,7 +66,7 @@ class _Model(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("alpha_min", C.c_double), ("alpha_max", C.c_double), ("t_eps", C.c_double),
                 ("dilation", C.c_double), ("near_plane", C.c_double), ("background", C.c_double * 3),
-                ("max_splats", C.c_int32), ("fragile_rel", C.c_double)]
+                ("max_splats", C.c_int32)]
 
 
 class _Window(C.Structure):
@@ -75,7 +75,17 @@ class _Window(C.Structure):
 
 class _Fwd(C.Structure):
     _fields_ = [("image", C.c_void_p), ("overdraw", C.c_void_p), ("n_listed", C.c_void_p),
-                ("fragile", C.c_void_p), ("signature", C.c_void_p)]
+                ("fragile", C.c_void_p), ("signature", C.c_void_p), ("n_outcomes", C.c_void_p)]
+
+
+class _Alt(C.Structure):
+    _fields_ = [("n_fwd", C.c_int64), ("fwd_pix", C.c_void_p), ("fwd_outcome", C.c_void_p),
+                ("fwd_overdraw", C.c_void_p), ("fwd_image", C.c_void_p),
+                ("n_grad", C.c_int64), ("grad_pix", C.c_void_p), ("grad_outcome", C.c_void_p),
+                ("grad_ju", C.c_void_p), ("grad_rec", C.c_void_p),
+                ("n_params", C.c_int32), ("n_jac", C.c_int64), ("jac_gid", C.c_void_p), ("jac", C.c_void_p),
+                ("n_eflip", C.c_int64), ("eflip_gid", C.c_void_p), ("eflip_mask", C.c_void_p),
+                ("eflip_dJ", C.c_void_p), ("eflip_gE", C.c_void_p)]
 
 
 class _Bwd(C.Structure):
@@ -91,9 +101,15 @@ def _load():
         lib = C.CDLL(build())
         P = C.POINTER
         lib.orc_render.argtypes = [P(_Scene), P(_Camera), P(_Model), P(_Opts), P(_Window), C.c_int, C.c_int,
-                                   P(_Fwd), P(_Bwd)]
-        lib.orc_project.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_void_p, C.c_void_p]
-        lib.orc_project_jacobian.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_int64, C.c_void_p]
+                                   P(_Fwd), P(_Bwd), P(_Alt)]
+        lib.orc_free_alt.argtypes = [P(_Alt)]
+        lib.orc_project.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p]
+        lib.orc_composite_outcomes.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double,
+                                               C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                               C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.orc_composite_outcomes.restype = C.c_int32
+        lib.orc_project_jacobian.argtypes = [P(_Scene), P(_Camera), P(_Opts), C.c_int64, C.c_void_p, C.c_int32]
         lib.orc_composite_list.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_int32, C.c_void_p, C.c_int32,
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p]
@@ -146,7 +162,6 @@ def _opts(opts):
     for i in range(3):
         r.background[i] = _f32(o["background"][i])
     r.max_splats = int(o["max_splats"])
-    r.fragile_rel = float(o["fragile_rel"])
     return r
 
 
@@ -184,7 +199,9 @@ def composite_list(alpha, E, model, t_eps=0.0, max_splats=0, background=(0.0, 0.
 
 def project(scene, camera, opts=None):
     """EWA projection of every Gaussian: rec[n, 10] = (u, v, A, B, C, aleph, E0, E1, E2, rbound), the FP32
-    sort depth z32[n] and valid[n] (in front of the near plane and able to reach alpha_min)."""
+    sort depth z32[n], valid[n] (in front of the near plane and able to reach alpha_min), and the error
+    bounds the oracle assumes for the GPU's FP32 records: pos_err[n, 2] (pixels) of (u, v) and e_band[n, 3]
+    of the colour channels before their max(0, .) clamp."""
     lib = _load()
     keep = []
     sc, n, _ = _scene(scene, keep)
@@ -192,29 +209,68 @@ def project(scene, camera, opts=None):
     rec = np.zeros((n, 10))
     z32 = np.zeros(n, dtype=np.float32)
     valid = np.zeros(n, dtype=np.int32)
-    lib.orc_project(C.byref(sc), C.byref(cam), C.byref(o), _ptr(rec), _ptr(z32), _ptr(valid))
-    return dict(rec=rec, z32=z32, valid=valid.astype(bool))
+    pos_err = np.zeros((n, 2))
+    e_band = np.zeros((n, 3))
+    lib.orc_project(C.byref(sc), C.byref(cam), C.byref(o), _ptr(rec), _ptr(z32), _ptr(valid), _ptr(pos_err),
+                    _ptr(e_band))
+    return dict(rec=rec, z32=z32, valid=valid.astype(bool), pos_err=pos_err, e_band=e_band)
 
 
-def project_jacobian(scene, camera, g, opts=None):
+def composite_outcomes(raw, E, model, band=None, alpha_min=0.0, alpha_max=np.inf, t_eps=0.0, max_splats=0,
+                       background=(0.0, 0.0, 0.0), max_out=64):
+    """Every outcome of one list's walk when the decisions within ``band`` (log2-domain error bound per
+    candidate; None: exact) of their thresholds may go either way. Returns a list of dict(m, color, T_end,
+    pbar[n]) (outcome 0 = the FP64 walk), or None when there were more than ``max_out``."""
+    lib = _load()
+    raw = _f64(raw).reshape(-1)
+    n = raw.shape[0]
+    E = _f64(E).reshape(n, 3)
+    bg = _f64(background).reshape(3)
+    b = None if band is None else _f64(np.broadcast_to(band, (n,)))
+    m_ = _model(model)
+    ms = np.zeros(max_out, np.int32)
+    out4 = np.zeros((max_out, 4))
+    pbar = np.zeros((max_out, max(n, 1)))
+    cnt = lib.orc_composite_outcomes(m_.kind, m_.param, float(alpha_min), float(alpha_max), float(t_eps),
+                                     int(max_splats), _ptr(bg), n, _ptr(raw), _ptr(b), _ptr(E), int(max_out),
+                                     _ptr(ms), _ptr(out4), _ptr(pbar))
+    if cnt < 0:
+        return None
+    return [dict(m=int(ms[i]), color=out4[i, :3].copy(), T_end=float(out4[i, 3]), pbar=pbar[i, :n].copy())
+            for i in range(cnt)]
+
+
+def project_jacobian(scene, camera, g, opts=None, eflip=0):
     """Jacobian [9, 11 + 3K] of (u, v, A, B, C, aleph, E0, E1, E2) w.r.t. (mean 3, log-scale 3, quat 4,
-    opacity logit 1, SH 3K) of Gaussian ``g``, by complex step."""
+    opacity logit 1, SH 3K) of Gaussian ``g``, by complex step. Bit ch of ``eflip`` takes colour channel
+    ch's max(0, .) clamp against the sign of its value."""
     lib = _load()
     keep = []
     sc, n, K = _scene(scene, keep)
     cam, o = _camera(camera), _opts(opts)
     jac = np.zeros((9, 11 + 3 * K))
-    lib.orc_project_jacobian(C.byref(sc), C.byref(cam), C.byref(o), int(g), _ptr(jac))
+    lib.orc_project_jacobian(C.byref(sc), C.byref(cam), C.byref(o), int(g), _ptr(jac), int(eflip))
     return jac
 
 
-def render(scene, camera, model, opts=None, window=None, nthreads=1, brute_force=False, dl_dimage=None):
+def render(scene, camera, model, opts=None, window=None, nthreads=1, brute_force=False, dl_dimage=None,
+           outcomes=False):
     """Render a window (x0, y0, w, h) of ``camera`` (default: the full image) per pixel in FP64.
 
-    Returns dict(image[h, w, 3], overdraw[h, w], n_listed[h, w], fragile[h, w], signature[h, w]) and, when
-    ``dl_dimage`` [h, w, 3] is given, the gradients d_means, d_log_scales, d_quats, d_opacity_logits, d_sh
-    (same shapes as the parameters), fragile_gauss[n] and, per gradient, its error scale s_* (the sum of
-    the absolute per-pixel terms chained through the absolute Jacobian).
+    Returns dict(image[h, w, 3], overdraw[h, w], n_listed[h, w], fragile[h, w], signature[h, w],
+    n_outcomes[h, w]) and, when ``dl_dimage`` [h, w, 3] is given, the gradients d_means, d_log_scales,
+    d_quats, d_opacity_logits, d_sh (same shapes as the parameters), fragile_gauss[n] (bit ch: colour
+    channel ch is borderline at its max(0, .) clamp) and, per gradient, its error scale s_* (the sum of the
+    absolute per-pixel terms chained through the absolute Jacobian). Image, overdraw and gradients are
+    those of the FP64 walk. ``fragile`` is 1 where a decision of the pixel's walk is borderline (within the
+    FP32 error bound of its threshold) and 2 where the enumeration was cut short (``unresolved``).
+
+    With ``outcomes`` the borderline decisions of every pixel are enumerated and ``alt`` holds every
+    outcome of every pixel that has more than one: ``fwd`` rows (pix = y w + x in the window, outcome,
+    overdraw, image[3]), with ``dl_dimage`` also ``grad`` rows (pix, outcome, ju, rec[18]: the per-entry
+    record-gradient terms and their absolute values), ``jac`` [n_jac, 9, np] with ``jac_gid`` (the
+    Jacobians of the Gaussians named by ``ju``), and ``eflip`` (gid, mask, dJ [., 3, np], gE [., 3]) for
+    Gaussians with a borderline colour clamp.
     """
     lib = _load()
     keep = []
@@ -229,8 +285,9 @@ def render(scene, camera, model, opts=None, window=None, nthreads=1, brute_force
     n_listed = np.zeros((h, w), dtype=np.int32)
     fragile = np.zeros((h, w), dtype=np.uint8)
     sig = np.zeros((h, w), dtype=np.uint64)
-    fwd = _Fwd(_ptr(image), _ptr(overdraw), _ptr(n_listed), _ptr(fragile), _ptr(sig))
-    res = dict(image=image, overdraw=overdraw, n_listed=n_listed, fragile=fragile.astype(bool), signature=sig)
+    nout = np.zeros((h, w), dtype=np.int32)
+    fwd = _Fwd(_ptr(image), _ptr(overdraw), _ptr(n_listed), _ptr(fragile), _ptr(sig), _ptr(nout))
+    res = dict(image=image, overdraw=overdraw, n_listed=n_listed, signature=sig, n_outcomes=nout)
     bwd_p = None
     if dl_dimage is not None:
         dl = _f64(dl_dimage).reshape(h, w, 3)
@@ -244,10 +301,39 @@ def render(scene, camera, model, opts=None, window=None, nthreads=1, brute_force
                    *(_ptr(scales["s_" + k]) for k in names))
         bwd_p = C.byref(bwd)
         keep.append(dl)
+    alt = _Alt() if outcomes else None
     lib.orc_render(C.byref(sc), C.byref(cam), C.byref(m_), C.byref(o), C.byref(win), int(nthreads),
-                   int(bool(brute_force)), C.byref(fwd), bwd_p)
-    res["fragile"] = fragile.astype(bool)
+                   int(bool(brute_force)), C.byref(fwd), bwd_p, C.byref(alt) if alt is not None else None)
+    res["fragile"] = fragile > 0
+    res["unresolved"] = fragile == 2
     if dl_dimage is not None:
         res.update(grads)
-        res["fragile_gauss"] = fg.astype(bool)
+        res["fragile_gauss"] = fg
+    if alt is not None:
+        try:
+            res["alt"] = _alt_arrays(alt)
+        finally:
+            lib.orc_free_alt(C.byref(alt))
     return res
+
+
+def _copy(ptr, n, dtype, shape=None):
+    if n == 0 or not ptr:
+        return np.zeros((0,) + tuple(shape or ()), dtype=dtype)
+    count = int(n * (np.prod(shape) if shape else 1))
+    arr = np.ctypeslib.as_array(C.cast(ptr, C.POINTER(np.ctypeslib.as_ctypes_type(dtype))), shape=(count,))
+    return arr.copy().reshape((n,) + tuple(shape or ()))
+
+
+def _alt_arrays(a):
+    npar = int(a.n_params)
+    return dict(
+        fwd=dict(pix=_copy(a.fwd_pix, a.n_fwd, np.int64), outcome=_copy(a.fwd_outcome, a.n_fwd, np.int32),
+                 overdraw=_copy(a.fwd_overdraw, a.n_fwd, np.int32), image=_copy(a.fwd_image, a.n_fwd, np.float64, (3,))),
+        grad=dict(pix=_copy(a.grad_pix, a.n_grad, np.int64), outcome=_copy(a.grad_outcome, a.n_grad, np.int32),
+                  ju=_copy(a.grad_ju, a.n_grad, np.int32), rec=_copy(a.grad_rec, a.n_grad, np.float64, (18,))),
+        jac=_copy(a.jac, a.n_jac, np.float64, (9, npar)), jac_gid=_copy(a.jac_gid, a.n_jac, np.int64),
+        eflip=dict(gid=_copy(a.eflip_gid, a.n_eflip, np.int64), mask=_copy(a.eflip_mask, a.n_eflip, np.uint8),
+                   dJ=_copy(a.eflip_dJ, a.n_eflip, np.float64, (3, npar)),
+                   gE=_copy(a.eflip_gE, a.n_eflip, np.float64, (3,))),
+    )

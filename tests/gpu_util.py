@@ -38,38 +38,6 @@ def frame_arrays(frame):
     )
 
 
-def grad_mismatch(gpu, ref, rel=1e-3, exclude=None, scale=None, scale_rel=1e-4):
-    """Elements violating |g - g_ref| <= rel * max(|g_ref|, 1e-3 * max|g_ref|) + scale_rel * scale, per tensor.
-
-    ``scale`` is the oracle's error scale of each gradient (sum of absolute per-pixel terms through the
-    absolute Jacobian). A gradient that is a sum of terms that cancel can only be as accurate as its
-    largest terms: in FP32 each term carries the error of the O(1) running quantities the replay
-    differences (1 - S at the saturating splat, L0 - sum E pbar, A - E_k taubar_k), about n u ~ 1e-5
-    absolute for lists of n ~ 100 splats, i.e. up to ~1e-4 of the term's size. A wrong term is off by
-    O(scale).
-    """
-    a = np.asarray(gpu, np.float64).reshape(len(ref), -1)
-    b = np.asarray(ref, np.float64).reshape(len(ref), -1)
-    floor = 1e-3 * np.abs(b).max() if b.size else 0.0
-    tol = rel * np.maximum(np.abs(b), floor)
-    if scale is not None:
-        tol = tol + scale_rel * np.asarray(scale, np.float64).reshape(len(ref), -1)
-    bad = np.abs(a - b) > tol
-    if exclude is not None:
-        bad[exclude] = False
-    return bad
-
-
-def describe_mismatch(gpu, ref, bad, scale=None, limit=5):
-    a = np.asarray(gpu, np.float64).reshape(len(ref), -1)
-    b = np.asarray(ref, np.float64).reshape(len(ref), -1)
-    s = None if scale is None else np.asarray(scale, np.float64).reshape(len(ref), -1)
-    out = []
-    for gi, j in list(zip(*np.nonzero(bad)))[:limit]:
-        out.append(f"[{gi},{j}] gpu={a[gi, j]:.6g} ref={b[gi, j]:.6g}" + ("" if s is None else f" scale={s[gi, j]:.4g}"))
-    return "; ".join(out)
-
-
 def batch_arrays(frame):
     """Host copies of a (batch) frame's buffers: records [n_views n, 12], keys, values, ranges [tiles, 2],
     replay state [pixels, 8], and the per-view pixel / tile bases."""

@@ -22,7 +22,8 @@ if not torch.cuda.is_available():
 import oracle  # noqa: E402
 from paper_2603_02887_gb300 import _abi, synth  # noqa: E402
 from paper_2603_02887_gb300.render import PARAM_KEYS, Renderer  # noqa: E402
-from tests.gpu_util import batch_arrays, describe_mismatch, frame_arrays, grad_mismatch, upload  # noqa: E402
+from tests import parity  # noqa: E402
+from tests.gpu_util import batch_arrays, frame_arrays, upload  # noqa: E402
 
 MODELS = ["exp", "sub", "lin", "sup"]
 NT = os.cpu_count() or 4
@@ -95,38 +96,27 @@ def _tiny_views():
 
 @pytest.mark.parametrize("model", MODELS)
 def test_batch_gradient_is_sum_over_views_oracle(rnd, model):
+    """Each view of a batch against the oracle (every pixel, tests/parity.py), and the batch gradient
+    against the sum of the oracle's per-view gradients for the outcomes each view's pixels took."""
     scene = synth.tiny_scene(0)
     cams = _tiny_views()
     params = upload(scene)
-    images, _, frame = rnd.render_batch(params, cams, model)
-    dls, ref = [], None
+    images, ods, frame = rnd.render_batch(params, cams, model)
+    dls, refs = [], []
     for v, cam in enumerate(cams):
         H, W = cam["height"], cam["width"]
-        ref0 = oracle.render(scene, cam, model, nthreads=NT)
-        ok = ~ref0["fragile"]
-        assert ref0["fragile"].sum() <= max(2, 0.01 * ok.size)
-        err = np.abs(frame.split(images)[v].cpu().numpy() - ref0["image"])[ok]
-        assert err.max() <= 1e-4, (v, err.max())
-        g = synth.upstream_gradient(H, W, seed=20 + v).astype(np.float64) * ok[..., None]
-        r = oracle.render(scene, cam, model, nthreads=NT, dl_dimage=g)
+        g = synth.upstream_gradient(H, W, seed=20 + v)
+        r = oracle.render(scene, cam, model, nthreads=NT, dl_dimage=g.astype(np.float64), outcomes=True)
+        m = parity.assert_forward(frame.split(images)[v].cpu().numpy(), frame.split(ods)[v].cpu().numpy(), r,
+                                  label=f"view {v}")
+        assert m.n_unresolved == 0, m.summary()
+        refs.append(parity.reference_gradients(r, m))
         dls.append(g.reshape(-1, 3))
-        if ref is None:
-            ref = {k: np.array(val, copy=True) for k, val in r.items() if k.startswith(("d_", "s_"))}
-            ref["fragile_gauss"] = r["fragile_gauss"].copy()
-        else:
-            for k in ref:
-                if k.startswith(("d_", "s_")):
-                    ref[k] = ref[k] + r[k]
-            ref["fragile_gauss"] |= r["fragile_gauss"]
-    dl = torch.from_numpy(np.concatenate(dls).astype(np.float32)).cuda()
+    dl = torch.from_numpy(np.concatenate(dls)).cuda()
     grads = rnd.backward(frame, params, dl)
-    report = {}
-    for k in PARAM_KEYS:
-        a = grads["d_" + k].cpu().numpy()
-        bad = grad_mismatch(a, ref["d_" + k], exclude=ref["fragile_gauss"], scale=ref["s_" + k])
-        if bad.any():
-            report[k] = f"{int(bad.sum())} of {bad.size}: " + describe_mismatch(a, ref["d_" + k], bad, ref["s_" + k])
-    assert not report, report
+    rep = parity.assert_gradients({k: v.cpu().numpy() for k, v in grads.items()}, parity.sum_refs(refs), None,
+                                  label=model)
+    print(f"[parity] batch of 3 views {model}: {rep.summary()}")
 
 
 @pytest.mark.parametrize("model", ["exp", "sup"])

@@ -7,7 +7,9 @@ on 16x16), on outputs the FP64 oracle computes one by one: windows of the full f
   ragged since 1080 = 67.5 x 16);
 * differentiation: 1M clustered Gaussians at 1297x840, forward + path-replay backward for the four models
   with an L1-type upstream gradient restricted to a 256x256 window, against the oracle's gradients of that
-  window; and central differences of the GPU render itself on 64 random raw parameters.
+  window; and the GPU's gradient on 64 random raw parameters against central differences of the FP64
+  oracle.
+Every pixel of a window is checked against the oracle's outcomes for it (tests/parity.py).
 Inputs are seeded synthetic scenes (paper_2603_02887_gb300.synth); no oracle input comes from the GPU.
 """
 import os
@@ -24,7 +26,8 @@ import bench  # noqa: E402
 import oracle  # noqa: E402
 from paper_2603_02887_gb300 import synth  # noqa: E402
 from paper_2603_02887_gb300.render import PARAM_KEYS, Renderer  # noqa: E402
-from tests.gpu_util import describe_mismatch, grad_mismatch, upload  # noqa: E402
+from tests import parity  # noqa: E402
+from tests.gpu_util import upload  # noqa: E402
 
 MODELS = ["exp", "sub", "lin", "sup"]
 NT = os.cpu_count() or 4
@@ -51,12 +54,10 @@ def test_single_view_500k_1080p_windows(rnd, single_view, model):
     img, od = image.cpu().numpy(), overdraw.cpu().numpy()
     for win in ((936, 516, 48, 48), (400, 300, 40, 40), (900, 1080 - 13, 64, 13)):
         x0, y0, w, h = win
-        ref = oracle.render(scene, cam, model, window=win, nthreads=NT)
-        ok = ~ref["fragile"]
-        assert ref["fragile"].sum() <= max(2, 0.01 * ok.size)
-        err = np.abs(img[y0:y0 + h, x0:x0 + w] - ref["image"])[ok]
-        assert err.max() <= 1e-4, (win, err.max())
-        assert np.array_equal(od[y0:y0 + h, x0:x0 + w][ok], ref["overdraw"][ok]), win
+        ref = oracle.render(scene, cam, model, window=win, nthreads=NT, outcomes=True)
+        m = parity.assert_forward(img[y0:y0 + h, x0:x0 + w], od[y0:y0 + h, x0:x0 + w], ref, label=f"{model} {win}")
+        assert m.n_unresolved == 0, m.summary()
+        print(f"[parity] 500k/1080p {model} window {win}: {m.summary()}")
         assert ref["overdraw"].mean() > 0.5, win  # the windows are not empty
 
 
@@ -72,65 +73,93 @@ def test_differentiation_1m_crop_gradients(rnd, diff_scene, model):
     x0, y0, w, h = win
     params = upload(scene)
     image, overdraw, frame = rnd.render(params, cam, model, OPTS[model])
-    ref0 = oracle.render(scene, cam, model, window=win, nthreads=NT)
-    ok = ~ref0["fragile"]
-    err = np.abs(image.cpu().numpy()[y0:y0 + h, x0:x0 + w] - ref0["image"])[ok]
-    assert err.max() <= 1e-4
-    g = synth.upstream_gradient(h, w, seed=11).astype(np.float64) * ok[..., None]
-    ref = oracle.render(scene, cam, model, window=win, nthreads=NT, dl_dimage=g)
+    g = synth.upstream_gradient(h, w, seed=11)
+    ref = oracle.render(scene, cam, model, window=win, nthreads=NT, dl_dimage=g.astype(np.float64), outcomes=True)
+    m = parity.assert_forward(image.cpu().numpy()[y0:y0 + h, x0:x0 + w], overdraw.cpu().numpy()[y0:y0 + h, x0:x0 + w],
+                              ref, label=model)
+    assert m.n_unresolved == 0, m.summary()
     dl = np.zeros((cam["height"], cam["width"], 3), np.float32)
     dl[y0:y0 + h, x0:x0 + w] = g
     grads = rnd.backward(frame, params, torch.from_numpy(dl).cuda())
     torch.cuda.synchronize()
-    report = {}
-    for k in PARAM_KEYS:
-        a = grads["d_" + k].cpu().numpy()
-        bad = grad_mismatch(a, ref["d_" + k], exclude=ref["fragile_gauss"], scale=ref["s_" + k])
-        if bad.any():
-            report[k] = f"{int(bad.sum())} of {bad.size}: " + describe_mismatch(a, ref["d_" + k], bad, ref["s_" + k])
-    assert not report, report
+    rep = parity.assert_gradients({k: v.cpu().numpy() for k, v in grads.items()}, ref, m, label=model)
+    print(f"[parity] 1M/1297x840 crop {model}: {m.summary()}; {rep.summary()}")
     assert np.count_nonzero(ref["d_opacity_logits"]) > 1000  # the window reaches many Gaussians
 
 
+def _window_subscene(scene, cam, win):
+    """The Gaussians that can reach a window: their candidate disc (alpha >= alpha_min 2^-0.5, the
+    oracle's widest candidate threshold) around the projected mean meets the window, with a 2 px margin.
+    A render of the window from them equals the full scene's."""
+    p = oracle.project(scene, cam)
+    rec = p["rec"]
+    A, B, C, aleph = rec[:, 2], rec[:, 3], rec[:, 4], rec[:, 5]
+    lam_min = 0.5 * (A + C) - np.sqrt(0.25 * (A - C) ** 2 + B ** 2)  # smallest eigenvalue of the conic
+    thr = np.float32(1 / 255.0) * 2 ** -0.5
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = np.sqrt(np.maximum(2 * np.log(aleph / thr), 0) / lam_min) + 2
+    x0, y0, w, h = win
+    sel = (p["z32"] > np.float32(0.2)) & (aleph >= thr) & (lam_min > 0)
+    sel &= (rec[:, 0] + r >= x0) & (rec[:, 0] - r <= x0 + w) & (rec[:, 1] + r >= y0) & (rec[:, 1] - r <= y0 + h)
+    idx = np.nonzero(sel)[0]
+    return {k: v[idx] for k, v in scene.items()}, idx
+
+
 def test_differentiation_1m_finite_differences(rnd, diff_scene):
-    """Central differences of the GPU render (loss accumulated in FP64) on 64 random raw parameters of
-    Gaussians that reach the window, against the GPU's path-replay gradient. A sample whose overdraw map
-    changes between the two sides of the stencil is redrawn (a decision flipped)."""
+    """The GPU's path-replay gradient on 64 random raw parameters against central differences of the
+    FP64 oracle (L = sum(g * image) over a 128x128 window of the 1M-Gaussian frame, g nonzero only there),
+    at the benchmark spec's relative 1e-3.
+
+    The oracle renders the window from the Gaussians that can reach it (the same image as from the whole
+    scene, checked). Steps are h = 1e-5 max(1, |theta|); a sample is redrawn when any pixel's composited
+    list, stop or clamp state differs between the two sides of the stencil (L is not differentiable
+    there). Where a pixel's GPU result took another legitimate outcome than the FP64 walk, the expected
+    value carries that outcome's difference (tests/parity.py); the tolerance is that of the crop test."""
     scene, cam = diff_scene
-    win = (520, 300, 256, 256)
+    win = (584, 364, 128, 128)
     x0, y0, w, h = win
     model = "sup"
     params = upload(scene)
-    _, od0, frame = rnd.render(params, cam, model, OPTS[model])
+    img0, od0, frame = rnd.render(params, cam, model, OPTS[model])
+    gw = synth.upstream_gradient(h, w, seed=12).astype(np.float64)
     g = np.zeros((cam["height"], cam["width"], 3), np.float32)
-    g[y0:y0 + h, x0:x0 + w] = synth.upstream_gradient(h, w, seed=12)
-    gt = torch.from_numpy(g).cuda()
-    grads = {k: v.cpu().numpy() for k, v in rnd.backward(frame, params, gt).items()}
-    live = np.nonzero(np.abs(grads["d_opacity_logits"]) > 0.05 * np.abs(grads["d_opacity_logits"]).max())[0]
+    g[y0:y0 + h, x0:x0 + w] = gw
+    grads = {k: v.cpu().numpy() for k, v in rnd.backward(frame, params, torch.from_numpy(g).cuda()).items()}
+    sub, idx = _window_subscene(scene, cam, win)
+    ref = oracle.render(sub, cam, model, window=win, nthreads=NT, dl_dimage=gw, outcomes=True)
+    full = oracle.render(scene, cam, model, window=win, nthreads=NT)
+    assert np.array_equal(ref["image"], full["image"]) and np.array_equal(ref["overdraw"], full["overdraw"])
+    m = parity.assert_forward(img0.cpu().numpy()[y0:y0 + h, x0:x0 + w], od0.cpu().numpy()[y0:y0 + h, x0:x0 + w], ref)
+    gref = parity.reference_gradients(ref, m)
+    live = np.nonzero(np.abs(ref["d_opacity_logits"]) > 0.05 * np.abs(ref["d_opacity_logits"]).max())[0]
     rng = np.random.default_rng(13)
-    checked = 0
+    checked, worst = 0, 0.0
     for _ in range(400):
         if checked == 64:
             break
         key = PARAM_KEYS[rng.integers(0, len(PARAM_KEYS))]
-        gi = int(rng.choice(live))
-        flat = params[key].view(params[key].shape[0], -1)
+        li = int(rng.choice(live))
+        flat = sub[key].reshape(len(sub[key]), -1)
         j = int(rng.integers(0, flat.shape[1]))
-        an = grads["d_" + key].reshape(len(scene[key]), -1)[gi, j]
-        if abs(an) < 1e-2 * np.abs(grads["d_" + key]).max():
-            continue
-        th = float(flat[gi, j])
-        hstep = 3e-4 * max(1.0, abs(th))
-        losses, ods = [], []
+        exp_adj = gref.d[key][li, j] - ref["d_" + key].reshape(len(sub[key]), -1)[li, j]
+        th = float(flat[li, j])
+        hstep = 1e-5 * max(1.0, abs(th))
+        outs = []
         for sgn in (1, -1):
-            flat[gi, j] = th + sgn * hstep
-            img, od, _ = rnd.render(params, cam, model, OPTS[model])
-            losses.append(float((img.double() * gt.double()).sum()))
-            ods.append(od)
-        flat[gi, j] = th
-        if not (torch.equal(ods[0], od0) and torch.equal(ods[1], od0)):
+            s2 = {k: v.astype(np.float64).copy() for k, v in sub.items()}
+            s2[key].reshape(len(s2[key]), -1)[li, j] = th + sgn * hstep
+            outs.append(oracle.render(s2, cam, model, window=win, nthreads=NT))
+        if not all(np.array_equal(o["signature"], ref["signature"]) for o in outs):
             continue
-        fd = (losses[0] - losses[1]) / (2 * hstep)
-        assert abs(fd - an) <= 0.05 * abs(an) + 1e-3, (key, gi, j, fd, an)
+        fd = (np.sum(gw * outs[0]["image"]) - np.sum(gw * outs[1]["image"])) / (2 * hstep)
+        expected = fd + exp_adj
+        an = float(grads["d_" + key].reshape(len(scene[key]), -1)[idx[li], j])
+        floor = parity.FLOOR_REL * np.abs(gref.d[key]).max()
+        tol = (parity.GRAD_REL * max(abs(expected), floor) + gref.allow[key][li, j]
+               + parity.SCALE_REL * gref.s[key][li, j])
+        assert abs(an - expected) <= tol, (key, li, j, an, expected, fd, tol)
+        worst = max(worst, abs(an - expected) / max(abs(expected), floor))
         checked += 1
     assert checked == 64
+    print(f"[parity] 1M/1297x840 finite differences of the FP64 oracle: 64 samples, worst |an - fd| / "
+          f"max(|fd|, floor) = {worst:.2e}")
