@@ -92,7 +92,9 @@ class _Bwd(C.Structure):
     _fields_ = [("dl_dimage", C.c_void_p), ("d_means", C.c_void_p), ("d_log_scales", C.c_void_p),
                 ("d_quats", C.c_void_p), ("d_opacity_logits", C.c_void_p), ("d_sh", C.c_void_p),
                 ("fragile_gauss", C.c_void_p), ("s_means", C.c_void_p), ("s_log_scales", C.c_void_p),
-                ("s_quats", C.c_void_p), ("s_opacity_logits", C.c_void_p), ("s_sh", C.c_void_p)]
+                ("s_quats", C.c_void_p), ("s_opacity_logits", C.c_void_p), ("s_sh", C.c_void_p),
+                ("p_means", C.c_void_p), ("p_log_scales", C.c_void_p), ("p_quats", C.c_void_p),
+                ("p_opacity_logits", C.c_void_p), ("p_sh", C.c_void_p)]
 
 
 def _load():
@@ -261,14 +263,16 @@ def render(scene, camera, model, opts=None, window=None, nthreads=1, brute_force
     n_outcomes[h, w]) and, when ``dl_dimage`` [h, w, 3] is given, the gradients d_means, d_log_scales,
     d_quats, d_opacity_logits, d_sh (same shapes as the parameters), fragile_gauss[n] (bit ch: colour
     channel ch is borderline at its max(0, .) clamp) and, per gradient, its error scale s_* (the sum of the
-    absolute per-pixel terms chained through the absolute Jacobian). Image, overdraw and gradients are
+    absolute per-pixel terms chained through the absolute Jacobian) and p_* (the same with each term
+    weighted by the bound of the relative FP32 error of its splat's pbar at that pixel). Image, overdraw
+    and gradients are
     those of the FP64 walk. ``fragile`` is 1 where a decision of the pixel's walk is borderline (within the
     FP32 error bound of its threshold) and 2 where the enumeration was cut short (``unresolved``).
 
     With ``outcomes`` the borderline decisions of every pixel are enumerated and ``alt`` holds every
     outcome of every pixel that has more than one: ``fwd`` rows (pix = y w + x in the window, outcome,
-    overdraw, image[3]), with ``dl_dimage`` also ``grad`` rows (pix, outcome, ju, rec[18]: the per-entry
-    record-gradient terms and their absolute values), ``jac`` [n_jac, 9, np] with ``jac_gid`` (the
+    overdraw, image[3]), with ``dl_dimage`` also ``grad`` rows (pix, outcome, ju, rec[27]: the per-entry
+    record-gradient terms, their absolute values and their FP32 error bounds), ``jac`` [n_jac, 9, np] with ``jac_gid`` (the
     Jacobians of the Gaussians named by ``ju``), and ``eflip`` (gid, mask, dJ [., 3, np], gE [., 3]) for
     Gaussians with a borderline colour clamp.
     """
@@ -296,9 +300,10 @@ def render(scene, camera, model, opts=None, window=None, nthreads=1, brute_force
         fg = np.zeros(n, dtype=np.uint8)
         names = ("means", "log_scales", "quats", "opacity_logits", "sh")
         scales = {"s_" + k: np.zeros_like(grads["d_" + k]) for k in names}
+        scales.update({"p_" + k: np.zeros_like(grads["d_" + k]) for k in names})
         grads.update(scales)
         bwd = _Bwd(_ptr(dl), *(_ptr(grads["d_" + k]) for k in names), _ptr(fg),
-                   *(_ptr(scales["s_" + k]) for k in names))
+                   *(_ptr(scales["s_" + k]) for k in names), *(_ptr(scales["p_" + k]) for k in names))
         bwd_p = C.byref(bwd)
         keep.append(dl)
     alt = _Alt() if outcomes else None
@@ -331,7 +336,7 @@ def _alt_arrays(a):
         fwd=dict(pix=_copy(a.fwd_pix, a.n_fwd, np.int64), outcome=_copy(a.fwd_outcome, a.n_fwd, np.int32),
                  overdraw=_copy(a.fwd_overdraw, a.n_fwd, np.int32), image=_copy(a.fwd_image, a.n_fwd, np.float64, (3,))),
         grad=dict(pix=_copy(a.grad_pix, a.n_grad, np.int64), outcome=_copy(a.grad_outcome, a.n_grad, np.int32),
-                  ju=_copy(a.grad_ju, a.n_grad, np.int32), rec=_copy(a.grad_rec, a.n_grad, np.float64, (18,))),
+                  ju=_copy(a.grad_ju, a.n_grad, np.int32), rec=_copy(a.grad_rec, a.n_grad, np.float64, (27,))),
         jac=_copy(a.jac, a.n_jac, np.float64, (9, npar)), jac_gid=_copy(a.jac_gid, a.n_jac, np.int64),
         eflip=dict(gid=_copy(a.eflip_gid, a.n_eflip, np.int64), mask=_copy(a.eflip_mask, a.n_eflip, np.uint8),
                    dJ=_copy(a.eflip_dJ, a.n_eflip, np.float64, (3, npar)),

@@ -114,6 +114,15 @@ typedef struct {
   double* s_quats;
   double* s_opacity_logits;
   double* s_sh;
+  /* Optional, likewise: the sum over the per-pixel terms of |term| times the bound of the relative error
+   * of the GPU's FP32 pbar of that entry (the FP32 record and running sums; composite()), chained through
+   * the absolute Jacobian: a bound of what the GPU's inputs, as opposed to its accumulation, put into
+   * each gradient. */
+  double* p_means;
+  double* p_log_scales;
+  double* p_quats;
+  double* p_opacity_logits;
+  double* p_sh;
 } orc_bwd;
 
 /* ------------------------------------------------------------------------------------------------
@@ -165,10 +174,11 @@ typedef struct {
  * (or the final alpha of a plain list), E[3 i..] its emission. band[i] (NULL: all decisions exact) is the
  * error bound of the FP32 log2(raw[i]) that the GPU compares; from it follow the bounds of the running
  * sums, propagated to first order and widened by ORC_SAFETY. Writes, for the composited entries j < m,
- * idx[j] (candidate index), alpha[j], clamped[j] (alpha_max clamp taken) and pbar[j]. */
+ * idx[j] (candidate index), alpha[j], clamped[j] (alpha_max clamp taken), pbar[j] and, when perr is not
+ * NULL, perr[j]: the bound of the relative error of the GPU's FP32 pbar[j] (0 without bands). */
 static void composite(int kind, double param, const comp_opts* co, const double bg[3], int n, const double* raw,
                       const double* band, const double* E, decider* d, int* idx, double* alpha, uint8_t* clamped,
-                      double* pbar, comp_result* r) {
+                      double* pbar, double* perr, comp_result* r) {
   memset(r, 0, sizeof(*r));
   r->k_lin = r->k_exp = -1;
   double C[3] = {0, 0, 0};
@@ -188,7 +198,7 @@ static void composite(int kind, double param, const comp_opts* co, const double 
     const double a = cl ? co->alpha_max : raw[i];
     const double ea = cl ? 0.0 : kLn2d * bl; /* relative error bound of alpha */
     const double* Ei = &E[3 * i];
-    double p;
+    double p, pe_rel = 0.0;
     int stop_here = 0, stop_before = 0;
     if (kind == ORC_EXP) {
       /* pbar_i = alpha_i T_i with T_i = prod_{j<i}(1 - alpha_j) (Table 1, row 1). The exponential never
@@ -197,6 +207,7 @@ static void composite(int kind, double param, const comp_opts* co, const double 
       const double rel = relT + a * ea / (1.0 - a) + 2.0 * U32;
       if (co->t_eps > 0 && decide(d, testT < co->t_eps, testT - co->t_eps, ORC_SAFETY * rel * testT)) break;
       p = a * T;
+      pe_rel = ea + relT + U32;
       T = testT;
       relT = rel;
     } else if (kind == ORC_QUAD || kind == ORC_BLEND) {
@@ -217,10 +228,12 @@ static void composite(int kind, double param, const comp_opts* co, const double 
       const double err_Sn = err_S + err_pt + U32 * Sn;
       if (decide(d, Sn >= 1.0, Sn - 1.0, ORC_SAFETY * err_Sn)) {
         p = 1.0 - S;
+        pe_rel = p > 0 ? (err_S + U32) / p : 0.0;
         sat = 1;
         stop_here = 1;
       } else {
         p = pt;
+        pe_rel = pt > 0 ? err_pt / pt : 0.0;
         S = Sn;
         err_S = err_Sn;
         tau += a;
@@ -239,6 +252,7 @@ static void composite(int kind, double param, const comp_opts* co, const double 
           r->k_exp = m;
         } else {
           pe = a * T;
+          pe_rel = ea + relT + U32;
           T = testT;
           relT = rel;
         }
@@ -247,8 +261,18 @@ static void composite(int kind, double param, const comp_opts* co, const double 
       if (!stop_before) {
         if (!sat) {
           const double Sn = S + a, err_Sn = err_S + a * ea + U32 * Sn;
-          if (decide(d, Sn >= 1.0, Sn - 1.0, ORC_SAFETY * err_Sn)) { pl = 1.0 - S; S = 1.0; sat = 1; r->k_lin = m; }
-          else { pl = a; S = Sn; err_S = err_Sn; }
+          if (decide(d, Sn >= 1.0, Sn - 1.0, ORC_SAFETY * err_Sn)) {
+            pl = 1.0 - S;
+            pe_rel = fmax(pe_rel, pl > 0 ? (err_S + U32) / pl : 0.0);
+            S = 1.0;
+            sat = 1;
+            r->k_lin = m;
+          } else {
+            pl = a;
+            pe_rel = fmax(pe_rel, ea);
+            S = Sn;
+            err_S = err_Sn;
+          }
         }
         for (int ch = 0; ch < 3; ++ch) Ce[ch] += Ei[ch] * pe;
         p = (1.0 - gam) * pl + gam * pe;
@@ -262,6 +286,7 @@ static void composite(int kind, double param, const comp_opts* co, const double 
     alpha[m] = a;
     clamped[m] = (uint8_t)cl;
     pbar[m] = p;
+    if (perr) perr[m] = band ? ORC_SAFETY * pe_rel : 0.0;
     for (int ch = 0; ch < 3; ++ch) C[ch] += Ei[ch] * p;
     ++m;
     if (stop_here) break;
@@ -600,6 +625,9 @@ static double alpha_band(const splat_d* s, double dx, double dy, double l2) {
   return ORC_SAFETY * U32 * (8.0 + 4.0 * fabs(L) + 4.0 * fabs(l2) + 35.0 * Q + pos);
 }
 
+/* Per-entry record-gradient terms: ORC_TERMS values per (pixel, composited entry), see entry_terms(). */
+#define ORC_TERMS 27
+
 /* Sparse outputs of a pixel with several outcomes (per worker thread, merged after the join). */
 typedef struct {
   int64_t pix;
@@ -610,7 +638,7 @@ typedef struct {
 typedef struct {
   int64_t pix;
   int32_t outcome, lid;
-  double g[18]; /* the 9 record-gradient terms and their absolute values */
+  double g[ORC_TERMS]; /* entry_terms() */
 } alt_grad_row;
 
 typedef struct {
@@ -646,7 +674,8 @@ typedef struct {
   int64_t* grad_pix;
   int32_t* grad_outcome;
   int32_t* grad_ju;      /* row of jac / jac_gid */
-  double* grad_rec;      /* [n_grad][18]: dL/d(u, v, A, B, C, aleph, E0, E1, E2) and their absolute values */
+  double* grad_rec;      /* [n_grad][27]: the terms of entry_terms(): dL/d(u, v, A, B, C, aleph, E0, E1, E2),
+                            their absolute values and their FP32 error bounds */
   int32_t n_params;      /* 11 + 3 K */
   int64_t n_jac;
   int64_t* jac_gid;      /* Gaussians named by the rows above */
@@ -679,7 +708,7 @@ typedef struct {
   orc_bwd* bwd;
   int want_alt;
   alt_buf* alt;          /* per thread */
-  double* grad_rec;      /* per thread [nthreads][nloc][18] */
+  double* grad_rec;      /* per thread [nthreads][nloc][ORC_TERMS] */
   int nthreads;
 } render_job;
 
@@ -696,7 +725,7 @@ static uint64_t fnv(uint64_t h, uint64_t v) {
 /* Per-thread scratch of one pixel's walk. */
 typedef struct {
   int cap;
-  double *raw, *band, *E, *alpha, *pbar, *Ee, *dal, *dE;
+  double *raw, *band, *E, *alpha, *pbar, *perr, *Ee, *dal, *dE;
   int* idx;
   uint8_t* clamped;
 } walk_buf;
@@ -709,6 +738,7 @@ static void walk_reserve(walk_buf* b, int n) {
   b->E = (double*)realloc(b->E, sizeof(double) * 3 * n);
   b->alpha = (double*)realloc(b->alpha, sizeof(double) * n);
   b->pbar = (double*)realloc(b->pbar, sizeof(double) * n);
+  b->perr = (double*)realloc(b->perr, sizeof(double) * n);
   b->Ee = (double*)realloc(b->Ee, sizeof(double) * 3 * n);
   b->dal = (double*)realloc(b->dal, sizeof(double) * n);
   b->dE = (double*)realloc(b->dE, sizeof(double) * 3 * n);
@@ -717,18 +747,21 @@ static void walk_reserve(walk_buf* b, int n) {
 }
 
 static void walk_free(walk_buf* b) {
-  free(b->raw); free(b->band); free(b->E); free(b->alpha); free(b->pbar); free(b->Ee); free(b->dal);
+  free(b->raw); free(b->band); free(b->E); free(b->alpha); free(b->pbar); free(b->perr); free(b->Ee); free(b->dal);
   free(b->dE); free(b->idx); free(b->clamped);
 }
 
-/* The 9 record-gradient terms of composited entry j of a walk at pixel (px, py) (and their absolute
- * values), given dL/dalpha_j and dL/dE_j. */
+/* The terms of composited entry j of a walk at pixel (px, py), given dL/dalpha_j and dL/dE_j: out[0..9)
+ * the 9 record-gradient terms dL/d(u, v, A, B, C, aleph, E0, E1, E2), out[9..18) their absolute values,
+ * out[18..27) their absolute values times rel, the bound of the relative error of the GPU's FP32 pbar_j
+ * (which is proportional to alpha_j: the error the FP32 record and running sums carry into the term). */
 static void entry_terms(const splat_d* s, double px, double py, double a, int clamped, double dal,
-                        const double* dE, double* out18) {
-  memset(out18, 0, sizeof(double) * 18);
+                        const double* dE, double rel, double* out) {
+  memset(out, 0, sizeof(double) * ORC_TERMS);
   for (int ch = 0; ch < 3; ++ch) {
-    out18[6 + ch] = dE[ch];
-    out18[15 + ch] = fabs(dE[ch]);
+    out[6 + ch] = dE[ch];
+    out[15 + ch] = fabs(dE[ch]);
+    out[24 + ch] = fabs(dE[ch]) * rel;
   }
   if (clamped) return; /* alpha = alpha_max does not depend on the splat */
   /* alpha = aleph exp(-q/2), q = A dx^2 + 2 B dx dy + C dy^2, (dx, dy) = p - (u, v) */
@@ -740,8 +773,9 @@ static void entry_terms(const splat_d* s, double px, double py, double a, int cl
   double t[6] = {dq * (-2.0 * (A * dx + B * dy)), dq * (-2.0 * (B * dx + C * dy)), dq * dx * dx,
                  dq * 2.0 * dx * dy, dq * dy * dy, dal * G};
   for (int r = 0; r < 6; ++r) {
-    out18[r] = t[r];
-    out18[9 + r] = fabs(t[r]);
+    out[r] = t[r];
+    out[9 + r] = fabs(t[r]);
+    out[18 + r] = fabs(t[r]) * rel;
   }
 }
 
@@ -751,7 +785,7 @@ static void* render_rows(void* argp) {
   const orc_window* w = J->win;
   int kind = J->model->kind;
   double par = J->model->param;
-  double* grec = J->grad_rec ? J->grad_rec + (size_t)wa->tid * (size_t)J->nloc * 18 : NULL;
+  double* grec = J->grad_rec ? J->grad_rec + (size_t)wa->tid * (size_t)J->nloc * ORC_TERMS : NULL;
   alt_buf* ab = J->alt ? &J->alt[wa->tid] : NULL;
   const comp_opts co = {J->o->alpha_min, J->o->alpha_max, J->o->t_eps, J->o->max_splats};
   walk_buf wb;
@@ -787,7 +821,7 @@ static void* render_rows(void* argp) {
         decider d = {path, plen, 0};
         comp_result r;
         composite(kind, par, &co, J->o->background, n, wb.raw, wb.band, wb.E, &d, wb.idx, wb.alpha, wb.clamped,
-                  wb.pbar, &r);
+                  wb.pbar, wb.perr, &r);
         const int oc = outcomes++;
         if (oc == 0) {
           for (int ch = 0; ch < 3; ++ch) J->fwd->image[3 * pix + ch] = r.color[ch];
@@ -829,18 +863,18 @@ static void* render_rows(void* argp) {
         if (several && ab) ab->g = (alt_grad_row*)grow(ab->g, &ab->cg, ab->ng + (size_t)r.m, sizeof(alt_grad_row));
         for (int i = 0; i < r.m; ++i) {
           const int lid = L[wb.idx[i]].g;
-          double t18[18];
-          entry_terms(&J->sp[lid], px, py, wb.alpha[i], wb.clamped[i], wb.dal[i], &wb.dE[3 * i], t18);
+          double tt[ORC_TERMS];
+          entry_terms(&J->sp[lid], px, py, wb.alpha[i], wb.clamped[i], wb.dal[i], &wb.dE[3 * i], wb.perr[i], tt);
           if (oc == 0) {
-            double* gr = grec + (size_t)lid * 18;
-            for (int k = 0; k < 18; ++k) gr[k] += t18[k];
+            double* gr = grec + (size_t)lid * ORC_TERMS;
+            for (int k = 0; k < ORC_TERMS; ++k) gr[k] += tt[k];
           }
           if (several && ab) {
             alt_grad_row* gr = &ab->g[ab->ng++];
             gr->pix = pix;
             gr->outcome = oc;
             gr->lid = lid;
-            memcpy(gr->g, t18, sizeof t18);
+            memcpy(gr->g, tt, sizeof tt);
           }
         }
       }
@@ -855,7 +889,7 @@ static void* render_rows(void* argp) {
 /* Complex-step chain from record gradients to raw-parameter gradients for one Gaussian (bit ch of eflip
  * takes colour channel ch's max(0, .) clamp the other way). */
 static void chain_to_params(const orc_scene* sc, const orc_camera* cam, const orc_opts* o, int64_t g,
-                            const double* grec, const double* gabs, orc_bwd* b, int eflip) {
+                            const double* grec, const double* gabs, const double* gerr, orc_bwd* b, int eflip) {
   int K = sh_count(sc->sh_degree);
   int np = 3 + 3 + 4 + 1 + 3 * K;
   double h = 1e-30;
@@ -868,32 +902,43 @@ static void chain_to_params(const orc_scene* sc, const orc_camera* cam, const or
     logit = sc->opacity_logits[g];
     double* dst;
     double* sdst;
-    if (j < 3) { p[j] += I * h; dst = &b->d_means[3 * g + j]; sdst = b->s_means ? &b->s_means[3 * g + j] : NULL; }
-    else if (j < 6) {
+    double* pdst;
+    int64_t at;
+    if (j < 3) {
+      p[j] += I * h;
+      at = 3 * g + j;
+      dst = &b->d_means[at]; sdst = b->s_means ? &b->s_means[at] : NULL; pdst = b->p_means ? &b->p_means[at] : NULL;
+    } else if (j < 6) {
       s[j - 3] += I * h;
-      dst = &b->d_log_scales[3 * g + j - 3];
-      sdst = b->s_log_scales ? &b->s_log_scales[3 * g + j - 3] : NULL;
+      at = 3 * g + j - 3;
+      dst = &b->d_log_scales[at];
+      sdst = b->s_log_scales ? &b->s_log_scales[at] : NULL;
+      pdst = b->p_log_scales ? &b->p_log_scales[at] : NULL;
     } else if (j < 10) {
       q[j - 6] += I * h;
-      dst = &b->d_quats[4 * g + j - 6];
-      sdst = b->s_quats ? &b->s_quats[4 * g + j - 6] : NULL;
+      at = 4 * g + j - 6;
+      dst = &b->d_quats[at]; sdst = b->s_quats ? &b->s_quats[at] : NULL; pdst = b->p_quats ? &b->p_quats[at] : NULL;
     } else if (j == 10) {
       logit += I * h;
       dst = &b->d_opacity_logits[g];
       sdst = b->s_opacity_logits ? &b->s_opacity_logits[g] : NULL;
+      pdst = b->p_opacity_logits ? &b->p_opacity_logits[g] : NULL;
     } else {
       sh[j - 11] += I * h;
-      dst = &b->d_sh[(int64_t)3 * K * g + j - 11];
-      sdst = b->s_sh ? &b->s_sh[(int64_t)3 * K * g + j - 11] : NULL;
+      at = (int64_t)3 * K * g + j - 11;
+      dst = &b->d_sh[at]; sdst = b->s_sh ? &b->s_sh[at] : NULL; pdst = b->p_sh ? &b->p_sh[at] : NULL;
     }
     if (!project_c(cam, o->dilation, K, p, s, q, logit, sh, rec, &lam, er, NULL, eflip)) continue;
-    double acc = 0, sacc = 0;
+    double acc = 0, sacc = 0, pacc = 0;
     for (int r = 0; r < 9; ++r) {
-      acc += grec[r] * cimag(rec[r]) / h;
-      if (gabs) sacc += gabs[r] * fabs(cimag(rec[r]) / h);
+      const double jr = cimag(rec[r]) / h;
+      acc += grec[r] * jr;
+      if (gabs) sacc += gabs[r] * fabs(jr);
+      if (gerr) pacc += gerr[r] * fabs(jr);
     }
     *dst = acc;
     if (sdst) *sdst = sacc;
+    if (pdst) *pdst = pacc;
   }
 }
 
@@ -929,7 +974,7 @@ int orc_project_jacobian(const orc_scene* sc, const orc_camera* cam, const orc_o
     double e[9] = {0};
     e[r] = 1.0;
     memset(dm, 0, sizeof dm); memset(ds, 0, sizeof ds); memset(dq, 0, sizeof dq); dl[0] = 0; memset(dh, 0, sizeof dh);
-    chain_to_params(sc, cam, o, g, e, NULL, &b, eflip);
+    chain_to_params(sc, cam, o, g, e, NULL, NULL, &b, eflip);
     double* row = jac + (size_t)r * np;
     for (int t = 0; t < 3; ++t) row[t] = dm[t];
     for (int t = 0; t < 3; ++t) row[3 + t] = ds[t];
@@ -1068,7 +1113,7 @@ int orc_render(const orc_scene* sc, const orc_camera* cam, const orc_model* mode
   job.px_capped = capped; job.fwd = fwd; job.bwd = bwd; job.nthreads = nthreads;
   job.want_alt = alt != NULL;
   if (alt) job.alt = (alt_buf*)calloc((size_t)nthreads, sizeof(alt_buf));
-  if (bwd) job.grad_rec = (double*)calloc((size_t)nthreads * (size_t)nloc * 18 + 1, sizeof(double));
+  if (bwd) job.grad_rec = (double*)calloc((size_t)nthreads * (size_t)nloc * ORC_TERMS + 1, sizeof(double));
   pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * nthreads);
   worker_arg* wa = (worker_arg*)malloc(sizeof(worker_arg) * nthreads);
   for (int t = 0; t < nthreads; ++t) {
@@ -1088,19 +1133,20 @@ int orc_render(const orc_scene* sc, const orc_camera* cam, const orc_model* mode
     memset(bwd->d_opacity_logits, 0, sizeof(double) * (size_t)n);
     memset(bwd->d_sh, 0, sizeof(double) * 3 * (size_t)K * (size_t)n);
     if (bwd->fragile_gauss) memset(bwd->fragile_gauss, 0, (size_t)n);
-    double* sarr[5] = {bwd->s_means, bwd->s_log_scales, bwd->s_quats, bwd->s_opacity_logits, bwd->s_sh};
+    double* sarr[10] = {bwd->s_means, bwd->s_log_scales, bwd->s_quats, bwd->s_opacity_logits, bwd->s_sh,
+                        bwd->p_means, bwd->p_log_scales, bwd->p_quats, bwd->p_opacity_logits, bwd->p_sh};
     size_t swid[5] = {3, 3, 4, 1, 3 * (size_t)K};
-    for (int k = 0; k < 5; ++k)
-      if (sarr[k]) memset(sarr[k], 0, sizeof(double) * swid[k] * (size_t)n);
-    grec_sum = (double*)calloc((size_t)nloc * 18 + 1, sizeof(double));
+    for (int k = 0; k < 10; ++k)
+      if (sarr[k]) memset(sarr[k], 0, sizeof(double) * swid[k % 5] * (size_t)n);
+    grec_sum = (double*)calloc((size_t)nloc * ORC_TERMS + 1, sizeof(double));
     for (int64_t l = 0; l < nloc; ++l) {
-      double* gr = grec_sum + (size_t)l * 18;
+      double* gr = grec_sum + (size_t)l * ORC_TERMS;
       for (int t = 0; t < nthreads; ++t)
-        for (int r = 0; r < 18; ++r) gr[r] += job.grad_rec[((size_t)t * nloc + l) * 18 + r];
+        for (int r = 0; r < ORC_TERMS; ++r) gr[r] += job.grad_rec[((size_t)t * nloc + l) * ORC_TERMS + r];
       int nz = 0;
-      for (int r = 0; r < 18; ++r) nz |= gr[r] != 0;
+      for (int r = 0; r < ORC_TERMS; ++r) nz |= gr[r] != 0;
       if (!nz) continue;
-      chain_to_params(sc, cam, o, gid[l], gr, gr + 9, bwd, 0);
+      chain_to_params(sc, cam, o, gid[l], gr, gr + 9, gr + 18, bwd, 0);
       if (bwd->fragile_gauss)
         for (int ch = 0; ch < 3; ++ch)
           if (fabs(all[l].e_real[ch]) <= all[l].e_band[ch]) bwd->fragile_gauss[gid[l]] |= (uint8_t)(1 << ch);
@@ -1120,7 +1166,7 @@ int orc_render(const orc_scene* sc, const orc_camera* cam, const orc_model* mode
     alt->grad_pix = (int64_t*)malloc(sizeof(int64_t) * (ng + 1));
     alt->grad_outcome = (int32_t*)malloc(sizeof(int32_t) * (ng + 1));
     alt->grad_ju = (int32_t*)malloc(sizeof(int32_t) * (ng + 1));
-    alt->grad_rec = (double*)malloc(sizeof(double) * 18 * (ng + 1));
+    alt->grad_rec = (double*)malloc(sizeof(double) * ORC_TERMS * (ng + 1));
     int32_t* ju_of = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nloc + 1));
     for (int64_t l = 0; l < nloc; ++l) ju_of[l] = -1;
     alt->jac_gid = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nloc + 1));
@@ -1140,7 +1186,7 @@ int orc_render(const orc_scene* sc, const orc_camera* cam, const orc_model* mode
         alt->grad_pix[kg] = b->g[i].pix;
         alt->grad_outcome[kg] = b->g[i].outcome;
         alt->grad_ju[kg] = ju_of[lid];
-        memcpy(&alt->grad_rec[18 * kg], b->g[i].g, sizeof(double) * 18);
+        memcpy(&alt->grad_rec[ORC_TERMS * kg], b->g[i].g, sizeof(double) * ORC_TERMS);
       }
       free(b->f);
       free(b->g);
@@ -1170,7 +1216,7 @@ int orc_render(const orc_scene* sc, const orc_camera* cam, const orc_model* mode
         if (!((mask >> ch) & 1)) continue;
         for (int t = 0; t < np; ++t)
           alt->eflip_dJ[((size_t)ne * 3 + ch) * np + t] = J1[(6 + ch) * np + t] - J0[(6 + ch) * np + t];
-        alt->eflip_gE[3 * ne + ch] = grec_sum[(size_t)l * 18 + 6 + ch];
+        alt->eflip_gE[3 * ne + ch] = grec_sum[(size_t)l * ORC_TERMS + 6 + ch];
       }
       free(J0);
       free(J1);
@@ -1199,7 +1245,7 @@ int orc_composite_list(int32_t kind, double param, double t_eps, int32_t max_spl
   double* pb = (double*)malloc(sizeof(double) * cap);
   for (int i = 0; i < n; ++i) pbar[i] = 0;
   comp_result r;
-  composite(kind, param, &co, bg, n, alpha, NULL, E, NULL, idx, a, cl, pb, &r);
+  composite(kind, param, &co, bg, n, alpha, NULL, E, NULL, idx, a, cl, pb, NULL, &r);
   for (int j = 0; j < r.m; ++j) pbar[idx[j]] = pb[j];
   for (int ch = 0; ch < 3; ++ch) out4[ch] = r.color[ch];
   out4[3] = r.T_end;
@@ -1246,7 +1292,7 @@ int32_t orc_composite_outcomes(int32_t kind, double param, double alpha_min, dou
     memcpy(path, paths[n_stack], (size_t)plen);
     decider d = {path, plen, 0};
     comp_result r;
-    composite(kind, param, &co, bg, n, raw, band, E, band ? &d : NULL, idx, a, cl, pb, &r);
+    composite(kind, param, &co, bg, n, raw, band, E, band ? &d : NULL, idx, a, cl, pb, NULL, &r);
     if (count >= max_out || count >= ORC_MAX_OUTCOMES) { over = 1; break; }
     m_out[count] = r.m;
     for (int ch = 0; ch < 3; ++ch) out4[4 * count + ch] = r.color[ch];
