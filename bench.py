@@ -67,6 +67,7 @@ def parse():
     p.add_argument("--no-batched", action="store_true", help="skip the batched multi-view measurement")
     p.add_argument("--batched-gaussians", type=int, default=3_000_000)
     p.add_argument("--batched-views", type=int, default=32)
+    p.add_argument("--batched-reps", type=int, default=20)
     p.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     p.add_argument("--no-training", action="store_true", help="skip the training-step measurement")
     p.add_argument("--training-steps", type=int, default=300)
@@ -76,6 +77,10 @@ def parse():
                    help="second arrival rate, between the capacities of the two forms")
     p.add_argument("--serving-workers", type=int, default=4)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-peaks", action="store_true", help="skip the FP32 / MUFU throughput microbenchmarks")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the per-model lines of the tiny and the 1M / 1297x840 configurations")
+    p.add_argument("--config-reps", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-crop", type=int, default=0, help="oracle crop side (0: sized automatically)")
     return p.parse_args()
@@ -97,9 +102,46 @@ def workload(args, rank):
     return scene, cam
 
 
+class _NVML:
+    """Read-only NVML queries through ctypes (SM clock, its maximum, power, clock-event reasons)."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, index):
+        import ctypes as C
+        self.C = C
+        lib = None
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                lib = C.CDLL(name)
+                break
+            except OSError:
+                continue
+        if lib is None or lib.nvmlInit_v2() != 0:
+            raise OSError("NVML unavailable")
+        self.lib = lib
+        self.h = C.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(index), C.byref(self.h)) != 0:
+            raise OSError("NVML: no device handle")
+        self.events = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        C = self.C
+        sm, smax, mw, reasons = C.c_uint(), C.c_uint(), C.c_uint(), C.c_ulonglong()
+        ok = (self.lib.nvmlDeviceGetClockInfo(self.h, 1, C.byref(sm)) == 0 and
+              self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, C.byref(smax)) == 0)
+        if not ok:
+            return None
+        self.lib.nvmlDeviceGetPowerUsage(self.h, C.byref(mw))
+        self.events(self.h, C.byref(reasons))
+        return float(sm.value), float(smax.value), mw.value / 1000.0, int(reasons.value)
+
+
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 100 ms; only the samples taken inside the timed
-    region (between mark_start and mark_end, by their timestamps) are summarised."""
+    """SM clocks and clock-event (throttle) reasons sampled during the timed region: through NVML every
+    5 ms when the library loads (so that even a region of tens of milliseconds holds several samples),
+    else nvidia-smi every 100 ms. Only the samples taken between mark_start and mark_end are summarised."""
 
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -108,7 +150,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.nvml = None
         self.lines = []
+        self.samples = []
         self.t0 = self.t1 = None
 
     def mark_start(self):
@@ -118,6 +162,15 @@ class ClockSampler:
         self.t1 = time.time()
 
     def start(self):
+        try:
+            self.nvml = _NVML(self.index)
+        except (OSError, AttributeError):
+            self.nvml = None
+        if self.nvml is not None:
+            self.running = True
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -131,7 +184,32 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append((time.time(), line.strip()))
 
+    def _poll(self):
+        while self.running:
+            smp = self.nvml.sample()
+            if smp is not None:
+                self.samples.append((time.time(), smp))
+            time.sleep(0.005)
+
+    def _summary_nvml(self):
+        self.running = False
+        self.thread.join(timeout=2)
+        t0 = self.t0 if self.t0 is not None else -1e30
+        t1 = self.t1 if self.t1 is not None else 1e30
+        sm, power, reasons, smax = [], [], set(), None
+        for stamp, (mhz, mx, w, bits) in self.samples:
+            if t0 <= stamp <= t1:
+                sm.append(mhz)
+                power.append(w)
+                smax = mx
+                reasons |= {name for bit, name in _NVML.REASONS.items() if bits & bit}
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_median": statistics.median(power) if power else None,
+                "window": "NVML samples every 5 ms taken during the timed region"}
+
     def stop(self):
+        if getattr(self, "nvml", None) is not None:
+            return self._summary_nvml()
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -335,13 +413,14 @@ def run_ours(args):
         per_model[m]["overdraw_reduction_vs_exp"] = round(per_model["exp"]["overdraw_mean"] /
                                                           max(per_model[m]["overdraw_mean"], 1e-9), 3)
 
-    # roofline of the dominant stage
+    # roofline of the dominant stage, against peaks measured on this GPU now
     stage_ms = {k: v[0] / K for k, v in stage.items()}
     if stage_direct is not stage:
         for k in ("project", "depth_sort", "scan_emit", "tile_sort", "tile_ranges", "composite_fwd"):
             stage_ms[k] = stage_direct[k][0] / 2
     dominant = max(stage_ms, key=stage_ms.get)
-    roof = roofline(dominant, stage_ms, frames, ods, args.gaussians, measured_peaks(), clk, opts)
+    pipe_peaks = measure_pipe_peaks(r, local) if not args.no_peaks else {}
+    roof = roofline(dominant, stage_ms, frames, ods, args.gaussians, measured_peaks(), clk, opts, pipe_peaks)
 
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world, "steps": K,
@@ -364,12 +443,14 @@ def run_ours(args):
         "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
         "stage_ms_source": stage_source,
         "gpu_launches": int(launches), "gpu_launches_per_step": round(launches / K, 1),
-        "roofline": roof, "clocks": clk,
+        "roofline": roof, "clocks": clk, "pipe_peaks": pipe_peaks,
     }
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, rs, streams, owner, scene, cam, opts, dl, dev, world)
     for x in rs[1:]:
         x.close()
+    if not args.no_configs and world == 1:
+        line["configs"] = run_configs(args, r, dev, local)
     if world == 1 and not (args.no_batched and args.no_serving and args.no_training):
         del params, frames, grads
     if not args.no_batched and world == 1:
@@ -518,36 +599,85 @@ def measured_traffic(kernel, opts):
     return float(np.mean([per[m] for m in MODELS])), rec.get("command", "")
 
 
-def roofline(dominant, stage_ms, frames, ods, n_gauss, peaks, clk, opts=None):
+# FP32 FLOPs per composited pixel-splat as the method's algorithmic work counts them (an FMA counts 2):
+# the forward evaluates d = p - mu, the quadratic form, alpha and the model's step and adds E pbar (about
+# 22); the replay does that again and forms dL/dalpha, the six moments and dL/dE (about 2.5 times as
+# much: 55). Each costs one ex2 (alpha). Entries walked but not composited (alpha < alpha_min) are the
+# rasterizer's overhead, not the method's work: the build's own count (FLOP_TEST per walked entry, above)
+# is reported beside it.
+FLOP_METHOD = {"composite_fwd": 22, "composite_bwd": 55}
+
+
+def measure_pipe_peaks(r, index):
+    """FP32 (fma.rn.f32 and the packed fma.rn.f32x2) and MUFU (ex2.approx) throughput of this GPU, measured
+    now by ngs_measure_peak (about 1 s each), with the SM clock sampled during each."""
+    from paper_2603_02887_gb300 import _abi
+
+    out = {"how": "ngs_measure_peak: 8 independent chains per thread, all SMs at full occupancy, best of 4 "
+                  "CUDA-event-timed launches over about 1 s"}
+    for name, kind in (("ffma", _abi.NGS_PEAK_FFMA), ("ffma2", _abi.NGS_PEAK_FFMA2), ("ex2", _abi.NGS_PEAK_EX2)):
+        clk = ClockSampler(index)
+        clk.start()
+        time.sleep(0.05)
+        clk.mark_start()
+        rate = r.measure_peak(kind, 1.0)
+        clk.mark_end()
+        c = clk.stop()
+        out[name] = {"value": round(rate / 1e12, 3), "unit": "T ex2/s" if name == "ex2" else "TFLOP/s",
+                     "sm_mhz": c.get("sm_mhz"), "reasons": c.get("reasons"), "clock_samples": c.get("samples")}
+    return out
+
+
+def roofline(dominant, stage_ms, frames, ods, n_gauss, peaks, clk, opts=None, pipe=None):
     """Roofline of the dominant stage, per launch (one launch per model per step).
 
-    Compositing stages are bound by FP32 issue: achieved = algorithmic FLOPs / CUDA-event time against
-    152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (maximum SM clock). Streaming stages are HBM bound:
-    algorithmic bytes / time against the measured copy bandwidth."""
+    Compositing stages are bound by FP32 issue and by the MUFU ex2 of each alpha: achieved = the method's
+    FLOPs (FLOP_METHOD per composited pixel-splat) / CUDA-event time, against the larger of the measured
+    fma.rn.f32 and fma.rn.f32x2 throughput (frac_fp32), and composited pixel-splats / time against the
+    measured ex2 throughput (frac_mufu). Without measured peaks: 152 SMs x 128 lanes x 2 x 2070 MHz.
+    Streaming stages are HBM bound: algorithmic bytes / time against the measured copy bandwidth."""
     import torch
 
     sm_count = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     if dominant in ("composite_fwd", "composite_bwd"):
-        flops = 0.0
+        build_flops, comp_total = 0.0, 0.0
         for m, f in frames.items():
             walked, comp = _walked_and_composited(f, ods[m])
             kind = "exp" if m == "exp" else "quad"
             per = FLOP_FWD[kind] if dominant == "composite_fwd" else FLOP_BWD[kind]
-            flops += FLOP_TEST * walked + per * comp
-        flops /= len(frames)  # per launch
+            build_flops += FLOP_TEST * walked + per * comp
+            comp_total += comp
+        build_flops /= len(frames)  # per launch
+        comp = comp_total / len(frames)
+        flops = FLOP_METHOD[dominant] * comp
         t = stage_ms[dominant] / len(frames) * 1e-3
         achieved = flops / t / 1e12
-        peak = sm_count * 128 * 2 * 2070e6 / 1e12
+        if pipe and "ffma" in pipe:
+            peak = max(pipe["ffma"]["value"], pipe["ffma2"]["value"])
+            source = ("measured: max of fma.rn.f32 and fma.rn.f32x2 throughput (pipe_peaks), "
+                      f"{pipe['ffma']['value']} / {pipe['ffma2']['value']} TFLOP/s")
+        else:
+            peak = sm_count * 128 * 2 * 2070e6 / 1e12
+            source = f"{sm_count} SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts and max clock)"
         traffic, note = measured_traffic(dominant, opts) if opts else (None, "launch options unknown")
         out = {"bound": "alu", "kernel": dominant, "achieved": round(achieved, 3), "peak": round(peak, 2),
-               "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+               "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "frac_fp32": round(achieved / peak, 4),
                "traffic": None if traffic is None else round(traffic),
                "traffic_source": note if traffic is None else "ncu dram__bytes_read.sum + dram__bytes_write.sum per "
                                                                 "launch, mean over the models: " + note,
-               "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts and max clock)",
-               "flops_per_launch": flops}
-        if clk.get("sm_mhz"):
-            out["frac_at_observed_clock"] = round(achieved / (peak * clk["sm_mhz"] / 2070.0), 4)
+               "peak_source": source,
+               "flops_per_launch": flops,
+               "flop_count": f"{FLOP_METHOD[dominant]} FLOP per composited pixel-splat (sum of overdraw) "
+                             f"{comp:.4g} per launch",
+               "achieved_build_count": round(build_flops / t / 1e12, 3),
+               "build_count": "11 FLOP per walked list entry + 12/20 (fwd) or 45/50 (replay) per composited splat"}
+        if pipe and "ex2" in pipe:
+            ex2_rate = comp / t / 1e12
+            out.update(ex2_achieved=round(ex2_rate, 4), ex2_peak=pipe["ex2"]["value"],
+                       frac_mufu=round(ex2_rate / pipe["ex2"]["value"], 4),
+                       mufu_count="one ex2 per composited pixel-splat")
+        if clk.get("sm_mhz") and pipe and pipe.get("ffma", {}).get("sm_mhz"):
+            out["clock_ratio_kernel_vs_peak"] = round(clk["sm_mhz"] / pipe["ffma"]["sm_mhz"], 4)
         return out
     pairs = float(np.mean([f.view()["n_pairs"] for f in frames.values()]))
     units = pairs if dominant in ("scan_emit", "tile_sort", "tile_ranges") else n_gauss
@@ -603,6 +733,69 @@ def launch_options(args, r, params, cams, reps=2, use_options=True):
     return out, src if len(given) == len(MODELS) else f"{src} for {sorted(given)}, else {tuned}"
 
 
+def run_configs(args, r, dev, index):
+    """Per-model forward and forward + backward Mpix/s of the other two single-view configurations:
+    tiny (1,000 Gaussians, SH 0, 128x128, L2 loss against a target rendered from a second seed) and
+    differentiation (1M clustered Gaussians, SH 3, 1297x840, L1 loss against a target rendered from
+    N(0, 0.01)-perturbed parameters). Median over --config-reps calls, L2 flushed before each; the launch
+    options are the single view's (TUNED_OPTIONS)."""
+    import torch
+
+    from paper_2603_02887_gb300 import synth
+    from paper_2603_02887_gb300.render import PARAM_KEYS
+
+    opts = parse_options(args.options)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {}
+    specs = (("tiny", lambda: synth.tiny_scene(0), lambda: synth.tiny_scene(1), synth.tiny_camera(), "l2"),
+             ("differentiation", lambda: synth.clustered_scene(1_000_000, seed=0, sh_degree=3),
+              None, synth.outside_camera(1297, 840), "l1"))
+    for name, make, make_target, cam, loss in specs:
+        scene = make()
+        params = {k: torch.from_numpy(np.ascontiguousarray(scene[k])).to(dev) for k in PARAM_KEYS}
+        tsc = make_target() if make_target else synth.perturbed(scene, seed=1)
+        tparams = {k: torch.from_numpy(np.ascontiguousarray(tsc[k])).to(dev) for k in PARAM_KEYS}
+        del scene, tsc
+        H, W = cam["height"], cam["width"]
+        res = {"gaussians": int(params["means"].shape[0]), "width": W, "height": H, "loss": loss,
+               "reps": args.config_reps, "l2": "flushed before every timed call (256 MB write)"}
+        clk = ClockSampler(index)
+        clk.start()
+        time.sleep(0.05)
+        clk.mark_start()
+        for m in MODELS:
+            tgt, _, ft = r.render(tparams, cam, m, opts[m])
+            img, od, f = r.render(params, cam, m, opts[m])
+            dl = (2.0 * (img - tgt) if loss == "l2" else torch.sign(img - tgt)).contiguous()
+            g = r.backward(f, params, dl)
+            r.recycle(ft)
+            tf, tfb = [], []
+            for i in range(args.config_reps + 3):
+                flush.zero_()
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record()
+                r.render(params, cam, m, opts[m], frame=f, image=img, overdraw=od)
+                e[1].record()
+                r.backward(f, params, dl, out=g)
+                e[2].record()
+                torch.cuda.synchronize()
+                if i >= 3:
+                    tf.append(e[0].elapsed_time(e[1]))
+                    tfb.append(e[0].elapsed_time(e[2]))
+            fwd, fb = statistics.median(tf), statistics.median(tfb)
+            res[m] = {"fwd_mpix_s": round(W * H / fwd / 1e3, 1), "fwd_bwd_mpix_s": round(W * H / fb / 1e3, 1),
+                      "fwd_ms": round(fwd, 4), "fwd_bwd_ms": round(fb, 4),
+                      "overdraw_mean": round(float(od.double().mean()), 3)}
+            r.recycle(f)
+        clk.mark_end()
+        res["clocks"] = clk.stop()
+        for m in MODELS[1:]:
+            res[m]["overdraw_reduction_vs_exp"] = round(res["exp"]["overdraw_mean"] / max(res[m]["overdraw_mean"], 1e-9), 3)
+        out[name] = res
+        del params, tparams
+    return out
+
+
 def run_batched(args, r, dev, single_view_models):
     """The batched form: one ngs_render_batch call renders a 3M-Gaussian clustered scene (SH 3) from 32
     cameras of uneven sizes (640x360 .. 1920x1080, poses on a sphere of radius 12 m), forward and forward +
@@ -631,14 +824,20 @@ def run_batched(args, r, dev, single_view_models):
     fviews = [r.frame() for _ in cams]
     vimg = [torch.empty((c["height"], c["width"], 3), device=dev) for c in cams]
     vod = [torch.empty((c["height"], c["width"]), dtype=torch.int32, device=dev) for c in cams]
-    reps = 3
+    reps = args.batched_reps
+    vgrads = [{"d_" + k: torch.empty_like(v) for k, v in params.items()} for _ in cams]
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    time.sleep(0.05)
+    clk.mark_start()
     for m in MODELS:
         img, od, fb = r.render_batch(params, cams, m, opts[m], frame=fb)
         dl = torch.sign(img - 0.5).contiguous()
+        dlv = fb.split(dl)
         g = r.backward(fb, params, dl)
         torch.cuda.synchronize()
-        tf, tfb, ts = [], [], []
-        for _ in range(reps):
+        tf, tfb, ts, tsb = [], [], [], []
+        for i in range(reps + 1):  # the first of each is untimed (graph captures, buffers)
             flush.zero_()
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             e[0].record()
@@ -647,28 +846,45 @@ def run_batched(args, r, dev, single_view_models):
             r.backward(fb, params, dl, out=g)
             e[2].record()
             torch.cuda.synchronize()
-            tf.append(e[0].elapsed_time(e[1]))
-            tfb.append(e[0].elapsed_time(e[2]))
-        for _ in range(3):
+            if i:
+                tf.append(e[0].elapsed_time(e[1]))
+                tfb.append(e[0].elapsed_time(e[2]))
+            # the same views one render (+ backward) call at a time
             flush.zero_()
-            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s0.record()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record()
             for v, c in enumerate(cams):
                 r.render(params, c, m, vopts[m], frame=fviews[v], image=vimg[v], overdraw=vod[v])
-            s1.record()
+            e[1].record()
+            flush.zero_()
+            e[2].record()
+            for v, c in enumerate(cams):
+                r.render(params, c, m, vopts[m], frame=fviews[v], image=vimg[v], overdraw=vod[v])
+                r.backward(fviews[v], params, dlv[v].contiguous(), out=vgrads[v])
+            e[3].record()
             torch.cuda.synchronize()
-            ts.append(s0.elapsed_time(s1))
+            if i:
+                ts.append(e[0].elapsed_time(e[1]))
+                tsb.append(e[2].elapsed_time(e[3]))
         same = all(torch.equal(a, b) for a, b in zip(vimg, fb.split(img)))
-        fwd, fwdbwd, single = min(tf), min(tfb), min(ts)
+        fwd, fwdbwd = statistics.median(tf), statistics.median(tfb)
+        single, single_b = statistics.median(ts), statistics.median(tsb)
         out[m] = {"fwd_mpix_s": round(npix / fwd / 1e3, 1), "fwd_bwd_mpix_s": round(npix / fwdbwd / 1e3, 1),
                   "fwd_ms": round(fwd, 3), "fwd_bwd_ms": round(fwdbwd, 3),
                   "one_view_at_a_time_fwd_ms": round(single, 3),
                   "one_view_at_a_time_fwd_mpix_s": round(npix / single / 1e3, 1),
-                  "batched_speedup_fwd": round(single / fwd, 3), "bit_identical_to_single_views": bool(same),
+                  "one_view_at_a_time_fwd_bwd_ms": round(single_b, 3),
+                  "one_view_at_a_time_fwd_bwd_mpix_s": round(npix / single_b / 1e3, 1),
+                  "batched_speedup_fwd": round(single / fwd, 3),
+                  "batched_speedup_fwd_bwd": round(single_b / fwdbwd, 3),
+                  "bit_identical_to_single_views": bool(same),
                   "pairs": int(fb.view()["n_pairs"]), "overdraw_mean": round(float(od.double().mean()), 3),
                   "launch_options": {k: opts[m][k] for k in ("tile_w", "tile_h", "chunk", "schedule")},
                   "one_view_at_a_time_launch_options": {k: vopts[m][k] for k in ("tile_w", "tile_h", "chunk",
                                                                                   "schedule")}}
+    clk.mark_end()
+    out["clocks"] = clk.stop()
+    out["timing"] = f"median of {reps} calls per form and model, after one untimed call"
     for m in MODELS[1:]:
         out[m]["overdraw_reduction_vs_exp"] = round(out["exp"]["overdraw_mean"] / max(out[m]["overdraw_mean"], 1e-9), 3)
     r.recycle(fb)
@@ -916,10 +1132,16 @@ def cpu_baseline(args, scene, cam, crop=None):
     cores = os.cpu_count() or 1
     crop = crop or args.cpu_crop or 640  # about 10-20 s of oracle work on 16 cores
     secs, px = oracle_sample(scene, cam, crop, cores)
+    crop1 = max(16, crop // 5)  # single-threaded: a smaller crop, about 10 s
+    secs1, px1 = oracle_sample(scene, cam, crop1, 1)
     return {"value": round(px / secs / 1e6, 5), "unit": "Mpix/s", "cores": cores, "kind": "oracle",
             "seconds": round(secs, 2),
             "sample": f"FP64 oracle, render + backward of the 4 models on the centred {crop}x{crop} crop of the same "
-                      f"view ({len(MODELS)} x {crop * crop} px; every call re-projects all {args.gaussians} Gaussians)"}
+                      f"view ({len(MODELS)} x {crop * crop} px; every call re-projects all {args.gaussians} Gaussians)",
+            "single_thread": {"value": round(px1 / secs1 / 1e6, 5), "unit": "Mpix/s", "cores": 1,
+                              "seconds": round(secs1, 2),
+                              "sample": f"the same on the centred {crop1}x{crop1} crop, one thread (the per-call "
+                                        "projection of every Gaussian weighs more on a small crop)"}}
 
 
 def run_reference(args):

@@ -281,6 +281,48 @@ NGS_API void ngs_reset_stage_times(ngs_ctx* ctx);
 /* Total number of kernel launches this context has issued (all stages). */
 NGS_API int64_t ngs_launch_count(const ngs_ctx* ctx);
 
+/* ---- memory planning and checked mode ------------------------------------------------------------- */
+
+/* Device memory that a render of n Gaussians from n_views cameras (and its backward) allocates in a fresh
+ * context and frame, for admission control before the render. A frame keeps its buffers and grows them
+ * by at least a quarter when a later render needs more; a context likewise.
+ *   frame_fixed     the frame's buffers sized by splat records, tiles and pixels: records (48 B per record),
+ *                   tile counts, depth keys and order (ping-pong), scan offsets, tile ranges, the per-pixel
+ *                   replay state (32 B per pixel), the view table, and the persistent schedule's work list;
+ *   frame_pairs     the frame's pair buffers (tile and record index, ping-pong: 16 B per pair) for n_pairs;
+ *   context         the context's scratch for this render: radix histograms of both sorts, scan block sums
+ *                   and the pair-count word;
+ *   backward        the context's per-record gradient scratch of ngs_render_backward (48 B per record);
+ *   total           their sum.
+ * n_pairs is the number of (tile, splat) pairs the pair buffers are sized for: the exact count for a
+ * synchronous render without graphs, else the frame's capacity (count + count / 4 + 1024). Every size is
+ * rounded up as the library's allocations are (to 256 B). Errors: NGS_ERR_INVALID_ARG as ngs_render_batch
+ * for the cameras and options, n < 0 or n_pairs < 0. No device call is made. */
+typedef struct {
+  size_t frame_fixed, frame_pairs, context, backward, total;
+} ngs_workspace;
+NGS_API int ngs_workspace_bytes(int64_t n, const ngs_camera* cams, int32_t n_views, const ngs_options* opt,
+                                int64_t n_pairs, ngs_workspace* out);
+
+/* Device bytes a context and a frame hold now (either may be NULL; its count is then 0). */
+NGS_API int ngs_memory_usage(const ngs_ctx* ctx, const ngs_frame* frame, size_t* ctx_bytes, size_t* frame_bytes);
+
+/* Checked mode (off by default): every render on the context first scans the Gaussian parameters and,
+ * when any is NaN or infinite, returns NGS_ERR_INVALID_ARG naming the array, having launched nothing
+ * else. The fast path does not scan; the scan reads each parameter once and synchronises the host with
+ * the stream (an asynchronous frame's render is then no longer free of host synchronisation). */
+NGS_API int ngs_set_checked(ngs_ctx* ctx, int enable);
+
+/* ---- roofline denominators --------------------------------------------------------------------------
+ * Throughput of the pipes the compositing kernels are bound by, measured on the context's device: eight
+ * independent dependency chains per thread on every SM at full occupancy, timed with CUDA events on
+ * `stream` over about `seconds` (0.01 .. 60) of work; *rate receives the best of four timed launches.
+ * Synchronises the stream. The paper has no counterpart: this is a measurement aid. */
+#define NGS_PEAK_FFMA 0  /* fma.rn.f32: FLOP/s, an FMA counting 2                                        */
+#define NGS_PEAK_FFMA2 1 /* fma.rn.f32x2 (two lanes per instruction): FLOP/s, an FMA counting 2 per lane  */
+#define NGS_PEAK_EX2 2   /* ex2.approx.ftz.f32 (MUFU): results per second                                 */
+NGS_API int ngs_measure_peak(ngs_ctx* ctx, int32_t kind, double seconds, double* rate, void* stream);
+
 /* ---- training step (Sec. 5.1 "Loss", "Optimization", "Densification") -------------------------------- */
 
 /* Image loss L = (1 - lambda) L1 + lambda (1 - SSIM) of `image` against `target` (both device

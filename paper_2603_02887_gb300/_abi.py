@@ -22,6 +22,9 @@ NGS_MODEL_VICINI = 3
 NGS_SCHEDULE_TILES = 0
 NGS_SCHEDULE_PERSISTENT = 1
 NGS_NUM_STAGES = 8
+NGS_PEAK_FFMA = 0
+NGS_PEAK_FFMA2 = 1
+NGS_PEAK_EX2 = 2
 STAGES = ("project", "depth_sort", "scan_emit", "tile_sort", "tile_ranges", "composite_fwd", "composite_bwd",
           "project_bwd")
 
@@ -96,6 +99,11 @@ class ServerStats(C.Structure):
                 ("now_s", C.c_double)]
 
 
+class Workspace(C.Structure):
+    _fields_ = [("frame_fixed", C.c_size_t), ("frame_pairs", C.c_size_t), ("context", C.c_size_t),
+                ("backward", C.c_size_t), ("total", C.c_size_t)]
+
+
 #: every function declared in include/ngs.h, with its ctypes signature
 SIGNATURES = {
     "ngs_default_options": (None, [C.POINTER(Options)]),
@@ -125,6 +133,11 @@ SIGNATURES = {
     "ngs_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
     "ngs_reset_stage_times": (None, [C.c_void_p]),
     "ngs_launch_count": (C.c_int64, [C.c_void_p]),
+    "ngs_workspace_bytes": (C.c_int, [C.c_int64, C.POINTER(Camera), C.c_int32, C.POINTER(Options), C.c_int64,
+                                      C.POINTER(Workspace)]),
+    "ngs_memory_usage": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    "ngs_set_checked": (C.c_int, [C.c_void_p, C.c_int]),
+    "ngs_measure_peak": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(C.c_double), C.c_void_p]),
     "ngs_loss_l1_ssim": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_float, C.c_void_p,
                                    C.POINTER(C.c_double), C.c_void_p]),
     "ngs_adam_step": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.POINTER(Grads), C.POINTER(Grads), C.POINTER(Grads),

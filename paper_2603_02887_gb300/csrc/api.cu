@@ -17,10 +17,15 @@ int fail(ngs_ctx* ctx, int code, const std::string& msg) {  // ctx may be null
   return code;
 }
 
+size_t grown_size(size_t cap, size_t bytes) {
+  if (cap && bytes <= cap) return cap;
+  const size_t nb = std::max(bytes, cap + cap / 4);
+  return (std::max<size_t>(nb, 256) + 255) & ~(size_t)255;
+}
+
 int ensure(ngs_ctx* ctx, DevBuf& b, size_t bytes) {
   if (bytes <= b.cap && b.p) return NGS_OK;
-  size_t nb = std::max(bytes, b.cap + b.cap / 4);
-  nb = (std::max<size_t>(nb, 256) + 255) & ~(size_t)255;
+  const size_t nb = grown_size(b.p ? b.cap : 0, bytes);
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.cap = 0;
@@ -197,6 +202,36 @@ static void camera_params(const ngs_camera* cam, CamParams& cp) {
   cp.H = cam->height;
 }
 
+// Bytes of every device buffer a render (and its backward) asks for: the one place these sizes are
+// written, used by the render itself and by ngs_workspace_bytes. cap: the pair buffers' item count.
+struct BufferPlan {
+  size_t rec, tile_count, keys, vals, offsets, ranges, state, views, work, sched;  // frame, per render
+  size_t pair_tile, pair_val;                                                       // frame, per pair
+  size_t scan_tmp, total, hist1, hist2;                                             // context
+  size_t grad2d;                                                                    // context, backward
+};
+
+static BufferPlan plan_buffers(uint64_t R, uint32_t n, uint32_t n_views, uint64_t ntiles, uint64_t pix_total,
+                               int schedule, uint64_t cap) {
+  BufferPlan b;
+  const size_t r1 = (size_t)std::max<uint64_t>(R, 1);
+  b.rec = sizeof(float4) * 3 * r1;
+  b.tile_count = b.keys = b.vals = sizeof(uint32_t) * r1;
+  b.offsets = sizeof(uint32_t) * ((size_t)R + 1);
+  b.ranges = sizeof(uint2) * (size_t)ntiles;
+  b.state = sizeof(float4) * 2 * (size_t)pix_total;
+  b.views = sizeof(ViewParams) * (size_t)n_views;
+  b.work = schedule == NGS_SCHEDULE_PERSISTENT ? sizeof(uint32_t) * (size_t)std::max<uint64_t>(ntiles, 1) : 0;
+  b.sched = schedule == NGS_SCHEDULE_PERSISTENT ? sizeof(uint32_t) * kSchedWords : 0;
+  b.pair_tile = b.pair_val = sizeof(uint32_t) * (size_t)std::max<uint64_t>(cap, 1);
+  b.scan_tmp = sizeof(uint64_t) * scan_tmp_words((uint32_t)R);
+  b.total = 2 * sizeof(uint64_t);
+  b.hist1 = sizeof(uint32_t) * radix_hist_words(std::max(n, 1u), std::max(n_views, 1u));
+  b.hist2 = sizeof(uint32_t) * radix_hist_words((uint32_t)std::max<uint64_t>(cap, 1), 1);
+  b.grad2d = sizeof(float4) * 3 * r1;
+  return b;
+}
+
 // Stage the view table in the frame's pinned buffer (the copy to the device is a launch of phase 1). The
 // staging is rewritten only after the previous copy from it has completed.
 static int stage_views(ngs_ctx* ctx, ngs_frame* f) {
@@ -223,8 +258,42 @@ static int stage_views(ngs_ctx* ctx, ngs_frame* f) {
     f->d_h_views = static_cast<const uint32_t*>(dev_alias);
     f->h_views_cap = f->view_host.size();
   }
-  NGS_TRY(ensure(ctx, f->views, bytes));
+  NGS_TRY(ensure(ctx, f->views, plan_buffers(0, 0, (uint32_t)f->view_host.size(), 0, 0, 0, 0).views));
   memcpy(f->h_views, f->view_host.data(), bytes);
+  return NGS_OK;
+}
+
+// Checked mode: every parameter of the Gaussians finite, else NGS_ERR_INVALID_ARG naming the array.
+__global__ void nonfinite_kernel(const float* __restrict__ a, size_t count, uint32_t bit, uint32_t* flag) {
+  pdl_wait();
+  bool bad = false;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(a[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, bit);
+}
+
+static int check_finite(ngs_ctx* ctx, const ngs_gaussians* g, cudaStream_t s) {
+  if (g->n == 0) return NGS_OK;
+  NGS_TRY(ensure(ctx, ctx->check_word, sizeof(uint64_t)));
+  cudaError_t e = cudaMemsetAsync(ctx->check_word.p, 0, sizeof(uint64_t), s);
+  if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("checked mode: ") + cudaGetErrorString(e));
+  const size_t n = (size_t)g->n, K3 = 3 * (size_t)(g->sh_degree + 1) * (size_t)(g->sh_degree + 1);
+  const float* arrays[5] = {g->means, g->log_scales, g->quats, g->opacity_logits, g->sh};
+  const size_t counts[5] = {3 * n, 3 * n, 4 * n, n, K3 * n};
+  for (int k = 0; k < 5; ++k) {
+    const unsigned blocks = (unsigned)std::min<size_t>((counts[k] + 255) / 256, (size_t)ctx->num_sms * 8);
+    launch_pdl(nonfinite_kernel, blocks, 256, 0, s, arrays[k], counts[k], 1u << k, ctx->check_word.as<uint32_t>());
+  }
+  publish_words(ctx, ctx->check_word.as<uint64_t>(), 1, kMirrorChecked, s);
+  ctx->launches += 6;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("checked mode: ") + cudaGetErrorString(e));
+  const uint64_t bits = static_cast<volatile uint64_t*>(ctx->h_total)[kMirrorChecked];
+  static const char* names[5] = {"means", "log_scales", "quats", "opacity_logits", "sh"};
+  for (int k = 0; k < 5; ++k)
+    if (bits & (1u << k))
+      return fail(ctx, NGS_ERR_INVALID_ARG, std::string("checked mode: non-finite value in ") + names[k]);
   return NGS_OK;
 }
 
@@ -500,19 +569,22 @@ int ngs::render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, co
   pl.overdraw = overdraws ? overdraws[0] : nullptr;
   const uint32_t R = pl.R;
 
-  // phase 1 buffers
-  NGS_TRY(ensure(ctx, f->rec, sizeof(float4) * 3 * (size_t)std::max(R, 1u)));
-  NGS_TRY(ensure(ctx, f->tile_count, sizeof(uint32_t) * (size_t)std::max(R, 1u)));
+  if (ctx->checked) NGS_TRY(check_finite(ctx, g, s));
+
+  // phase 1 buffers (sizes shared with ngs_workspace_bytes)
+  const BufferPlan bp = plan_buffers(R, pl.n, (uint32_t)n_views, pl.ntiles, pix_total, rp.schedule, 0);
+  NGS_TRY(ensure(ctx, f->rec, bp.rec));
+  NGS_TRY(ensure(ctx, f->tile_count, bp.tile_count));
   for (int k = 0; k < 2; ++k) {
-    NGS_TRY(ensure(ctx, f->gkeys[k], sizeof(uint32_t) * (size_t)std::max(R, 1u)));
-    NGS_TRY(ensure(ctx, f->gvals[k], sizeof(uint32_t) * (size_t)std::max(R, 1u)));
+    NGS_TRY(ensure(ctx, f->gkeys[k], bp.keys));
+    NGS_TRY(ensure(ctx, f->gvals[k], bp.vals));
   }
-  NGS_TRY(ensure(ctx, f->offsets, sizeof(uint32_t) * ((size_t)R + 1)));
-  NGS_TRY(ensure(ctx, f->ranges, sizeof(uint2) * (size_t)pl.ntiles));
-  NGS_TRY(ensure(ctx, f->state, sizeof(float4) * 2 * (size_t)pix_total));
-  NGS_TRY(ensure(ctx, ctx->scan_tmp, sizeof(uint64_t) * scan_tmp_words(R)));
+  NGS_TRY(ensure(ctx, f->offsets, bp.offsets));
+  NGS_TRY(ensure(ctx, f->ranges, bp.ranges));
+  NGS_TRY(ensure(ctx, f->state, bp.state));
+  NGS_TRY(ensure(ctx, ctx->scan_tmp, bp.scan_tmp));
   if (!ctx->total.p) {
-    NGS_TRY(ensure(ctx, ctx->total, 2 * sizeof(uint64_t)));
+    NGS_TRY(ensure(ctx, ctx->total, bp.total));
     const cudaError_t ze = cudaMemsetAsync(ctx->total.p, 0, 2 * sizeof(uint64_t), s);
     if (ze != cudaSuccess) {
       free_buf(ctx->total);  // zeroed on the next render's first use again
@@ -520,10 +592,10 @@ int ngs::render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, co
     }
   }
   rp.check = reinterpret_cast<uint32_t*>(ctx->total.as<uint64_t>() + 1);
-  NGS_TRY(ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(std::max(pl.n, 1u), (uint32_t)n_views)));
+  NGS_TRY(ensure(ctx, ctx->hist, bp.hist1));
   if (rp.schedule == NGS_SCHEDULE_PERSISTENT) {
-    NGS_TRY(ensure(ctx, f->work, sizeof(uint32_t) * (size_t)std::max(pl.ntiles, 1u)));
-    NGS_TRY(ensure(ctx, f->sched, sizeof(uint32_t) * kSchedWords));
+    NGS_TRY(ensure(ctx, f->work, bp.work));
+    NGS_TRY(ensure(ctx, f->sched, bp.sched));
   }
   NGS_TRY(stage_views(ctx, f));
   if (admit) NGS_TRY(admit(admit_user, 0, sizeof(uint32_t) * 4 * (size_t)R));
@@ -577,11 +649,12 @@ int ngs::render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, co
       np_dev = reinterpret_cast<const uint32_t*>(ctx->total.p);
     }
   }
+  const BufferPlan bp2 = plan_buffers(R, pl.n, (uint32_t)n_views, pl.ntiles, pix_total, rp.schedule, cap);
   for (int k = 0; k < 2; ++k) {
-    NGS_TRY(ensure(ctx, f->ptile[k], sizeof(uint32_t) * (size_t)std::max(cap, 1u)));
-    NGS_TRY(ensure(ctx, f->pvals[k], sizeof(uint32_t) * (size_t)std::max(cap, 1u)));
+    NGS_TRY(ensure(ctx, f->ptile[k], bp2.pair_tile));
+    NGS_TRY(ensure(ctx, f->pvals[k], bp2.pair_val));
   }
-  NGS_TRY(ensure(ctx, ctx->hist, sizeof(uint32_t) * radix_hist_words(std::max(cap, 1u), 1)));
+  NGS_TRY(ensure(ctx, ctx->hist, bp2.hist2));
   KeyBuf k2;
   k2.add(rp);
   k2.add(cap);
@@ -662,6 +735,7 @@ NGS_API void ngs_destroy(ngs_ctx* ctx) {
   free_buf(ctx->loss_tmp);
   free_buf(ctx->densify_tmp);
   free_buf(ctx->densify_totals);
+  free_buf(ctx->check_word);
   if (ctx->h_total) cudaFreeHost(ctx->h_total);
   for (auto& p : ctx->pending) {
     cudaEventDestroy(p.a);
@@ -775,7 +849,7 @@ int ngs::backward_frame(ngs_ctx* ctx, const ngs_frame* f, const ngs_gaussians* g
   if (g->n > 0 && (!out->d_means || !out->d_log_scales || !out->d_quats || !out->d_opacity_logits || !out->d_sh))
     return fail(ctx, NGS_ERR_INVALID_ARG, "null gradient array");
   const uint32_t R = f->rp.n_records;
-  NGS_TRY(ensure(ctx, ctx->grad2d, sizeof(float4) * 3 * (size_t)std::max(R, 1u)));
+  NGS_TRY(ensure(ctx, ctx->grad2d, plan_buffers(R, 0, 1, 0, 0, 0, 0).grad2d));
   // the replay adds into the record gradients: a failed clear must not let it add onto stale values
   cudaError_t e = cudaMemsetAsync(ctx->grad2d.p, 0, sizeof(float4) * 3 * (size_t)R, s);
   if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("clearing the record gradients: ") + cudaGetErrorString(e));
@@ -885,5 +959,57 @@ NGS_API void ngs_reset_stage_times(ngs_ctx* ctx) {
 }
 
 NGS_API int64_t ngs_launch_count(const ngs_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+NGS_API int ngs_set_checked(ngs_ctx* ctx, int enable) {
+  if (!ctx) return NGS_ERR_INVALID_ARG;
+  ctx->checked = enable != 0;
+  return NGS_OK;
+}
+
+NGS_API int ngs_workspace_bytes(int64_t n, const ngs_camera* cams, int32_t n_views, const ngs_options* o,
+                                int64_t n_pairs, ngs_workspace* out) {
+  if (!cams || !o || !out || n < 0 || n >= (1ll << 31) || n_pairs < 0 || n_pairs >= (1ll << 31))
+    return NGS_ERR_INVALID_ARG;
+  if (n_views < 1 || n_views > kMaxViews) return NGS_ERR_INVALID_ARG;
+  const bool tile_ok = (o->tile_w == 8 && o->tile_h == 8) || (o->tile_w == 16 && o->tile_h == 16) ||
+                       (o->tile_w == 16 && o->tile_h == 32);
+  if (!tile_ok) return NGS_ERR_INVALID_ARG;
+  uint64_t tiles = 0, pix = 0;
+  for (int v = 0; v < n_views; ++v) {
+    if (check_camera(nullptr, &cams[v]) != NGS_OK) return NGS_ERR_INVALID_ARG;
+    tiles += (uint64_t)((cams[v].width + o->tile_w - 1) / o->tile_w) * ((cams[v].height + o->tile_h - 1) / o->tile_h);
+    pix += (uint64_t)cams[v].width * cams[v].height;
+  }
+  const uint64_t R = (uint64_t)n * (uint64_t)n_views;
+  if (R >= (1ull << 32)) return NGS_ERR_INVALID_ARG;
+  const BufferPlan b = plan_buffers(R, (uint32_t)n, (uint32_t)n_views, tiles, pix, o->schedule, (uint64_t)n_pairs);
+  auto fresh = [](size_t bytes) { return bytes ? grown_size(0, bytes) : (size_t)0; };
+  out->frame_fixed = fresh(b.rec) + fresh(b.tile_count) + 2 * fresh(b.keys) + 2 * fresh(b.vals) + fresh(b.offsets) +
+                     fresh(b.ranges) + fresh(b.state) + fresh(b.views) + fresh(b.work) + fresh(b.sched);
+  out->frame_pairs = 2 * fresh(b.pair_tile) + 2 * fresh(b.pair_val);
+  out->context = fresh(b.scan_tmp) + fresh(b.total) + grown_size(grown_size(0, b.hist1), b.hist2);
+  out->backward = fresh(b.grad2d);
+  out->total = out->frame_fixed + out->frame_pairs + out->context + out->backward;
+  return NGS_OK;
+}
+
+NGS_API int ngs_memory_usage(const ngs_ctx* ctx, const ngs_frame* f, size_t* ctx_bytes, size_t* frame_bytes) {
+  if (ctx_bytes) {
+    *ctx_bytes = 0;
+    if (ctx)
+      for (const DevBuf* b : {&ctx->hist, &ctx->scan_tmp, &ctx->grad2d, &ctx->total, &ctx->flush, &ctx->loss_tmp,
+                              &ctx->densify_tmp, &ctx->densify_totals, &ctx->check_word})
+        *ctx_bytes += b->p ? b->cap : 0;
+  }
+  if (frame_bytes) {
+    *frame_bytes = 0;
+    if (f)
+      for (const DevBuf* b : {&f->rec, &f->tile_count, &f->gkeys[0], &f->gkeys[1], &f->gvals[0], &f->gvals[1],
+                              &f->offsets, &f->ptile[0], &f->ptile[1], &f->pvals[0], &f->pvals[1], &f->ranges,
+                              &f->state, &f->views, &f->keys64, &f->work, &f->sched})
+        *frame_bytes += b->p ? b->cap : 0;
+  }
+  return NGS_OK;
+}
 
 }  // extern "C"

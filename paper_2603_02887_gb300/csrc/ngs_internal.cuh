@@ -235,6 +235,8 @@ struct ngs_ctx {
   ngs::DevBuf flush;     // autotuner: scratch cleared between timed calls to evict L2
   ngs::DevBuf loss_tmp;  // image loss: moment and partial-derivative planes
   ngs::DevBuf densify_tmp, densify_totals;  // split / prune decisions, scans and totals
+  ngs::DevBuf check_word;  // checked mode: one bit per parameter array holding a non-finite value
+  bool checked = false;    // checked mode (ngs_set_checked)
   uint64_t* h_total = nullptr;    // pinned, mapped mirror of the scalars read back (kMirrorWords words),
                                   // written by publish_words
   uint64_t* d_h_total = nullptr;  // its device-side address
@@ -319,10 +321,13 @@ int check_model(ngs_ctx* ctx, const ngs_model* model);
 
 // error / allocation helpers (api.cu)
 int fail(ngs_ctx* ctx, int code, const std::string& msg);
+// Device allocation of `bytes` into b, unless it already holds that much; a new allocation takes
+// grown_size(current capacity, bytes): at least a quarter more than before, rounded up to 256 B.
 int ensure(ngs_ctx* ctx, DevBuf& b, size_t bytes);
+size_t grown_size(size_t cap, size_t bytes);
 // Slots of the context's mapped mirror: the pair count and the device error word of the last render, the
-// loss sums (two doubles), the densified Gaussian count.
-constexpr int kMirrorTotal = 0, kMirrorLoss = 2, kMirrorDensify = 4, kMirrorWords = 8;
+// loss sums (two doubles), the densified Gaussian count, the checked-mode scan's bits.
+constexpr int kMirrorTotal = 0, kMirrorLoss = 2, kMirrorDensify = 4, kMirrorChecked = 5, kMirrorWords = 8;
 // Copy n (<= 32) 64-bit device words into mirror slots [slot, slot + n) with one kernel on stream s.
 void publish_words(ngs_ctx* ctx, const uint64_t* src, int n, int slot, cudaStream_t s);
 void stage_begin(ngs_ctx* ctx, cudaStream_t s, int stage, cudaEvent_t* out);

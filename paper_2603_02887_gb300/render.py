@@ -312,6 +312,36 @@ class Renderer:
     def launch_count(self) -> int:
         return int(self.lib.ngs_launch_count(self.ctx))
 
+    def set_checked(self, enable: bool):
+        """Checked mode: renders refuse NaN / infinite parameters (NGSError naming the array)."""
+        _abi.check(self.lib.ngs_set_checked(self.ctx, int(bool(enable))), self.ctx)
+
+    def memory_usage(self, frame: Frame | None = None) -> tuple:
+        """(context bytes, frame bytes) of device memory held now."""
+        a, b = C.c_size_t(), C.c_size_t()
+        self.lib.ngs_memory_usage(self.ctx, frame.handle if frame is not None else None, C.byref(a), C.byref(b))
+        return int(a.value), int(b.value)
+
+    def measure_peak(self, kind: int, seconds: float = 1.0) -> float:
+        """Measured throughput of a pipe (_abi.NGS_PEAK_*): FLOP/s or ex2 results per second."""
+        rate = C.c_double()
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        _abi.check(self.lib.ngs_measure_peak(self.ctx, int(kind), float(seconds), C.byref(rate), stream), self.ctx)
+        return float(rate.value)
+
+
+def workspace_bytes(n: int, cameras, options=None, n_pairs: int = 0) -> dict:
+    """Device bytes a render of n Gaussians from ``cameras`` (one dict or a list) and its backward allocate in
+    a fresh context and frame, with the pair buffers sized for ``n_pairs`` (ngs_workspace_bytes). No
+    device call."""
+    cams = [cameras] if isinstance(cameras, dict) else list(cameras)
+    arr = (_abi.Camera * len(cams))(*(_camera(c) for c in cams))
+    out = _abi.Workspace()
+    rc = _abi.load().ngs_workspace_bytes(int(n), arr, len(cams), C.byref(_options(options)), int(n_pairs), C.byref(out))
+    if rc != _abi.NGS_OK:
+        raise _abi.NGSError(f"ngs_workspace_bytes: invalid arguments (status {rc})", rc)
+    return {k: int(getattr(out, k)) for k, _ in _abi.Workspace._fields_}
+
 
 _renderers = threading.local()
 
