@@ -867,6 +867,25 @@ def run_batched(args, r, dev, single_view_models):
                 ts.append(e[0].elapsed_time(e[1]))
                 tsb.append(e[2].elapsed_time(e[3]))
         same = all(torch.equal(a, b) for a, b in zip(vimg, fb.split(img)))
+        # per-stage CUDA-event times of one more call of each form, with direct launches (replayed graph
+        # phases carry no stage events): which stages batching shrinks and which it cannot
+        r.set_graphs(False)
+        stages = {}
+        for form in ("batched", "one_view_at_a_time"):
+            flush.zero_()
+            r.set_timing(True)
+            r.reset_stage_times()
+            if form == "batched":
+                r.render_batch(params, cams, m, opts[m], frame=fb, images=img, overdraw=od)
+                r.backward(fb, params, dl, out=g)
+            else:
+                for v, c in enumerate(cams):
+                    r.render(params, c, m, vopts[m], frame=fviews[v], image=vimg[v], overdraw=vod[v])
+                    r.backward(fviews[v], params, dlv[v].contiguous(), out=vgrads[v])
+            torch.cuda.synchronize()
+            stages[form] = {k: round(v[0], 3) for k, v in r.stage_times().items()}
+            r.set_timing(False)
+        r.set_graphs(not args.no_graphs)
         fwd, fwdbwd = statistics.median(tf), statistics.median(tfb)
         single, single_b = statistics.median(ts), statistics.median(tsb)
         out[m] = {"fwd_mpix_s": round(npix / fwd / 1e3, 1), "fwd_bwd_mpix_s": round(npix / fwdbwd / 1e3, 1),
@@ -877,6 +896,7 @@ def run_batched(args, r, dev, single_view_models):
                   "one_view_at_a_time_fwd_bwd_mpix_s": round(npix / single_b / 1e3, 1),
                   "batched_speedup_fwd": round(single / fwd, 3),
                   "batched_speedup_fwd_bwd": round(single_b / fwdbwd, 3),
+                  "stage_ms": stages,
                   "bit_identical_to_single_views": bool(same),
                   "pairs": int(fb.view()["n_pairs"]), "overdraw_mean": round(float(od.double().mean()), 3),
                   "launch_options": {k: opts[m][k] for k in ("tile_w", "tile_h", "chunk", "schedule")},
@@ -1130,9 +1150,9 @@ def cpu_baseline(args, scene, cam, crop=None):
 
     oracle.build()
     cores = os.cpu_count() or 1
-    crop = crop or args.cpu_crop or 640  # about 10-20 s of oracle work on 16 cores
+    crop = crop or args.cpu_crop or 480  # about 10-20 s of oracle work on 16 cores
     secs, px = oracle_sample(scene, cam, crop, cores)
-    crop1 = max(16, crop // 5)  # single-threaded: a smaller crop, about 10 s
+    crop1 = max(16, crop // 3)  # single-threaded: a smaller crop, about 10 s
     secs1, px1 = oracle_sample(scene, cam, crop1, 1)
     return {"value": round(px / secs / 1e6, 5), "unit": "Mpix/s", "cores": cores, "kind": "oracle",
             "seconds": round(secs, 2),

@@ -381,8 +381,8 @@ NGS_API int ngs_densify(ngs_ctx* ctx, int64_t n, int32_t sh_degree, const ngs_gr
  *    request for the same scene and model (in arrival order, at most max_batch_views) and renders them as
  *    one ngs_render_batch-style pass; requests that arrive while the GPU is busy join the next batch.
  *    Each image equals ngs_render of that request alone, bit for bit.
- *  - Admission by memory: a batch reserves its depth-sort buffer bytes (16 per splat record) before it
- *    starts and its tile-sort bytes (16 per pair) once the exact pair count is known; it waits while the
+ *  - Admission by memory: a batch reserves the bytes ngs_workspace_bytes reports for it -- frame_fixed +
+ *    context before it starts, frame_pairs once the exact pair count is known; it waits while the
  *    reservations of the batches in flight would exceed mem_budget. The oldest batch in flight may always
  *    proceed (counted in over_budget_admissions when that exceeds the budget), so one always progresses.
  * Threading: submit, poll and get_stats may be called from any host thread. Requests reference caller-owned
@@ -392,7 +392,7 @@ typedef struct ngs_server ngs_server;
 typedef struct {
   int32_t workers;         /* 1..64 (default 4)                                                        */
   int32_t max_batch_views; /* 1..4096 (default 16)                                                     */
-  int64_t mem_budget;      /* bytes of sort buffers all batches in flight may reserve (default 8 GiB)   */
+  int64_t mem_budget;      /* bytes all batches in flight may reserve (default 8 GiB)                  */
   int32_t graphs;          /* 1: workers capture/replay CUDA graphs of the render phases; 0 (default):  */
                            /* direct launches (batch shapes vary, so replays rarely match a capture)   */
   int32_t reserved;        /* 0                                                                         */

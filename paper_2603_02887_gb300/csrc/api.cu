@@ -263,6 +263,18 @@ static int stage_views(ngs_ctx* ctx, ngs_frame* f) {
   return NGS_OK;
 }
 
+// The bytes ngs_workspace_bytes reports, from one plan: a fresh allocation of each buffer.
+static size_t fresh_bytes(size_t bytes) { return bytes ? grown_size(0, bytes) : (size_t)0; }
+static size_t plan_frame_fixed(const BufferPlan& b) {
+  return fresh_bytes(b.rec) + fresh_bytes(b.tile_count) + 2 * fresh_bytes(b.keys) + 2 * fresh_bytes(b.vals) +
+         fresh_bytes(b.offsets) + fresh_bytes(b.ranges) + fresh_bytes(b.state) + fresh_bytes(b.views) +
+         fresh_bytes(b.work) + fresh_bytes(b.sched);
+}
+static size_t plan_frame_pairs(const BufferPlan& b) { return 2 * fresh_bytes(b.pair_tile) + 2 * fresh_bytes(b.pair_val); }
+static size_t plan_context(const BufferPlan& b) {
+  return fresh_bytes(b.scan_tmp) + fresh_bytes(b.total) + grown_size(grown_size(0, b.hist1), b.hist2);
+}
+
 // Checked mode: every parameter of the Gaussians finite, else NGS_ERR_INVALID_ARG naming the array.
 __global__ void nonfinite_kernel(const float* __restrict__ a, size_t count, uint32_t bit, uint32_t* flag) {
   pdl_wait();
@@ -598,7 +610,9 @@ int ngs::render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, co
     NGS_TRY(ensure(ctx, f->sched, bp.sched));
   }
   NGS_TRY(stage_views(ctx, f));
-  if (admit) NGS_TRY(admit(admit_user, 0, sizeof(uint32_t) * 4 * (size_t)R));
+  // admission reserves what ngs_workspace_bytes reports: the frame's record, tile and pixel buffers and the
+  // context's scratch now, the pair buffers once the pair count is known
+  if (admit) NGS_TRY(admit(admit_user, 0, plan_frame_fixed(bp) + plan_context(bp)));
 
   KeyBuf k1;
   k1.add(*g);
@@ -639,7 +653,9 @@ int ngs::render_views_out(ngs_ctx* ctx, ngs_frame* f, const ngs_gaussians* g, co
     const uint64_t P = mirror[0];
     if (P >= (1ull << 31)) return fail(ctx, NGS_ERR_INVALID_ARG, "more than 2^31 (tile, Gaussian) pairs");
     np = (uint32_t)P;
-    if (admit) NGS_TRY(admit(admit_user, 1, sizeof(uint32_t) * 4 * (size_t)np));
+    if (admit)
+      NGS_TRY(admit(admit_user, 1, plan_frame_pairs(plan_buffers(R, pl.n, (uint32_t)n_views, pl.ntiles, pix_total,
+                                                                 rp.schedule, np))));
     // the capacity that graph replays and asynchronous renders reuse while the count fits
     if (np > f->pair_cap) f->pair_cap = (uint32_t)std::min<uint64_t>((uint64_t)np + np / 4 + 1024, (1ull << 31) - 1);
     // phase 2: exact sizes, or, for graph replays, the capacity
@@ -983,12 +999,10 @@ NGS_API int ngs_workspace_bytes(int64_t n, const ngs_camera* cams, int32_t n_vie
   const uint64_t R = (uint64_t)n * (uint64_t)n_views;
   if (R >= (1ull << 32)) return NGS_ERR_INVALID_ARG;
   const BufferPlan b = plan_buffers(R, (uint32_t)n, (uint32_t)n_views, tiles, pix, o->schedule, (uint64_t)n_pairs);
-  auto fresh = [](size_t bytes) { return bytes ? grown_size(0, bytes) : (size_t)0; };
-  out->frame_fixed = fresh(b.rec) + fresh(b.tile_count) + 2 * fresh(b.keys) + 2 * fresh(b.vals) + fresh(b.offsets) +
-                     fresh(b.ranges) + fresh(b.state) + fresh(b.views) + fresh(b.work) + fresh(b.sched);
-  out->frame_pairs = 2 * fresh(b.pair_tile) + 2 * fresh(b.pair_val);
-  out->context = fresh(b.scan_tmp) + fresh(b.total) + grown_size(grown_size(0, b.hist1), b.hist2);
-  out->backward = fresh(b.grad2d);
+  out->frame_fixed = plan_frame_fixed(b);
+  out->frame_pairs = plan_frame_pairs(b);
+  out->context = plan_context(b);
+  out->backward = fresh_bytes(b.grad2d);
   out->total = out->frame_fixed + out->frame_pairs + out->context + out->backward;
   return NGS_OK;
 }

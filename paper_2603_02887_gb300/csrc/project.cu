@@ -162,26 +162,53 @@ __device__ __forceinline__ void store_sh(float* dst, const float (&c)[3 * K]) {
   }
 }
 
+// A request to bring the line holding `p` into L1 (PTX prefetch; no register is written).
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
+// The raw parameters of one Gaussian other than its SH coefficients, read in one go so that their loads
+// are in flight together (the quaternion as one 16-byte load when the array is 16-byte aligned).
+struct RawParams {
+  float m[3], ls[3], q[4], logit;
+};
+
+__device__ __forceinline__ RawParams load_params(const ngs_gaussians& g, int i) {
+  RawParams r;
+  const float* m = g.means + 3 * (int64_t)i;
+  const float* ls = g.log_scales + 3 * (int64_t)i;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    r.m[k] = m[k];
+    r.ls[k] = ls[k];
+  }
+  if (((uintptr_t)g.quats & 15) == 0) {
+    const float4 q = reinterpret_cast<const float4*>(g.quats)[i];
+    r.q[0] = q.x, r.q[1] = q.y, r.q[2] = q.z, r.q[3] = q.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.q[k] = g.quats[4 * (int64_t)i + k];
+  }
+  r.logit = g.opacity_logits[i];
+  return r;
+}
+
 // sh_src: Gaussian i's 3K SH coefficients (in global memory, or staged in shared memory by the caller).
 template <int DEG, bool VEC = false>
-__device__ __forceinline__ void forward_map(const ngs_gaussians& g, const CamParams& cam, const RenderParams& rp,
-                                            int i, ProjState<DEG>& st, const float* sh_src) {
+__device__ __forceinline__ void forward_map(const RawParams& prm, const CamParams& cam, const RenderParams& rp,
+                                            ProjState<DEG>& st, const float* sh_src) {
   constexpr int K = ProjState<DEG>::K;
-  const float* m = g.means + 3 * (int64_t)i;
-  float px = m[0], py = m[1], pz = m[2];
+  const float px = prm.m[0], py = prm.m[1], pz = prm.m[2];
   st.x = cam.R[0] * px + cam.R[1] * py + cam.R[2] * pz + cam.t[0];
   st.y = cam.R[3] * px + cam.R[4] * py + cam.R[5] * pz + cam.t[1];
   st.z = view_depth(cam, px, py, pz);
   st.iz = 1.f / st.z;
-  const float* q = g.quats + 4 * (int64_t)i;
+  const float* q = prm.q;
   st.qnorm = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
   float inv = 1.f / st.qnorm;
 #pragma unroll
   for (int k = 0; k < 4; ++k) st.qn[k] = q[k] * inv;
   quat_to_rot(st.qn[0], st.qn[1], st.qn[2], st.qn[3], st.Rq);
-  const float* ls = g.log_scales + 3 * (int64_t)i;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) st.S[k] = expf(ls[k]);
+  for (int k = 0; k < 3; ++k) st.S[k] = expf(prm.ls[k]);
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -214,7 +241,7 @@ __device__ __forceinline__ void forward_map(const ngs_gaussians& g, const CamPar
   st.A = st.s11 * idet;
   st.B = -st.s01 * idet;
   st.C = st.s00 * idet;
-  st.aleph = 1.f / (1.f + expf(-g.opacity_logits[i]));
+  st.aleph = 1.f / (1.f + expf(-prm.logit));
   float d0 = px - cam.campos[0], d1 = py - cam.campos[1], d2 = pz - cam.campos[2];
   st.dnorm = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
   float idn = 1.f / st.dnorm;
@@ -350,7 +377,7 @@ __global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, const Vie
   uint32_t count = 0;
   if (z > rp.near_plane) {
     ProjState<DEG> st;
-    forward_map<DEG, VEC>(g, cam, rp, i, st, g.sh + (int64_t)i * ProjState<DEG>::K * 3);
+    forward_map<DEG, VEC>(load_params(g, i), cam, rp, st, g.sh + (int64_t)i * ProjState<DEG>::K * 3);
     if (st.det > 0.f && st.aleph >= rp.alpha_min && isfinite(st.A) && isfinite(st.C)) {
       float u = cam.fx * st.x * st.iz + cam.cx;
       float v = cam.fy * st.y * st.iz + cam.cy;
@@ -415,18 +442,17 @@ struct ParamGrad {
 // DIRECT (a single view): each gradient is stored to `out` as soon as it is known instead, which keeps it
 // out of the registers live across the rest of the chain.
 template <int DEG, bool VEC, bool DIRECT>
-__device__ __forceinline__ void add_view_gradient(const ngs_gaussians& g, const CamParams& cam,
-                                                  const RenderParams& rp, int i, const float4* gr,
+__device__ __forceinline__ void add_view_gradient(const RawParams& prm, const CamParams& cam,
+                                                  const RenderParams& rp, int i, float4 g0, float4 g1, float4 g2,
                                                   ParamGrad<DEG>& acc, const ngs_grads& out, const float* sh_src,
                                                   float* dsh_dst) {
   constexpr int K = ProjState<DEG>::K;
-  float4 g0 = gr[0], g1 = gr[1], g2 = gr[2];
   // the replay accumulates w / ln 2 (w = dL/d(log2 alpha)): restore the factor on the six moments
   g0 = make_float4(g0.x * kLn2, g0.y * kLn2, g0.z * kLn2, g0.w * kLn2);
   g1.x *= kLn2;
   g1.y *= kLn2;
   ProjState<DEG> st;
-  forward_map<DEG, VEC>(g, cam, rp, i, st, sh_src);
+  forward_map<DEG, VEC>(prm, cam, rp, st, sh_src);
   // moments -> record gradient (the record's A', B', C' are these same products) -> natural quantities
   const float Ap = kConicScale * st.A, Bp = 2.f * kConicScale * st.B, Cp = kConicScale * st.C;
   float du = -(2.f * Ap * g0.x + Bp * g0.y);
@@ -575,6 +601,18 @@ __global__ void __launch_bounds__(128, MULTI ? 1 : 4) project_backward_kernel(ng
   __shared__ float4 s_sh[kStage ? 128 * (Q + 1) : 1];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // every line this Gaussian's chain reads is requested here, together with the warp's SH staging below,
+  // so that the loads after the test of its tile count find them in L1 (prefetches hold no registers)
+  if (i < g.n) {
+    prefetch_l1(g.means + 3 * (int64_t)i);
+    prefetch_l1(g.log_scales + 3 * (int64_t)i);
+    prefetch_l1(g.quats + 4 * (int64_t)i);
+    prefetch_l1(g.opacity_logits + i);
+    if constexpr (!MULTI) {
+      prefetch_l1(grad2d + 3 * (int64_t)i);
+      prefetch_l1(grad2d + 3 * (int64_t)i + 2);
+    }
+  }
   const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + warp * 32;  // first Gaussian of the warp
   const int64_t left = g.n - g0;
   const int warp_n = left <= 0 ? 0 : (left >= 32 ? 32 : (int)left);
@@ -601,16 +639,19 @@ __global__ void __launch_bounds__(128, MULTI ? 1 : 4) project_backward_kernel(ng
       if (tile_count[i] != 0) {
         const float* sh_src = kStage ? reinterpret_cast<const float*>(my_sh) : g.sh + (int64_t)i * K * 3;
         float* dsh_dst = kStage ? reinterpret_cast<float*>(my_sh) : out.d_sh + (int64_t)i * K * 3;
-        add_view_gradient<DEG, VEC, true>(g, cam0, rp, i, grad2d + 3 * (int64_t)i, acc, out, sh_src, dsh_dst);
+        const float4* gr = grad2d + 3 * (int64_t)i;
+        add_view_gradient<DEG, VEC, true>(load_params(g, i), cam0, rp, i, gr[0], gr[1], gr[2], acc, out, sh_src,
+                                          dsh_dst);
         written = true;
       }
     } else {
+      const RawParams prm = load_params(g, i);
       for (int v = 0; v < (int)rp.n_views; ++v) {
         const int64_t r = (int64_t)v * g.n + i;
         if (tile_count[r] == 0) continue;
         const CamParams cam = views[v].cam;
-        add_view_gradient<DEG, VEC, false>(g, cam, rp, i, grad2d + 3 * r, acc, out, g.sh + (int64_t)i * K * 3,
-                                           nullptr);
+        add_view_gradient<DEG, VEC, false>(prm, cam, rp, i, grad2d[3 * r], grad2d[3 * r + 1], grad2d[3 * r + 2], acc,
+                                           out, g.sh + (int64_t)i * K * 3, nullptr);
       }
     }
     if (!written) {  // the sums over views (or zeros: culled in every view)

@@ -7,9 +7,10 @@
 // order, up to max_batch_views): requests that arrived while the GPU was busy join the next batch. The
 // batch is one multi-view render; each request's image is written to the caller's own buffer.
 //
-// Admission: the memory a render's sort buffers need is known in two steps -- the depth sort's (4 words
-// per splat record) before the render starts, the tile sort's (4 words per pair) once the exact pair
-// count is read back. Each step reserves its bytes against mem_budget and waits while they do not fit;
+// Admission: the memory a render needs is known in two steps, as ngs_workspace_bytes reports it -- the
+// frame's record, tile and pixel buffers and the context's scratch before the render starts, the pair
+// buffers (16 bytes per pair) once the exact pair count is read back. Each step reserves its bytes against
+// mem_budget and waits while they do not fit;
 // the oldest batch in flight may always go on (so some batch always makes progress), and is counted as an
 // over-budget admission when it had to exceed the budget to do so.
 #include <algorithm>
