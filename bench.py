@@ -1200,7 +1200,7 @@ def run_reference(args):
 TRAFFIC_COMMAND = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
                    "--clock-control none --nvtx --nvtx-include timed/ -k regex:composite_ --csv python bench.py "
                    "--steps 1 --warmup 3 --no-e2e --no-cpu-baseline --no-batched --no-serving --no-training "
-                   "--streams 1")
+                   "--no-configs --no-peaks --streams 1")
 
 
 def main():
