@@ -14,7 +14,7 @@ their differences, chained through the absolute Jacobian, is the element's ``all
 channel at its max(0, .) clamp (per Gaussian, not per pixel) may be clamped or not: each combination of
 its borderline channels is a candidate reference for that Gaussian's gradients.
 
-The gradient criterion per element (spec: relative 1e-3; SURVEY c14 floor):
+The gradient criterion per element (relative 1e-3, with a floor of 1e-3 x the tensor's largest gradient):
   strict:  |g - g_ref| <= 1e-3 max(|g_ref|, 1e-3 max|g_ref|) + allowance
   scaled:  the same + 1e-4 s + p. A gradient is a sum of per-pixel terms that may cancel; in FP32 it is
            only as accurate as its terms: s (the oracle's sum of the absolute terms chained through the

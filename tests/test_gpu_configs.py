@@ -105,10 +105,19 @@ def _window_subscene(scene, cam, win):
     return {k: v[idx] for k, v in scene.items()}, idx
 
 
-def test_differentiation_1m_finite_differences(rnd, diff_scene):
+@pytest.fixture(scope="module")
+def fd_window(diff_scene):
+    scene, cam = diff_scene
+    win = (584, 364, 128, 128)
+    sub, idx = _window_subscene(scene, cam, win)
+    return win, sub, idx
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_differentiation_1m_finite_differences(rnd, diff_scene, fd_window, model):
     """The GPU's path-replay gradient on 64 random raw parameters against central differences of the
     FP64 oracle (L = sum(g * image) over a 128x128 window of the 1M-Gaussian frame, g nonzero only there),
-    at the benchmark spec's relative 1e-3.
+    at the benchmark spec's relative 1e-3, for each of the four models.
 
     The oracle renders the window from the Gaussians that can reach it (the same image as from the whole
     scene, checked). Steps are h = 1e-5 max(1, |theta|); a sample is redrawn when any pixel's composited
@@ -116,19 +125,18 @@ def test_differentiation_1m_finite_differences(rnd, diff_scene):
     there). Where a pixel's GPU result took another legitimate outcome than the FP64 walk, the expected
     value carries that outcome's difference (tests/parity.py); the tolerance is that of the crop test."""
     scene, cam = diff_scene
-    win = (584, 364, 128, 128)
+    win, sub, idx = fd_window
     x0, y0, w, h = win
-    model = "sup"
     params = upload(scene)
     img0, od0, frame = rnd.render(params, cam, model, OPTS[model])
     gw = synth.upstream_gradient(h, w, seed=12).astype(np.float64)
     g = np.zeros((cam["height"], cam["width"], 3), np.float32)
     g[y0:y0 + h, x0:x0 + w] = gw
     grads = {k: v.cpu().numpy() for k, v in rnd.backward(frame, params, torch.from_numpy(g).cuda()).items()}
-    sub, idx = _window_subscene(scene, cam, win)
     ref = oracle.render(sub, cam, model, window=win, nthreads=NT, dl_dimage=gw, outcomes=True)
-    full = oracle.render(scene, cam, model, window=win, nthreads=NT)
-    assert np.array_equal(ref["image"], full["image"]) and np.array_equal(ref["overdraw"], full["overdraw"])
+    if model == "sup":  # the window's Gaussians render the same image as the whole scene
+        full = oracle.render(scene, cam, model, window=win, nthreads=NT)
+        assert np.array_equal(ref["image"], full["image"]) and np.array_equal(ref["overdraw"], full["overdraw"])
     m = parity.assert_forward(img0.cpu().numpy()[y0:y0 + h, x0:x0 + w], od0.cpu().numpy()[y0:y0 + h, x0:x0 + w], ref)
     gref = parity.reference_gradients(ref, m)
     live = np.nonzero(np.abs(ref["d_opacity_logits"]) > 0.05 * np.abs(ref["d_opacity_logits"]).max())[0]
@@ -161,5 +169,5 @@ def test_differentiation_1m_finite_differences(rnd, diff_scene):
         worst = max(worst, abs(an - expected) / max(abs(expected), floor))
         checked += 1
     assert checked == 64
-    print(f"[parity] 1M/1297x840 finite differences of the FP64 oracle: 64 samples, worst |an - fd| / "
-          f"max(|fd|, floor) = {worst:.2e}")
+    print(f"[parity] 1M/1297x840 {model}: finite differences of the FP64 oracle, 64 samples, worst "
+          f"|an - fd| / max(|fd|, floor) = {worst:.2e}")

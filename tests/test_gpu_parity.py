@@ -210,6 +210,28 @@ def test_edge_cases(rnd):
         _forward_check(rnd, synth.tiny_scene(1, n=200), small, model)
 
 
+@pytest.mark.parametrize("model", ["exp", "sup"])
+def test_maximum_image_width(rnd, model):
+    """The largest accepted image side (16384 px) with a ragged last tile row: a 16384 x 21 frame against
+    the oracle on windows at both ends and the middle; and 16385 is refused."""
+    from paper_2603_02887_gb300._abi import NGSError
+
+    cam = synth.pinhole(np.concatenate([np.eye(3), np.zeros((3, 1))], 1), 16384, 21, 3000.0, 3000.0)
+    scene = synth.tiny_scene(5, n=4000)
+    scene["means"][:, 0] *= 8.0  # spread across the wide frame, past both ends
+    params = upload(scene)
+    image, overdraw, _ = rnd.render(params, cam, model)
+    img, od = image.cpu().numpy(), overdraw.cpu().numpy()
+    assert od.sum() > 0
+    for x0 in (0, 8192 - 32, 16384 - 64):
+        win = (x0, 0, 64, 21)
+        ref = oracle.render(scene, cam, model, window=win, nthreads=NT, outcomes=True)
+        m = parity.assert_forward(img[:, x0:x0 + 64], od[:, x0:x0 + 64], ref, label=f"{model} x0={x0}")
+        assert m.n_unresolved == 0
+    with pytest.raises(NGSError):
+        rnd.render(params, dict(cam, width=16385), model)
+
+
 @pytest.mark.parametrize("model", MODELS)
 def test_max_splats_cap(rnd, model):
     _forward_check(rnd, synth.tiny_scene(2), synth.tiny_camera(), model, dict(max_splats=3))
