@@ -117,7 +117,7 @@ def fd_window(diff_scene):
 def test_differentiation_1m_finite_differences(rnd, diff_scene, fd_window, model):
     """The GPU's path-replay gradient on 64 random raw parameters against central differences of the
     FP64 oracle (L = sum(g * image) over a 128x128 window of the 1M-Gaussian frame, g nonzero only there),
-    at the benchmark spec's relative 1e-3, for each of the four models.
+    at relative 1e-3, for each of the four models.
 
     The oracle renders the window from the Gaussians that can reach it (the same image as from the whole
     scene, checked). Steps are h = 1e-5 max(1, |theta|); a sample is redrawn when any pixel's composited
