@@ -369,8 +369,11 @@ def run_ours(args):
             step(events[i] if events else None, serial=True)
         torch.cuda.synchronize()
         out = {}
+        per_ctx.clear()
         for x in rs:
-            for k, v in x.stage_times().items():
+            st = x.stage_times()
+            per_ctx.append({k: v[0] / n for k, v in st.items()})
+            for k, v in st.items():
                 out[k] = [a + b for a, b in zip(out[k], v)] if k in out else list(v)
             x.set_timing(False)
             x.set_graphs(not args.no_graphs)
@@ -380,6 +383,7 @@ def run_ours(args):
     # direct launches. With one stream the backward stages (the dominant ones) are the timed region's own;
     # with several, overlapping kernels would inflate each other's event times, so they come from K more
     # steps with the models one after another.
+    per_ctx = []  # the last stage_steps call's per-context stage ms per step
     if S == 1:
         stage = r.stage_times()
         r.set_timing(False)
@@ -388,10 +392,21 @@ def run_ours(args):
     else:
         model_ev = [{m: [torch.cuda.Event(enable_timing=True) for _ in range(3)] for m in MODELS} for _ in range(K)]
         stage = stage_steps(K, not args.no_graphs, model_ev)
+        stage_bwd_ctx = list(per_ctx)
         stage_source = (f"{K} further steps with the models one after another" if args.no_graphs else
                         f"backward stages: {K} further steps with the models one after another; "
                         "forward stages: 2 further such steps with direct launches")
     stage_direct = stage if args.no_graphs else stage_steps(2, False)
+    # per model, where each model has a context of its own: the backward stages from the K serial steps,
+    # the forward stages from the direct-launch steps
+    stage_per_model = None
+    if S == len(MODELS):
+        stage_per_model = {}
+        for m in MODELS:
+            d = dict(stage_bwd_ctx[owner[m]])
+            d.update({k: v for k, v in per_ctx[owner[m]].items() if k not in ("composite_bwd", "project_bwd")}
+                     if stage_direct is not stage else {})
+            stage_per_model[m] = {k: round(v * 1e3, 1) for k, v in d.items()}
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = max_over_ranks(sum(step_ms), device=dev)
     ms_per_step = total_ms / K
@@ -442,6 +457,7 @@ def run_ours(args):
                              "two models' kernels)"),
         "stage_ms_per_step": {k: round(v, 4) for k, v in stage_ms.items()},
         "stage_ms_source": stage_source,
+        "stage_us_per_model": stage_per_model,
         "gpu_launches": int(launches), "gpu_launches_per_step": round(launches / K, 1),
         "roofline": roof, "clocks": clk, "pipe_peaks": pipe_peaks,
     }

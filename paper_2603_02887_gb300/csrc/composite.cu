@@ -131,7 +131,7 @@ struct PairStageBuf {
   float4 q1[CH];  // {A', A', B', B'}
   float4 q2[CH];  // {C', C', L, L}
   float4 q3[CH];  // {E0, E0, E1, E1}
-  float2 q4[CH];  // {E2, E2}
+  float4 q4[CH];  // {E2, E2, record index (bits), 0}: one 16-byte load gives E2 and the atomics' target
 };
 
 // The packed form (exponential and quadratic models) is used while its staging (72 B per record) stays
@@ -142,14 +142,13 @@ constexpr bool kPairForm = (KIND == NGS_MODEL_EXP || KIND == NGS_MODEL_QUAD) && 
 template <int B, int CH>
 __device__ __forceinline__ void stage_chunk_pairs(const float4* __restrict__ rec, const uint32_t* __restrict__ ids,
                                                   const RenderParams& rp, uint32_t base, uint32_t end,
-                                                  PairStageBuf<CH>& sb, uint32_t* s_id) {
+                                                  PairStageBuf<CH>& sb) {
 #pragma unroll
   for (int k = 0; k < (CH + B - 1) / B; ++k) {
     const int slot = k * B + (int)threadIdx.x;
     const uint32_t i = base + (uint32_t)slot;
     if (slot < CH && i < end) {
       const uint32_t id = ids[i];
-      if (s_id) s_id[slot] = id < rp.n_records ? id : 0u;
       float4 r0, r1;
       float e2;
       stage_record(rec, id, rp, r0, r1, e2);
@@ -157,7 +156,7 @@ __device__ __forceinline__ void stage_chunk_pairs(const float4* __restrict__ rec
       sb.q1[slot] = make_float4(r0.z, r0.z, r0.w, r0.w);
       sb.q2[slot] = make_float4(r1.x, r1.x, r1.y, r1.y);
       sb.q3[slot] = make_float4(r1.z, r1.z, r1.w, r1.w);
-      sb.q4[slot] = make_float2(e2, e2);
+      sb.q4[slot] = make_float4(e2, e2, __uint_as_float(id < rp.n_records ? id : 0u), 0.f);
     }
   }
 }
@@ -375,7 +374,7 @@ __device__ __forceinline__ void forward_tile_pairs(const float4* __restrict__ re
   const float2 c2 = make_float2(rp.c, rp.c);
   for (uint32_t base = range.x; base < range.y; base += CH) {
     if (__syncthreads_count(done0 && done1) == B) break;
-    stage_chunk_pairs<B, CH>(rec, ids, rp, base, range.y, sb, nullptr);
+    stage_chunk_pairs<B, CH>(rec, ids, rp, base, range.y, sb);
     __syncthreads();
     const int cnt = (int)min((uint32_t)CH, range.y - base);
     if (__any_sync(kFull, !(done0 && done1))) {
@@ -390,7 +389,7 @@ __device__ __forceinline__ void forward_tile_pairs(const float4* __restrict__ re
         const bool on0 = !done0 && e.x >= l2min, on1 = !done1 && e.y >= l2min;
         if (!(on0 || on1)) continue;
         const float4 q3 = sb.q3[j];
-        const float2 E0 = lo_hi(q3, false), E1 = lo_hi(q3, true), E2 = sb.q4[j];
+        const float2 E0 = lo_hi(q3, false), E1 = lo_hi(q3, true), E2 = lo_hi(sb.q4[j], false);
         const float2 alpha = make_float2(on0 ? fminf(amax, fast_exp2(e.x)) : 0.f, on1 ? fminf(amax, fast_exp2(e.y)) : 0.f);
         const uint32_t pos = base + j - range.x;
         bool c0, c1;  // composited (the overdraw count)
@@ -684,27 +683,32 @@ struct BwdPair {
   float2 S, tau, nEk, nTh;  // quadratic: S, taubar, -g.E_k, -g.Theta
 };
 
-// One list entry for both pixels: adds their contributions to v (the 9 per-splat sums, the dx moments
-// included) and returns whether either pixel composited the splat.
-template <int KIND>
-__device__ __forceinline__ bool bwd_pair_step(BwdPair& p, float4 q0, float4 q1, float4 q2, float4 q3, float2 q4,
-                                              uint32_t pos, const RenderParams& rp, float (&v)[9]) {
-  const float2 one = make_float2(1.f, 1.f), neg = make_float2(-1.f, -1.f);
-  // the quadratic form, as splat_log2_alpha_col computes it per pixel
-  const float2 dx = __fadd2_rn(p.px, lo_hi(q0, false));  // px - u, equal in both lanes
+// The quadratic form of an entry at both pixels (as splat_log2_alpha_col computes it per pixel): e = log2
+// of aleph K, dx (px - u, equal in both lanes: one column) and dy.
+__device__ __forceinline__ float2 pair_log2_alpha(const BwdPair& p, float4 q0, float4 q1, float4 q2, float2& dx,
+                                                  float2& dy) {
+  dx = __fadd2_rn(p.px, lo_hi(q0, false));
   const float2 adx = __fmul2_rn(lo_hi(q1, false), dx);
-  const float2 dy = __fadd2_rn(p.py, lo_hi(q0, true));
+  dy = __fadd2_rn(p.py, lo_hi(q0, true));
   const float2 t = __ffma2_rn(lo_hi(q1, true), dy, adx);
   const float2 cdd = __fmul2_rn(__fmul2_rn(lo_hi(q2, false), dy), dy);
-  const float2 e = __fadd2_rn(lo_hi(q2, true), __ffma2_rn(dx, t, cdd));
-  const bool on0 = pos < p.last0 && e.x >= rp.log2_alpha_min;
-  const bool on1 = pos < p.last1 && e.y >= rp.log2_alpha_min;
-  if (!(on0 || on1)) return false;
+  return __fadd2_rn(lo_hi(q2, true), __ffma2_rn(dx, t, cdd));
+}
+
+// One list entry for both pixels, given the quadratic form (e, dx, dy) and which pixels composite it
+// (on0 / on1: not past their stop, alpha >= alpha_min): adds their contributions to v (the 9 per-splat
+// sums, the dx moments included). A pixel that does not composite it gets alpha = 0, which leaves its
+// running sums exactly as they were and adds nothing, so the warp runs the step whenever any lane is on.
+template <int KIND>
+__device__ __forceinline__ void bwd_pair_step(BwdPair& p, float2 e, float2 dx, float2 dy, float4 q3, float4 q4,
+                                              bool on0, bool on1, const RenderParams& rp, float (&v)[9]) {
+  const float2 one = make_float2(1.f, 1.f), neg = make_float2(-1.f, -1.f);
   const float raw0 = fast_exp2(e.x), raw1 = fast_exp2(e.y);
   const float2 alpha = make_float2(on0 ? fminf(rp.alpha_max, raw0) : 0.f, on1 ? fminf(rp.alpha_max, raw1) : 0.f);
   // w = dL/de: zero where alpha is clamped at alpha_max (it no longer depends on e) or not composited
   bool live0 = on0 && raw0 < rp.alpha_max, live1 = on1 && raw1 < rp.alpha_max;
-  const float2 gE = __ffma2_rn(p.g2, q4, __ffma2_rn(p.g1, lo_hi(q3, true), __fmul2_rn(p.g0, lo_hi(q3, false))));
+  const float2 gE =
+      __ffma2_rn(p.g2, lo_hi(q4, false), __ffma2_rn(p.g1, lo_hi(q3, true), __fmul2_rn(p.g0, lo_hi(q3, false))));
   float2 dLda, wE;
   if constexpr (KIND == NGS_MODEL_QUAD) {
     const float2 ct = __ffma2_rn(make_float2(rp.c, rp.c), p.tau, one);  // 1 + c taubar_i
@@ -744,7 +748,6 @@ __device__ __forceinline__ bool bwd_pair_step(BwdPair& p, float4 q0, float4 q1, 
   v[6] = c0.x + c0.y;
   v[7] = c1.x + c1.y;
   v[8] = c2.x + c2.y;
-  return true;
 }
 
 template <int TW, int TH, int KIND, int CH>
@@ -753,7 +756,7 @@ __device__ __forceinline__ void backward_tile_pairs(const float4* __restrict__ r
                                                     const ViewParams* __restrict__ views,
                                                     const float* __restrict__ dl_dimage,
                                                     const float4* __restrict__ state, float4* __restrict__ grad2d,
-                                                    uint32_t tile, PairStageBuf<CH>& sb, uint32_t* s_id) {
+                                                    uint32_t tile, PairStageBuf<CH>& sb) {
   using G = TileGeom<TW, TH, kBwdPix>;
   constexpr int B = G::kThreads;
   const TileView tv = tile_view(rp, views, (uint32_t)tile);
@@ -808,16 +811,23 @@ __device__ __forceinline__ void backward_tile_pairs(const float4* __restrict__ r
   const uint32_t warp_last = __reduce_max_sync(kFull, my_last);
   for (uint32_t base = range.x; base < range.y; base += CH) {
     if (__syncthreads_count(base >= my_last) == B) break;
-    stage_chunk_pairs<B, CH>(rec, ids, rp, base, range.y, sb, s_id);
+    stage_chunk_pairs<B, CH>(rec, ids, rp, base, range.y, sb);
     __syncthreads();
     if (base < warp_last) {
       const int cnt = (int)(min(warp_last, min(base + (uint32_t)CH, range.y)) - base);
       for (int j = 0; j < cnt; ++j) {
-        float v[9];
-        const bool on = bwd_pair_step<KIND>(p, sb.q0[j], sb.q1[j], sb.q2[j], sb.q3[j], sb.q4[j], base + j, rp, v);
+        float2 dx, dy;
+        const float2 e = pair_log2_alpha(p, sb.q0[j], sb.q1[j], sb.q2[j], dx, dy);
+        const uint32_t pos = base + j;
+        const bool on0 = pos < p.last0 && e.x >= rp.log2_alpha_min;
+        const bool on1 = pos < p.last1 && e.y >= rp.log2_alpha_min;
+        const bool on = on0 || on1;
         const uint32_t mask = __ballot_sync(kFull, on);
-        if (mask) {
-          float4* dst = grad2d + 3 * (size_t)s_id[j];
+        if (mask) {  // warp-uniform: the step is exact for the lanes that are off
+          float v[9];
+          const float4 q4 = sb.q4[j];
+          bwd_pair_step<KIND>(p, e, dx, dy, sb.q3[j], q4, on0, on1, rp, v);
+          float4* dst = grad2d + 3 * (size_t)__float_as_uint(q4.z);
           if (__popc(mask) <= kDirectLanes) {
             if (on) {
               atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
@@ -951,10 +961,10 @@ __global__ void __launch_bounds__(TW* TH / kBwdPix) composite_backward_kernel(co
   pdl_wait();
   using Buf = std::conditional_t<kPairForm<KIND, CH>, PairStageBuf<CH>, StageBuf<CH>>;
   __shared__ Buf sb;
-  __shared__ uint32_t s_id[CH];
+  __shared__ uint32_t s_id[kPairForm<KIND, CH> ? 1 : CH];  // the packed form carries the index in its q4
   auto one_tile = [&](uint32_t tile) {
     if constexpr (kPairForm<KIND, CH>)
-      backward_tile_pairs<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, dl_dimage, state, grad2d, tile, sb, s_id);
+      backward_tile_pairs<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, dl_dimage, state, grad2d, tile, sb);
     else
       backward_tile<TW, TH, KIND, CH>(rec, ids, ranges, rp, views, dl_dimage, state, grad2d, tile, sb, s_id);
   };
