@@ -130,3 +130,24 @@ def sorted_pairs(rec, log2_amin, tile_w, tile_h, width, height):
         ranges[:, 0] = np.where(ends > starts, starts, 0)
         ranges[:, 1] = np.where(ends > starts, ends, 0)
     return keys, vals, ranges
+
+
+def tile_lists(rec, log2_amin, tile_w, tile_h, width, height, tiles):
+    """For each tile t of `tiles`, its values (record indices) after the stable sort, computed for that tile
+    alone: the records whose bounding box holds the tile and whose row span in the tile's row reaches its
+    column, ordered by (FP32 depth bits, index). For checking large renders tile by tile, where
+    sorted_pairs would be slow. Returns {t: uint32 array}."""
+    rec = np.asarray(rec, F)
+    x0, x1, y0, y1, ok, tiles_x, tiles_y = tile_box(rec[:, 0], rec[:, 1], rec[:, 10], rec[:, 11], tile_w, tile_h,
+                                                     width, height)
+    zbits = rec[:, 9].view(np.uint32).astype(np.int64)
+    out = {}
+    with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
+        for t in tiles:
+            ty, tx = divmod(int(t), tiles_x)
+            hit = [g for g in np.nonzero(ok & (x0 <= tx) & (x1 >= tx) & (y0 <= ty) & (y1 >= ty))[0]
+                   if (span := _Ellipse(rec[g], log2_amin).row_span(ty, x0[g], x1[g], tile_w, tile_h))
+                   and span[0] <= tx <= span[1]]
+            hit = np.array(hit, np.int64)
+            out[int(t)] = hit[np.lexsort((hit, zbits[hit]))].astype(np.uint32)
+    return out

@@ -391,7 +391,7 @@ static cudaError_t phase2(ngs_ctx* ctx, ngs_frame* f, const RenderPlan& pl, uint
   stage_begin(ctx, s, 4, &ev);
   launches = cap ? 1 : 0;
   launch_tile_ranges(f->ptile[f->p_final].as<uint32_t>(), f->pvals[f->p_final].as<uint32_t>(), views, pl.n, rp.n_views,
-                     cap, np_dev, pl.ntiles, f->ranges.as<uint2>(), s);
+                     cap, np_dev, pl.ntiles, f->ranges.as<uint2>(), rp.check, s);
   const uint32_t* work = nullptr;
   uint32_t* counter = nullptr;
   if (rp.schedule == NGS_SCHEDULE_PERSISTENT) {

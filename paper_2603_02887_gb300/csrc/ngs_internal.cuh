@@ -60,6 +60,7 @@ struct RenderParams {
 
 constexpr uint32_t kCheckIndex = 1u;     // a sorted pair named a splat record index >= n_records
 constexpr uint32_t kCheckCapacity = 2u;  // an asynchronous render met more pairs than its capacity
+constexpr uint32_t kCheckTile = 8u;      // a sorted pair named a tile outside the batch's tiles
 
 // Geometry of the view holding global tile t. A single view takes it from the kernel parameters (no
 // dependent load before the tile's work starts); a batch looks it up in the view table.
@@ -368,10 +369,10 @@ void launch_compose_keys(const uint32_t* tiles, const uint32_t* vals, const floa
                          uint32_t n_per_view, uint32_t n_views, uint32_t npairs, uint64_t* keys, cudaStream_t s);
 // [start, end) of every global tile's pairs into `ranges`, which the caller has zeroed (zero-length ranges
 // stay (0, 0)); npairs_cap items are covered by the grid, of which the first *npairs_dev are valid if
-// npairs_dev is not null.
+// npairs_dev is not null. A pair naming a record or tile out of range is skipped and reported in *check.
 void launch_tile_ranges(const uint32_t* tiles, const uint32_t* vals, const ViewParams* views, uint32_t n_per_view,
                         uint32_t n_views, uint32_t npairs_cap, const uint32_t* npairs_dev, uint32_t ntiles,
-                        uint2* ranges, cudaStream_t s);
+                        uint2* ranges, uint32_t* check, cudaStream_t s);
 // Persistent schedule: work[] lists all tiles by descending pair count (buckets of floor(log2(pairs)),
 // any order within a bucket). `sched` holds kSchedWords zeroed words: [0] forward and [1] backward work
 // counters, then per-bucket counts and cursors.

@@ -312,13 +312,22 @@ __device__ __forceinline__ uint32_t global_tile(const uint32_t* __restrict__ til
 
 __global__ void tile_ranges_kernel(const uint32_t* __restrict__ tiles, const uint32_t* __restrict__ vals,
                                    const ViewParams* __restrict__ views, uint32_t n_per_view, uint32_t n_views,
-                                   uint32_t npairs_cap, const uint32_t* __restrict__ npairs_dev,
-                                   uint2* __restrict__ ranges) {
+                                   uint32_t npairs_cap, const uint32_t* __restrict__ npairs_dev, uint32_t ntiles,
+                                   uint2* __restrict__ ranges, uint32_t* check) {
   pdl_wait();
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t npairs = npairs_dev ? min(*npairs_dev, npairs_cap) : npairs_cap;
   if (i >= npairs) return;
+  // a pair naming a record or tile out of range (never from a correct sort) is skipped and reported
+  if (vals[i] >= n_per_view * n_views) {
+    atomicOr(check, kCheckIndex);
+    return;
+  }
   const uint32_t t = global_tile(tiles, vals, views, n_per_view, n_views, i);
+  if (t >= ntiles) {
+    atomicOr(check, kCheckTile);
+    return;
+  }
   if (i == 0 || global_tile(tiles, vals, views, n_per_view, n_views, i - 1) != t) ranges[t].x = i;
   if (i == npairs - 1 || global_tile(tiles, vals, views, n_per_view, n_views, i + 1) != t) ranges[t].y = i + 1;
 }
@@ -422,10 +431,10 @@ cudaError_t launch_scan_counts(const uint32_t* tile_count, const uint32_t* order
 
 void launch_tile_ranges(const uint32_t* tiles, const uint32_t* vals, const ViewParams* views, uint32_t n_per_view,
                         uint32_t n_views, uint32_t npairs_cap, const uint32_t* npairs_dev, uint32_t ntiles,
-                        uint2* ranges, cudaStream_t s) {
+                        uint2* ranges, uint32_t* check, cudaStream_t s) {
   if (npairs_cap == 0) return;
   launch_pdl(tile_ranges_kernel, (npairs_cap + 255) / 256, 256, 0, s, tiles, vals, views, n_per_view, n_views,
-             npairs_cap, npairs_dev, ranges);
+             npairs_cap, npairs_dev, ntiles, ranges, check);
 }
 
 void launch_compose_keys(const uint32_t* tiles, const uint32_t* vals, const float4* rec, const ViewParams* views,

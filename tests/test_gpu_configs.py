@@ -5,6 +5,8 @@ on 16x16), on outputs the FP64 oracle computes one by one: windows of the full f
 * single large view: 500k clustered Gaussians (SH 3) at 1920x1080, forward for the four models, on three
   windows (centre, an off-centre region, and a stretch of the bottom edge, where the 16-pixel tiles are
   ragged since 1080 = 67.5 x 16);
+* the pair sort of the exponential model's 8x8 tiles at 1920x1080 with 500k and 2M Gaussians: properties
+  of the whole sorted array, and sampled tiles against the oracle's list for each;
 * differentiation: 1M clustered Gaussians at 1297x840, forward + path-replay backward for the four models
   with an L1-type upstream gradient restricted to a 256x256 window, against the oracle's gradients of that
   window; and the GPU's gradient on 64 random raw parameters against central differences of the FP64
@@ -24,10 +26,11 @@ if not torch.cuda.is_available():
 
 import bench  # noqa: E402
 import oracle  # noqa: E402
+from oracle import binning  # noqa: E402
 from paper_2603_02887_gb300 import synth  # noqa: E402
 from paper_2603_02887_gb300.render import PARAM_KEYS, Renderer  # noqa: E402
 from tests import parity  # noqa: E402
-from tests.gpu_util import upload  # noqa: E402
+from tests.gpu_util import frame_arrays, upload  # noqa: E402
 
 MODELS = ["exp", "sub", "lin", "sup"]
 NT = os.cpu_count() or 4
@@ -59,6 +62,42 @@ def test_single_view_500k_1080p_windows(rnd, single_view, model):
         assert m.n_unresolved == 0, m.summary()
         print(f"[parity] 500k/1080p {model} window {win}: {m.summary()}")
         assert ref["overdraw"].mean() > 0.5, win  # the windows are not empty
+
+
+@pytest.mark.parametrize("n", [500_000, 2_000_000])
+def test_pair_sort_full_size(rnd, n):
+    """The pair sort at full size in the exponential model's bench launch options (8x8 tiles, 1920x1080):
+    500k Gaussians give about 4.2M pairs (the sort's tiles of 1024 keys), 2M more than 2^23 (tiles of 4096
+    keys). Over the whole array: tiles non-decreasing, each tile's pairs in (depth, index) order, the ranges
+    the runs of each tile. Tile by tile against the oracle's list (oracle/binning.tile_lists on the GPU's own
+    records): the 8 longest lists and 56 random non-empty ones."""
+    scene = synth.clustered_scene(n, seed=0 if n == 500_000 else 4, sh_degree=3)
+    cam = synth.outside_camera(1920, 1080)
+    _, _, frame = rnd.render(upload(scene), cam, "exp", OPTS["exp"])
+    fa = frame_arrays(frame)
+    keys, vals, ranges = fa["keys"], fa["values"], fa["ranges"].astype(np.int64)
+    P = len(keys)
+    assert P > (1 << 23) if n > 500_000 else P > 4_000_000, P
+    tile, z = (keys >> np.uint64(32)).astype(np.int64), (keys & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    assert np.all(np.diff(tile) >= 0)
+    same = tile[1:] == tile[:-1]
+    dz = np.diff(z)
+    assert np.all(dz[same] >= 0)
+    tie = same & (dz == 0)
+    assert np.all(vals[1:][tie] > vals[:-1][tie])
+    lens = ranges[:, 1] - ranges[:, 0]
+    assert lens.sum() == P
+    nz = np.nonzero(lens)[0]
+    assert np.array_equal(tile[ranges[nz, 0]], nz) and np.array_equal(tile[ranges[nz, 1] - 1], nz)
+    rng = np.random.default_rng(n)
+    pick = sorted(set(np.argsort(lens)[-8:].tolist()) | set(rng.choice(nz, 56, replace=False).tolist()))
+    exp = binning.tile_lists(fa["records"], fa["view"]["log2_alpha_min"], 8, 8, 1920, 1080, pick)
+    for t in pick:
+        s, e = ranges[t]
+        assert np.array_equal(vals[s:e], exp[t]), t
+    print(f"[parity] pair sort {n} Gaussians, 1920x1080 8x8: {P} pairs; {len(pick)} tiles checked, longest "
+          f"{int(lens.max())}")
+    rnd.recycle(frame)
 
 
 @pytest.fixture(scope="module")

@@ -1,6 +1,6 @@
 """Pins of the tile-binning oracle (no GPU): every pixel a splat reaches lies in a covered tile (brute
-force over pixels, FP64), covered tiles are a subset of the bounding box, and the stable sort agrees with
-Python's sorted() on (key, emission index)."""
+force over pixels, FP64), covered tiles are a subset of the bounding box, the stable sort agrees with
+Python's sorted() on (key, emission index), and the per-tile list equals that tile's run of the sort."""
 import math
 
 import numpy as np
@@ -75,3 +75,17 @@ def test_sorted_pairs_match_python_sort():
         s, e = ranges[t]
         assert np.all((keys[s:e] >> np.uint64(32)) == t)
     assert ranges[:, 1].max() == len(keys)
+
+
+def test_tile_list_matches_sorted_pairs():
+    rng = np.random.default_rng(2)
+    width, height = 90, 60
+    rec = _records(rng, 150, width, height)
+    for tw, th in ((8, 8), (16, 16)):
+        keys, vals, ranges = binning.sorted_pairs(rec, L2MIN, tw, th, width, height)
+        lists = binning.tile_lists(rec, L2MIN, tw, th, width, height, range(len(ranges)))
+        for t in range(len(ranges)):
+            s, e = ranges[t]
+            assert np.array_equal(lists[t], vals[s:e]), (tw, t)
+        assert len(keys) > 100
+
