@@ -886,7 +886,8 @@ int ngs::backward_frame(ngs_ctx* ctx, const ngs_frame* f, const ngs_gaussians* g
   stage_end(ctx, s, 6, ev, 1);
   NGS_TRY(check_launch(ctx, "composite backward"));
   stage_begin(ctx, s, 7, &ev);
-  launch_project_backward(*g, views, f->view_host[0].cam, f->rp, f->tile_count.as<uint32_t>(), ctx->grad2d.as<float4>(), *out, s);
+  launch_project_backward(*g, views, f->view_host[0].cam, f->rp, f->tile_count.as<uint32_t>(), ctx->grad2d.as<float4>(), *out,
+                          ctx->num_sms, s);
   stage_end(ctx, s, 7, ev, g->n ? 1 : 0);
   NGS_TRY(check_launch(ctx, "projection backward"));
   return NGS_OK;

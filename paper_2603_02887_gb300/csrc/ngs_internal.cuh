@@ -344,7 +344,7 @@ void launch_project(const ngs_gaussians& g, const ViewParams* views, const CamPa
 // cam0: the camera of view 0 (the only one when rp.n_views == 1).
 void launch_project_backward(const ngs_gaussians& g, const ViewParams* views, const CamParams& cam0,
                              const RenderParams& rp, const uint32_t* tile_count, const float4* grad2d,
-                             const ngs_grads& out, cudaStream_t s);
+                             const ngs_grads& out, int num_sms, cudaStream_t s);
 // Stable radix sort of (key, value) pairs on bits [begin_bit, end_bit), independently within each of
 // `nseg` segments of seg_len items. If n_dev is not null, only the first min(*n_dev, seg_len) items of a
 // segment are sorted (a count known on the device only; seg_len is then the capacity). Returns the index

@@ -95,7 +95,8 @@ extern "C" NGS_API int ngs_render_backward_static(ngs_ctx* ctx, const ngs_frame*
   ctx->launches += 1;
   ctx->stage_launches[6] += 1;
   if (n) {
-    launch_project_backward(*g, views, f->view_host[0].cam, f->rp, f->tile_count.as<uint32_t>(), grad2d, *out, s);
+    launch_project_backward(*g, views, f->view_host[0].cam, f->rp, f->tile_count.as<uint32_t>(), grad2d, *out,
+                            ctx->num_sms, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ctx, NGS_ERR_CUDA, std::string("projection backward: ") + cudaGetErrorString(e));
     ctx->launches += 1;

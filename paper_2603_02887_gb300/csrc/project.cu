@@ -8,6 +8,8 @@
 // Backward: the exact chain rule of the same map, from splat-record gradients to raw parameters.
 #include <math.h>
 
+#include <algorithm>
+
 #include "ngs_internal.cuh"
 
 namespace ngs {
@@ -677,12 +679,17 @@ __device__ __forceinline__ void add_view_gradient(const RawParams& prm, const Ca
   }
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // One thread per Gaussian; MULTI: loop over the views of a batch (records v n + i), else the one view
 // `cam0`, passed by value so that its entries are constant-bank operands rather than registers.
 // Culled splats (no tile) contribute nothing; a Gaussian culled in every view gets zeros.
 // One view: at most 128 registers (4 CTAs per SM). Without the SH staging below, 5 CTAs per SM hid the
 // memory latency best (a sweep of 3..8 on GB300: 0.35 / 0.32 / 0.31 / 0.33 / 0.34 / 0.41 ms per 4 calls);
 // with it, 4 CTAs per SM take 0.285 ms, while 5 spill and take 0.39.
+// The CTAs stride over blocks of 128 Gaussians (a grid of one wave for a single view): while a block
+// computes, the next block's lines are already on their way into L2, so that DRAM stays busy through the
+// long arithmetic stretch of each block.
 template <int DEG, bool VEC, bool MULTI>
 __global__ void __launch_bounds__(128, MULTI ? 1 : 4) project_backward_kernel(ngs_gaussians g, const ViewParams* __restrict__ views,
                                                                CamParams cam0, RenderParams rp,
@@ -696,80 +703,104 @@ __global__ void __launch_bounds__(128, MULTI ? 1 : 4) project_backward_kernel(ng
   constexpr bool kStage = VEC && !MULTI;
   constexpr int Q = VEC ? 3 * K / 4 : 1;  // float4 per Gaussian
   __shared__ float4 s_sh[kStage ? 128 * (Q + 1) : 1];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // every line this Gaussian's chain reads is requested here, together with the warp's SH staging below,
-  // so that the loads after the test of its tile count find them in L1 (prefetches hold no registers)
-  if (i < g.n) {
-    prefetch_l1(g.means + 3 * (int64_t)i);
-    prefetch_l1(g.log_scales + 3 * (int64_t)i);
-    prefetch_l1(g.quats + 4 * (int64_t)i);
-    prefetch_l1(g.opacity_logits + i);
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < g.n; b0 += step) {
+    const int i = (int)(b0 + threadIdx.x);
+    // every line this Gaussian's chain reads is requested here, together with the warp's SH staging below,
+    // so that the loads after the test of its tile count find them in L1 (prefetches hold no registers)
+    if (i < g.n) {
+      prefetch_l1(g.means + 3 * (int64_t)i);
+      prefetch_l1(g.log_scales + 3 * (int64_t)i);
+      prefetch_l1(g.quats + 4 * (int64_t)i);
+      prefetch_l1(g.opacity_logits + i);
+      if constexpr (!MULTI) {
+        prefetch_l1(grad2d + 3 * (int64_t)i);
+        prefetch_l1(grad2d + 3 * (int64_t)i + 2);
+      }
+    }
+    const int64_t g0 = b0 + warp * 32;  // first Gaussian of the warp
+    const int64_t left = g.n - g0;
+    const int warp_n = left <= 0 ? 0 : (left >= 32 ? 32 : (int)left);
+    float4* my_sh = kStage ? &s_sh[threadIdx.x * (Q + 1)] : nullptr;
+    if constexpr (kStage) {
+      const float4* src = reinterpret_cast<const float4*>(g.sh) + g0 * Q;
+      for (int idx = lane; idx < warp_n * Q; idx += 32) {
+        const int j = idx / Q;
+        s_sh[(warp * 32 + j) * (Q + 1) + (idx - j * Q)] = src[idx];
+      }
+      __syncwarp();
+    }
     if constexpr (!MULTI) {
-      prefetch_l1(grad2d + 3 * (int64_t)i);
-      prefetch_l1(grad2d + 3 * (int64_t)i + 2);
-    }
-  }
-  const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + warp * 32;  // first Gaussian of the warp
-  const int64_t left = g.n - g0;
-  const int warp_n = left <= 0 ? 0 : (left >= 32 ? 32 : (int)left);
-  float4* my_sh = kStage ? &s_sh[threadIdx.x * (Q + 1)] : nullptr;
-  if constexpr (kStage) {
-    const float4* src = reinterpret_cast<const float4*>(g.sh) + g0 * Q;
-    for (int idx = lane; idx < warp_n * Q; idx += 32) {
-      const int j = idx / Q;
-      s_sh[(warp * 32 + j) * (Q + 1) + (idx - j * Q)] = src[idx];
-    }
-    __syncwarp();
-  }
-  if (i < g.n) {
-    ParamGrad<DEG> acc;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) acc.m[k] = acc.ls[k] = 0.f;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) acc.q[k] = 0.f;
-    acc.op = 0.f;
-#pragma unroll
-    for (int k = 0; k < 3 * K; ++k) acc.sh[k] = 0.f;
-    bool written = false;
-    if constexpr (!MULTI) {
-      if (tile_count[i] != 0) {
-        const float* sh_src = kStage ? reinterpret_cast<const float*>(my_sh) : g.sh + (int64_t)i * K * 3;
-        float* dsh_dst = kStage ? reinterpret_cast<float*>(my_sh) : out.d_sh + (int64_t)i * K * 3;
-        const float4* gr = grad2d + 3 * (int64_t)i;
-        add_view_gradient<DEG, VEC, true>(load_params(g, i), cam0, rp, i, gr[0], gr[1], gr[2], acc, out, sh_src,
-                                          dsh_dst);
-        written = true;
+      // the next block's lines into L2 (the warp's SH block: Q * 512 bytes, one 128-byte line per lane step)
+      const int64_t nx = (int64_t)i + step;
+      if (nx < g.n) {
+        prefetch_l2(g.means + 3 * nx);
+        prefetch_l2(g.log_scales + 3 * nx);
+        prefetch_l2(g.quats + 4 * nx);
+        prefetch_l2(g.opacity_logits + nx);
+        prefetch_l2(grad2d + 3 * nx);
+        prefetch_l2(grad2d + 3 * nx + 2);
+        prefetch_l2(tile_count + nx);
       }
-    } else {
-      const RawParams prm = load_params(g, i);
-      for (int v = 0; v < (int)rp.n_views; ++v) {
-        const int64_t r = (int64_t)v * g.n + i;
-        if (tile_count[r] == 0) continue;
-        const CamParams cam = views[v].cam;
-        add_view_gradient<DEG, VEC, false>(prm, cam, rp, i, grad2d[3 * r], grad2d[3 * r + 1], grad2d[3 * r + 2], acc,
-                                           out, g.sh + (int64_t)i * K * 3, nullptr);
+      if constexpr (kStage) {
+        const int64_t ng0 = g0 + step;
+        const int64_t nleft = g.n - ng0;
+        const int nwarp = nleft <= 0 ? 0 : (nleft >= 32 ? 32 : (int)nleft);
+        const char* nsrc = reinterpret_cast<const char*>(reinterpret_cast<const float4*>(g.sh) + ng0 * Q);
+        for (int line = lane; line * 128 < nwarp * Q * 16; line += 32) prefetch_l2(nsrc + line * 128);
       }
     }
-    if (!written) {  // the sums over views (or zeros: culled in every view)
+    if (i < g.n) {
+      ParamGrad<DEG> acc;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        out.d_means[3 * (int64_t)i + k] = acc.m[k];
-        out.d_log_scales[3 * (int64_t)i + k] = acc.ls[k];
+      for (int k = 0; k < 3; ++k) acc.m[k] = acc.ls[k] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc.q[k] = 0.f;
+      acc.op = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3 * K; ++k) acc.sh[k] = 0.f;
+      bool written = false;
+      if constexpr (!MULTI) {
+        if (tile_count[i] != 0) {
+          const float* sh_src = kStage ? reinterpret_cast<const float*>(my_sh) : g.sh + (int64_t)i * K * 3;
+          float* dsh_dst = kStage ? reinterpret_cast<float*>(my_sh) : out.d_sh + (int64_t)i * K * 3;
+          const float4* gr = grad2d + 3 * (int64_t)i;
+          add_view_gradient<DEG, VEC, true>(load_params(g, i), cam0, rp, i, gr[0], gr[1], gr[2], acc, out, sh_src,
+                                            dsh_dst);
+          written = true;
+        }
+      } else {
+        const RawParams prm = load_params(g, i);
+        for (int v = 0; v < (int)rp.n_views; ++v) {
+          const int64_t r = (int64_t)v * g.n + i;
+          if (tile_count[r] == 0) continue;
+          const CamParams cam = views[v].cam;
+          add_view_gradient<DEG, VEC, false>(prm, cam, rp, i, grad2d[3 * r], grad2d[3 * r + 1], grad2d[3 * r + 2],
+                                             acc, out, g.sh + (int64_t)i * K * 3, nullptr);
+        }
       }
+      if (!written) {  // the sums over views (or zeros: culled in every view)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) out.d_quats[4 * (int64_t)i + k] = acc.q[k];
-      out.d_opacity_logits[i] = acc.op;
-      if constexpr (kStage) store_sh<K, VEC>(reinterpret_cast<float*>(my_sh), acc.sh);
-      else store_sh<K, VEC>(out.d_sh + (int64_t)i * K * 3, acc.sh);
+        for (int k = 0; k < 3; ++k) {
+          out.d_means[3 * (int64_t)i + k] = acc.m[k];
+          out.d_log_scales[3 * (int64_t)i + k] = acc.ls[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out.d_quats[4 * (int64_t)i + k] = acc.q[k];
+        out.d_opacity_logits[i] = acc.op;
+        if constexpr (kStage) store_sh<K, VEC>(reinterpret_cast<float*>(my_sh), acc.sh);
+        else store_sh<K, VEC>(out.d_sh + (int64_t)i * K * 3, acc.sh);
+      }
     }
-  }
-  if constexpr (kStage) {
-    __syncwarp();
-    float4* dst = reinterpret_cast<float4*>(out.d_sh) + g0 * Q;
-    for (int idx = lane; idx < warp_n * Q; idx += 32) {
-      const int j = idx / Q;
-      dst[idx] = s_sh[(warp * 32 + j) * (Q + 1) + (idx - j * Q)];
+    if constexpr (kStage) {
+      __syncwarp();
+      float4* dst = reinterpret_cast<float4*>(out.d_sh) + g0 * Q;
+      for (int idx = lane; idx < warp_n * Q; idx += 32) {
+        const int j = idx / Q;
+        dst[idx] = s_sh[(warp * 32 + j) * (Q + 1) + (idx - j * Q)];
+      }
+      __syncwarp();  // the next block's staging overwrites these rows
     }
   }
 }
@@ -808,29 +839,34 @@ void launch_emit_pairs(const float4* rec, const uint32_t* order, const uint32_t*
 template <int DEG, bool VEC>
 static void project_backward_views(const ngs_gaussians& g, const ViewParams* views, const CamParams& cam0,
                                    const RenderParams& rp, const uint32_t* tile_count, const float4* grad2d,
-                                   const ngs_grads& out, cudaStream_t s) {
-  int blocks = (int)((g.n + 127) / 128);
-  if (rp.n_views > 1)
-    launch_pdl(project_backward_kernel<DEG, VEC, true>, blocks, 128, 0, s, g, views, cam0, rp, tile_count, grad2d, out);
-  else
-    launch_pdl(project_backward_kernel<DEG, VEC, false>, blocks, 128, 0, s, g, views, cam0, rp, tile_count, grad2d, out);
+                                   const ngs_grads& out, int num_sms, cudaStream_t s) {
+  const int64_t blocks = (g.n + 127) / 128;
+  if (rp.n_views > 1) {
+    launch_pdl(project_backward_kernel<DEG, VEC, true>, (unsigned)blocks, 128, 0, s, g, views, cam0, rp, tile_count,
+               grad2d, out);
+  } else {
+    // one wave: 4 CTAs per SM (the kernel's register bound)
+    const int64_t wave = 4 * (int64_t)std::max(num_sms, 1);
+    launch_pdl(project_backward_kernel<DEG, VEC, false>, (unsigned)std::min(blocks, wave), 128, 0, s, g, views, cam0,
+               rp, tile_count, grad2d, out);
+  }
 }
 
 void launch_project_backward(const ngs_gaussians& g, const ViewParams* views, const CamParams& cam0,
                              const RenderParams& rp, const uint32_t* tile_count, const float4* grad2d,
-                             const ngs_grads& out, cudaStream_t s) {
+                             const ngs_grads& out, int num_sms, cudaStream_t s) {
   if (g.n == 0) return;
   bool vec = ((uintptr_t)g.sh & 15) == 0 && ((uintptr_t)out.d_sh & 15) == 0;
   switch (rp.sh_degree) {
-    case 0: project_backward_views<0, false>(g, views, cam0, rp, tile_count, grad2d, out, s); break;
+    case 0: project_backward_views<0, false>(g, views, cam0, rp, tile_count, grad2d, out, num_sms, s); break;
     case 1:
-      if (vec) project_backward_views<1, true>(g, views, cam0, rp, tile_count, grad2d, out, s);
-      else project_backward_views<1, false>(g, views, cam0, rp, tile_count, grad2d, out, s);
+      if (vec) project_backward_views<1, true>(g, views, cam0, rp, tile_count, grad2d, out, num_sms, s);
+      else project_backward_views<1, false>(g, views, cam0, rp, tile_count, grad2d, out, num_sms, s);
       break;
-    case 2: project_backward_views<2, false>(g, views, cam0, rp, tile_count, grad2d, out, s); break;
+    case 2: project_backward_views<2, false>(g, views, cam0, rp, tile_count, grad2d, out, num_sms, s); break;
     default:
-      if (vec) project_backward_views<3, true>(g, views, cam0, rp, tile_count, grad2d, out, s);
-      else project_backward_views<3, false>(g, views, cam0, rp, tile_count, grad2d, out, s);
+      if (vec) project_backward_views<3, true>(g, views, cam0, rp, tile_count, grad2d, out, num_sms, s);
+      else project_backward_views<3, false>(g, views, cam0, rp, tile_count, grad2d, out, num_sms, s);
       break;
   }
 }

@@ -318,8 +318,9 @@ __global__ void tile_ranges_kernel(const uint32_t* __restrict__ tiles, const uin
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t npairs = npairs_dev ? min(*npairs_dev, npairs_cap) : npairs_cap;
   if (i >= npairs) return;
-  // a pair naming a record or tile out of range (never from a correct sort) is skipped and reported
-  if (vals[i] >= n_per_view * n_views) {
+  // a pair naming a record or tile out of range (never from a correct sort) is skipped and reported (the
+  // record index only where it selects the view; the compositing checks it anyway)
+  if (n_views > 1 && vals[i] >= n_per_view * n_views) {
     atomicOr(check, kCheckIndex);
     return;
   }
