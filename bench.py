@@ -720,9 +720,10 @@ def parse_options(spec=TUNED_OPTIONS) -> dict:
     return out
 
 
-def launch_options(args, r, params, cams, reps=2, use_options=True):
+def launch_options(args, r, params, cams, reps=2, use_options=True, tables=None):
     """Per-model launch options: the fixed ones given on the command line, else the library's autotuner
-    (render + backward timed under every tile shape x chunk x schedule on this very workload)."""
+    (render + backward timed under every tile shape x chunk x schedule on this very workload). `tables`,
+    if a dict, receives each tuned model's timing table [(tile_w, tile_h, chunk, schedule, ms)]."""
     fixed = {}
     if args.tile:
         fixed["tile_w"], fixed["tile_h"] = (int(v) for v in args.tile.split("x"))
@@ -740,8 +741,10 @@ def launch_options(args, r, params, cams, reps=2, use_options=True):
         if m in given:
             out[m] = given[m]
         else:
-            best, _ = r.autotune(params, cams, m, backward=True, reps=reps)
+            best, table = r.autotune(params, cams, m, backward=True, reps=reps)
             out[m] = best
+            if tables is not None:
+                tables[m] = table
     tuned = f"autotuned (render + backward, median of {reps} with L2 cleared before each, 18 candidates per model)"
     if not given:
         return out, tuned
@@ -827,7 +830,8 @@ def run_batched(args, r, dev, single_view_models):
     params = {k: torch.from_numpy(np.ascontiguousarray(scene[k])).to(dev) for k in PARAM_KEYS}
     del scene
     npix = sum(c["width"] * c["height"] for c in cams)
-    opts, tuning = launch_options(args, r, params, cams, reps=3, use_options=False)
+    tables = {}
+    opts, tuning = launch_options(args, r, params, cams, reps=3, use_options=False, tables=tables)
     # the one-view-at-a-time form gets its own tuning, on the largest view
     big = max(cams, key=lambda c: c["width"] * c["height"])
     vopts, _ = launch_options(args, r, params, [big], reps=3, use_options=False)
@@ -918,6 +922,11 @@ def run_batched(args, r, dev, single_view_models):
                   "launch_options": {k: opts[m][k] for k in ("tile_w", "tile_h", "chunk", "schedule")},
                   "one_view_at_a_time_launch_options": {k: vopts[m][k] for k in ("tile_w", "tile_h", "chunk",
                                                                                   "schedule")}}
+        if m in tables:  # the tuner's render + backward ms of both schedules at the chosen tile and chunk
+            pick = opts[m]
+            out[m]["tuner_schedule_ms"] = {
+                ("persistent" if row[3] else "tiles"): round(row[4], 3) for row in tables[m]
+                if (row[0], row[1], row[2]) == (pick["tile_w"], pick["tile_h"], pick["chunk"])}
     clk.mark_end()
     out["clocks"] = clk.stop()
     out["timing"] = f"median of {reps} calls per form and model, after one untimed call"
