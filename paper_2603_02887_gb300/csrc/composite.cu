@@ -378,7 +378,7 @@ __device__ __forceinline__ void forward_tile_pairs(const float4* __restrict__ re
     __syncthreads();
     const int cnt = (int)min((uint32_t)CH, range.y - base);
     if (__any_sync(kFull, !(done0 && done1))) {
-      for (int j = 0; j < cnt && !(done0 && done1); ++j) {
+      for (int j = 0; j < cnt; ++j) {
         const float4 q0 = sb.q0[j], q1 = sb.q1[j], q2 = sb.q2[j];
         const float2 dx = __fadd2_rn(px, lo_hi(q0, false));
         const float2 adx = __fmul2_rn(lo_hi(q1, false), dx);
@@ -387,7 +387,13 @@ __device__ __forceinline__ void forward_tile_pairs(const float4* __restrict__ re
         const float2 cdd = __fmul2_rn(__fmul2_rn(lo_hi(q2, false), dy), dy);
         const float2 e = __fadd2_rn(lo_hi(q2, true), __ffma2_rn(dx, t, cdd));
         const bool on0 = !done0 && e.x >= l2min, on1 = !done1 && e.y >= l2min;
-        if (!(on0 || on1)) continue;
+        // warp-uniform: a lane that does not composite the entry (or has stopped) runs the step with
+        // alpha = 0, which leaves its sums exactly as they were; the warp leaves the chunk once all of its
+        // pixels have stopped
+        if (__ballot_sync(kFull, on0 || on1) == 0u) {
+          if (__all_sync(kFull, done0 && done1)) break;
+          continue;
+        }
         const float4 q3 = sb.q3[j];
         const float2 E0 = lo_hi(q3, false), E1 = lo_hi(q3, true), E2 = lo_hi(sb.q4[j], false);
         const float2 alpha = make_float2(on0 ? fminf(amax, fast_exp2(e.x)) : 0.f, on1 ? fminf(amax, fast_exp2(e.y)) : 0.f);
