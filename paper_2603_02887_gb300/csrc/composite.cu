@@ -543,9 +543,10 @@ struct BwdPixel {
 
 // Sum nine per-lane values over the warp and add the totals to dst[0..8] with one atomic instruction.
 // Values 0..7 go through a transposing butterfly: at each of three steps a lane keeps half of the values
-// it carries and sends the other half to its partner, so after xor 16, 8, 4 (and two plain xor 2, 1
-// steps) lane l holds the warp total of value ((l >> 2) & 7). Value 8 uses an ordinary tree.
-// 21 shuffles + 21 adds instead of 45 + 45.
+// it carries and sends the other half to its partner, so after xor 16, 8, 4 a lane carries one of them,
+// summed over 8 lanes; value 8 is summed over the same lanes by a plain tree. The last two steps (xor 2,
+// 1) carry both, half of the lanes each, so that lane l ends with the warp total of value ((l >> 2) & 7)
+// when l % 4 == 0, and lane 2 with that of value 8: 12 shuffles instead of 45 for nine plain trees.
 __device__ __forceinline__ void warp_reduce9_add(const float (&v)[9], float* dst, int lane) {
   const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
   float w[4];
@@ -564,15 +565,19 @@ __device__ __forceinline__ void warp_reduce9_add(const float (&v)[9], float* dst
   }
   float send = b2 ? x[0] : x[1];
   float y = (b2 ? x[1] : x[0]) + __shfl_xor_sync(kFull, send, 4);
-  y += __shfl_xor_sync(kFull, y, 2);
-  y += __shfl_xor_sync(kFull, y, 1);
+  // the ninth value over lane bits 4..2, then both over bits 1 and 0 in one transposing step: lanes with
+  // bit 1 clear carry y, lanes with it set carry e
   float e = v[8];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(kFull, e, o);
+  e += __shfl_xor_sync(kFull, e, 16);
+  e += __shfl_xor_sync(kFull, e, 8);
+  e += __shfl_xor_sync(kFull, e, 4);
+  const bool b1 = lane & 2;
+  float z = (b1 ? e : y) + __shfl_xor_sync(kFull, b1 ? y : e, 2);
+  z += __shfl_xor_sync(kFull, z, 1);
   if ((lane & 3) == 0)
-    atomicAdd(dst + ((lane >> 2) & 7), y);
-  else if (lane == 1)
-    atomicAdd(dst + 8, e);
+    atomicAdd(dst + ((lane >> 2) & 7), z);  // value (lane >> 2) & 7, summed over the warp
+  else if ((lane & 3) == 2 && lane < 4)
+    atomicAdd(dst + 8, z);                  // the ninth, summed over the warp
 }
 
 // One list entry for one pixel of the replay: adds the pixel's contributions to the per-splat sums that

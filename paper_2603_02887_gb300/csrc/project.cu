@@ -362,7 +362,7 @@ constexpr int kCoopRows = 8;
 // A single view takes its camera from the kernel parameters (cam0), a batch (or a captured graph, which
 // must serve any pose) from the view table; the arithmetic below is the same code either way.
 template <int DEG, bool VEC>
-__global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, const ViewParams* __restrict__ views,
+__global__ void __launch_bounds__(256, 4) project_kernel(ngs_gaussians g, const ViewParams* __restrict__ views,
                                                       CamParams cam0, RenderParams rp, float4* rec,
                                                       uint32_t* depth_key, uint32_t* tile_count, uint32_t* order) {
   pdl_wait();
@@ -374,6 +374,19 @@ __global__ void __launch_bounds__(256) project_kernel(ngs_gaussians g, const Vie
     rp.tiles_y = views[view].tiles_y;
   }
   const int64_t r = (int64_t)view * g.n + i;  // record index
+  if (i < g.n) {
+    // every line the projection reads, requested at once: the loads behind the depth test and inside the
+    // colour find them in L1 instead of making three round trips to memory one after another
+    prefetch_l1(g.means + 3 * (int64_t)i);
+    prefetch_l1(g.log_scales + 3 * (int64_t)i);
+    prefetch_l1(g.quats + 4 * (int64_t)i);
+    prefetch_l1(g.opacity_logits + i);
+    const char* sh = reinterpret_cast<const char*>(g.sh + (int64_t)i * ProjState<DEG>::K * 3);
+    constexpr int kShBytes = ProjState<DEG>::K * 3 * 4;
+#pragma unroll
+    for (int o = 0; o < kShBytes; o += 128) prefetch_l1(sh + o);
+    prefetch_l1(sh + kShBytes - 4);
+  }
   // every lane stays to the end: the warp counts its tall splats' tiles together
   uint32_t count = 0;
   bool tall = false;
