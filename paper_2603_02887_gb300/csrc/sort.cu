@@ -244,14 +244,18 @@ int radix_sort(K* keys[2], uint32_t* vals[2], uint32_t seg_len, uint32_t nseg, c
 // ---- exclusive scan of tile counts taken in depth order ---------------------------------------------
 
 constexpr int kScanThreads = 512;
-constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanThreads * kScanItems;
+// Items per thread: 2 up to kScanSmall items, where the scan is a few hundred CTAs of gathers and more
+// CTAs hide their latency; 8 above, which keeps the per-CTA sums that one CTA scans short.
+constexpr uint32_t kScanSmall = 1u << 21;
+constexpr int scan_items(uint32_t n) { return n <= kScanSmall ? 2 : 8; }
 
+template <int kScanItems>
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ count,
                                                                    const uint32_t* __restrict__ order, uint32_t n,
                                                                    uint64_t* __restrict__ block_sums) {
   pdl_wait();
   __shared__ uint64_t s_warp[kScanThreads / 32];
+  constexpr int kScanTile = kScanThreads * kScanItems;
   uint64_t sum = 0;
   uint32_t base = blockIdx.x * (uint32_t)kScanTile;
 #pragma unroll
@@ -278,11 +282,13 @@ __global__ void __launch_bounds__(1024) scan_block_sums_kernel(uint64_t* block_s
   if (threadIdx.x == 0) *total = carry;
 }
 
+template <int kScanItems>
 __global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const uint32_t* __restrict__ count,
                                                                   const uint32_t* __restrict__ order, uint32_t n,
                                                                   const uint64_t* __restrict__ block_offsets,
                                                                   uint32_t* __restrict__ offsets) {
   pdl_wait();
+  constexpr int kScanTile = kScanThreads * kScanItems;
   __shared__ uint32_t s_warp[kScanThreads / 32];
   uint32_t base = blockIdx.x * (uint32_t)kScanTile + threadIdx.x * kScanItems;  // blocked arrangement
   uint32_t v[kScanItems], local = 0;
@@ -413,7 +419,10 @@ int radix_sort_u32(uint32_t* keys[2], uint32_t* vals[2], uint32_t seg_len, uint3
 
 
 
-size_t scan_tmp_words(uint32_t n) { return (size_t)(n + kScanTile - 1) / kScanTile + 1; }
+size_t scan_tmp_words(uint32_t n) {
+  const uint32_t tile = (uint32_t)(kScanThreads * scan_items(n));
+  return (size_t)(n + tile - 1) / tile + 1;
+}
 
 cudaError_t launch_scan_counts(const uint32_t* tile_count, const uint32_t* order, uint32_t n, uint32_t* offsets,
                                uint64_t* block_sums, uint64_t* total, cudaStream_t s, int* launches) {
@@ -422,10 +431,16 @@ cudaError_t launch_scan_counts(const uint32_t* tile_count, const uint32_t* order
     if (e == cudaSuccess) e = cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
     return e;
   }
-  uint32_t nblocks = (n + kScanTile - 1) / kScanTile;
-  launch_pdl(scan_reduce_kernel, nblocks, kScanThreads, 0, s, tile_count, order, n, block_sums);
+  const int items = scan_items(n);
+  const uint32_t tile = (uint32_t)(kScanThreads * items);
+  const uint32_t nblocks = (n + tile - 1) / tile;
+  if (items == 2) launch_pdl(scan_reduce_kernel<2>, nblocks, kScanThreads, 0, s, tile_count, order, n, block_sums);
+  else launch_pdl(scan_reduce_kernel<8>, nblocks, kScanThreads, 0, s, tile_count, order, n, block_sums);
   launch_pdl(scan_block_sums_kernel, 1, 1024, 0, s, block_sums, nblocks, total);
-  launch_pdl(scan_final_kernel, nblocks, kScanThreads, 0, s, tile_count, order, n, block_sums, offsets);
+  if (items == 2)
+    launch_pdl(scan_final_kernel<2>, nblocks, kScanThreads, 0, s, tile_count, order, n, block_sums, offsets);
+  else
+    launch_pdl(scan_final_kernel<8>, nblocks, kScanThreads, 0, s, tile_count, order, n, block_sums, offsets);
   *launches += 3;
   return cudaSuccess;
 }
