@@ -497,9 +497,14 @@ template <int TW, int TH, int KIND, int CH>
 constexpr bool kPairFwd = kPairForm<KIND, CH> && (KIND == NGS_MODEL_EXP || TW * TH >= 256);
 template <int TW, int TH, int KIND, int CH>
 constexpr int kFwdThreads = TW * TH / (kPairFwd<TW, TH, KIND, CH> ? 2 : 1);
+// The packed quadratic forward on 16x16 tiles: nine CTAs of 128 threads per SM (at most 56 registers)
+// instead of the eight its 64 registers would allow.
+template <int TW, int TH, int KIND, int CH>
+constexpr int kFwdMinBlocks = (kPairFwd<TW, TH, KIND, CH> && KIND == NGS_MODEL_QUAD && TW * TH == 256) ? 9 : 1;
 
 template <int TW, int TH, int KIND, int CH, bool PERSIST>
-__global__ void __launch_bounds__(kFwdThreads<TW, TH, KIND, CH>) composite_forward_kernel(const float4* __restrict__ rec,
+__global__ void __launch_bounds__(kFwdThreads<TW, TH, KIND, CH>, kFwdMinBlocks<TW, TH, KIND, CH>)
+    composite_forward_kernel(const float4* __restrict__ rec,
                                                                    const uint32_t* __restrict__ ids,
                                                                    const uint2* __restrict__ ranges, RenderParams rp,
                                                                    const ViewParams* __restrict__ views,
