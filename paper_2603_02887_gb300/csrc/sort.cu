@@ -324,19 +324,35 @@ __global__ void tile_ranges_kernel(const uint32_t* __restrict__ tiles, const uin
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t npairs = npairs_dev ? min(*npairs_dev, npairs_cap) : npairs_cap;
   if (i >= npairs) return;
-  // a pair naming a record or tile out of range (never from a correct sort) is skipped and reported (the
-  // record index only where it selects the view; the compositing checks it anyway)
-  if (n_views > 1 && vals[i] >= n_per_view * n_views) {
+  if (n_views == 1) {
+    const uint32_t t = tiles[i];
+    if (t >= ntiles) {  // never from a correct sort: skipped and reported
+      atomicOr(check, kCheckTile);
+      return;
+    }
+    if (i == 0 || tiles[i - 1] != t) ranges[t].x = i;
+    if (i == npairs - 1 || tiles[i + 1] != t) ranges[t].y = i + 1;
+    return;
+  }
+  // a batch: a run is a (view-local tile, view) pair, compared without the view table; only the first and
+  // last pair of a run look up the view's first tile
+  const uint32_t n_records = n_per_view * n_views;
+  const uint32_t v = vals[i];
+  if (v >= n_records) {  // never from a correct sort: skipped and reported (the compositing checks it too)
     atomicOr(check, kCheckIndex);
     return;
   }
-  const uint32_t t = global_tile(tiles, vals, views, n_per_view, n_views, i);
+  const uint32_t loc = tiles[i], view = v / n_per_view;
+  auto same = [&](uint32_t j) { return tiles[j] == loc && vals[j] / n_per_view == view; };
+  const bool first = i == 0 || !same(i - 1), last = i == npairs - 1 || !same(i + 1);
+  if (!(first || last)) return;
+  const uint32_t t = __ldg(&views[view].tile_base) + loc;
   if (t >= ntiles) {
     atomicOr(check, kCheckTile);
     return;
   }
-  if (i == 0 || global_tile(tiles, vals, views, n_per_view, n_views, i - 1) != t) ranges[t].x = i;
-  if (i == npairs - 1 || global_tile(tiles, vals, views, n_per_view, n_views, i + 1) != t) ranges[t].y = i + 1;
+  if (first) ranges[t].x = i;
+  if (last) ranges[t].y = i + 1;
 }
 
 __global__ void compose_keys_kernel(const uint32_t* __restrict__ tiles, const uint32_t* __restrict__ vals,
