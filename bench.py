@@ -34,7 +34,7 @@ MODELS = ("exp", "sub", "lin", "sup")
 # ngs_autotune's pick for this workload on GB300 (render + backward; the bench re-tunes with --autotune):
 # fixed so that runs are reproducible and the recorded ncu traffic (profiles/composite_traffic.json)
 # applies to the launches timed.
-TUNED_OPTIONS = "exp=8x8/64/persistent,sub=16x16/128/persistent,lin=16x16/128/tiles,sup=16x16/128/persistent"
+TUNED_OPTIONS = "exp=8x8/32/persistent,sub=16x16/128/persistent,lin=16x16/128/tiles,sup=16x16/128/tiles"
 METRIC = "Mpix/s fwd & fwd+bwd per transmittance model; overdraw/pixel; p50/p99 latency"
 WORKLOAD = "single view, 500k clustered Gaussians (SH 3, FP32), 1920x1080, 4 transmittance models, fwd+bwd"
 
