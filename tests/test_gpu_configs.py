@@ -7,6 +7,9 @@ on 16x16), on outputs the FP64 oracle computes one by one: windows of the full f
   ragged since 1080 = 67.5 x 16);
 * the pair sort of the exponential model's 8x8 tiles at 1920x1080 with 500k and 2M Gaussians: properties
   of the whole sorted array, and sampled tiles against the oracle's list for each;
+* batched multi-view: 3M clustered Gaussians from 32 cameras of uneven size in one batch, forward for the
+  four models on windows of three views, and the batch's gradient from an upstream gradient on one
+  view's window against the oracle's gradients of that window;
 * differentiation: 1M clustered Gaussians at 1297x840, forward + path-replay backward for the four models
   with an L1-type upstream gradient restricted to a 256x256 window, against the oracle's gradients of that
   window; and the GPU's gradient on 64 random raw parameters against central differences of the FP64
@@ -210,3 +213,60 @@ def test_differentiation_1m_finite_differences(rnd, diff_scene, fd_window, model
     assert checked == 64
     print(f"[parity] 1M/1297x840 {model}: finite differences of the FP64 oracle, 64 samples, worst "
           f"|an - fd| / max(|fd|, floor) = {worst:.2e}")
+
+
+# The batched workload's launch options: what ngs_autotune picks for it on GB300 (bench.py's batched leg
+# tunes them on every run; they do not change any result).
+BATCH_OPTS = {"exp": dict(tile_w=16, tile_h=16, chunk=128, schedule="tiles"),
+              **{m: dict(tile_w=16, tile_h=32, chunk=256, schedule="tiles") for m in ("sub", "lin", "sup")}}
+
+
+@pytest.fixture(scope="module")
+def batched_scene():
+    return synth.clustered_scene(3_000_000, seed=0, sh_degree=3), synth.orbit_cameras(32, radius=12.0, seed=2)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_batched_3m_32_views(rnd, batched_scene, model):
+    """The batched configuration at full size (3M Gaussians, 32 views of 640x360 .. 1920x1080 in one
+    batch): every pixel of a 40x40 window at the centre of views 0, 13 and 31 against the oracle's outcomes;
+    then the batch's gradient for an upstream gradient that is nonzero on a 48x48 window of view 13 only,
+    against the oracle's gradients of that window (rendered from the Gaussians that can reach it: every
+    other Gaussian's GPU gradient must be exactly zero)."""
+    scene, cams = batched_scene
+    params = upload(scene)
+    images, overdraw, frame = rnd.render_batch(params, cams, model, options=BATCH_OPTS[model])
+    imgs, ods = frame.split(images), frame.split(overdraw)
+    for v in (0, 13, 31):
+        c = cams[v]
+        win = (c["width"] // 2 - 20, c["height"] // 2 - 20, 40, 40)
+        x0, y0, w, h = win
+        ref = oracle.render(scene, c, model, window=win, nthreads=NT, outcomes=True)
+        m = parity.assert_forward(imgs[v].cpu().numpy()[y0:y0 + h, x0:x0 + w],
+                                  ods[v].cpu().numpy()[y0:y0 + h, x0:x0 + w], ref, label=f"{model} view {v}")
+        assert m.n_unresolved == 0, m.summary()
+        assert ref["overdraw"].mean() > 0.5, (v, win)
+        print(f"[parity] batched 3M x 32 {model} view {v} {win}: {m.summary()}")
+    v = 13
+    c = cams[v]
+    win = (c["width"] // 2 + 16, c["height"] // 2 - 24, 48, 48)
+    x0, y0, w, h = win
+    gw = synth.upstream_gradient(h, w, seed=21)
+    base = int(frame.view()["view_pixel_base"][v])
+    dl = torch.zeros((images.shape[0], 3), dtype=torch.float32)
+    rows = base + (np.arange(y0, y0 + h)[:, None] * c["width"] + np.arange(x0, x0 + w)[None, :]).reshape(-1)
+    dl[torch.from_numpy(rows)] = torch.from_numpy(gw.reshape(-1, 3))
+    grads = {k: t.cpu().numpy() for k, t in rnd.backward(frame, params, dl.cuda()).items()}
+    sub, idx = _window_subscene(scene, c, win)
+    ref = oracle.render(sub, c, model, window=win, nthreads=NT, dl_dimage=gw.astype(np.float64), outcomes=True)
+    m = parity.assert_forward(imgs[v].cpu().numpy()[y0:y0 + h, x0:x0 + w], ods[v].cpu().numpy()[y0:y0 + h, x0:x0 + w],
+                              ref, label=f"{model} view {v} gradient window")
+    others = np.ones(len(scene["means"]), bool)
+    others[idx] = False
+    for k in PARAM_KEYS:
+        assert not np.any(grads["d_" + k][others]), (model, k)  # Gaussians that cannot reach the window
+    rep = parity.assert_gradients({k: g[idx] for k, g in grads.items()}, ref, m, label=model)
+    assert np.count_nonzero(ref["d_opacity_logits"]) > 100
+    print(f"[parity] batched 3M x 32 {model} view {v} gradients {win}: {m.summary()}; {rep.summary()}")
+    rnd.recycle(frame)
+
